@@ -1,0 +1,209 @@
+"""CPU oracle for the LambdaCC best-move / contraction path.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the CPU-baseline
+leg of the benchmark may import this package; the library never does.  The
+arithmetic lives in ``lcc_oracle.c`` (plain single-threaded C, exact int128
+gains); this module only marshals numpy arrays through ctypes.
+
+Graphs are CSR triples ``(off int64[n+1], nbr int32[nnz], w int64[nnz])``;
+an unweighted graph passes ``w`` of ones.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build, LIB
+
+NODEW_UNIT, NODEW_DEGREE, NODEW_CUSTOM = 0, 1, 2
+VSET_ALL, VSET_NBR_VERTICES, VSET_NBR_CLUSTERS = 0, 1, 2
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(LIB)
+        P = C.c_void_p
+        I64 = C.c_int64
+        _lib.orc_objective.argtypes = [I64, P, P, P, P, I64, I64, P, P, P]
+        _lib.orc_objective_pairs.argtypes = [I64, P, P, P, P, I64, I64, P, P, P]
+        _lib.orc_desired_range.argtypes = [I64, I64, I64, P, P, P, P, I64, I64,
+                                           P, P, P]
+        _lib.orc_compress.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_free.argtypes = [P]
+        _lib.orc_cluster.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
+                                     C.c_int, C.c_int, C.c_int, C.c_int, P, P,
+                                     P, P, P]
+        _lib.orc_best_moves.argtypes = [I64, P, P, P, P, I64, I64, C.c_int,
+                                        C.c_int, P, P]
+        _lib.orc_sequential_sweep.argtypes = [I64, P, P, P, P, I64, I64, P, I64]
+        _lib.orc_sequential_sweep.restype = I64
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _i128(hi, lo):
+    return (int(hi) << 64) | int(lo)
+
+
+def _graph(off, nbr, w):
+    off = _c(off, np.int64)
+    nbr = _c(nbr, np.int32)
+    w = np.ones(len(nbr), np.int64) if w is None else _c(w, np.int64)
+    return off, nbr, w
+
+
+def objective_num(off, nbr, w, k, p, q, labels, literal=False):
+    """Exact q * CC(labels) as a Python int (Sec. 2 objective, ordered pairs).
+
+    literal=True evaluates the O(n^2) double sum of the definition."""
+    off, nbr, w = _graph(off, nbr, w)
+    k = _c(k, np.int64)
+    labels = _c(labels, np.int32)
+    hi = C.c_int64()
+    lo = C.c_uint64()
+    fn = lib().orc_objective_pairs if literal else lib().orc_objective
+    rc = fn(len(off) - 1, _p(off), _p(nbr), _p(w), _p(k), p, q, _p(labels),
+            C.byref(hi), C.byref(lo))
+    if rc:
+        raise ValueError("oracle objective failed: %d" % rc)
+    v = _i128(hi.value, lo.value)
+    if v >= 1 << 127:
+        v -= 1 << 128
+    return v
+
+
+def desired(off, nbr, w, k, p, q, L, K, v0=0, v1=None):
+    """Desired cluster D[v] of every v in [v0, v1) under the snapshot (L, K)."""
+    off, nbr, w = _graph(off, nbr, w)
+    n = len(off) - 1
+    v1 = n if v1 is None else v1
+    offw = _c(off[v0:v1 + 1] - off[v0], np.int64)
+    nbrw = nbr[off[v0]:off[v1]]
+    ww = w[off[v0]:off[v1]]
+    k = _c(k, np.int64)
+    L = _c(L, np.int32)
+    K = _c(K, np.int64)
+    D = np.empty(v1 - v0, np.int32)
+    rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
+                                 p, q, _p(L), _p(K), _p(D))
+    if rc:
+        raise ValueError("oracle desired failed: %d" % rc)
+    return D
+
+
+def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K):
+    """As desired(), with rows [v0, v1) already cut out as a CSR window."""
+    offw = _c(offw, np.int64)
+    nbrw = _c(nbrw, np.int32)
+    ww = _c(ww, np.int64)
+    k = _c(k, np.int64)
+    L = _c(L, np.int32)
+    K = _c(K, np.int64)
+    D = np.empty(v1 - v0, np.int32)
+    rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
+                                 p, q, _p(L), _p(K), _p(D))
+    if rc:
+        raise ValueError("oracle desired failed: %d" % rc)
+    return D
+
+
+def compress(off, nbr, w, k, L):
+    """Compress (Sec. 3.1): returns (map, off2, nbr2, w2, k2)."""
+    off, nbr, w = _graph(off, nbr, w)
+    n = len(off) - 1
+    k = _c(k, np.int64)
+    L = _c(L, np.int32)
+    mp = np.empty(n, np.int32)
+    n2 = C.c_int64()
+    nnz2 = C.c_int64()
+    po = C.c_void_p()
+    pn = C.c_void_p()
+    pw = C.c_void_p()
+    pk = C.c_void_p()
+    rc = lib().orc_compress(n, _p(off), _p(nbr), _p(w), _p(k), _p(L), _p(mp),
+                            C.byref(n2), C.byref(nnz2), C.byref(po),
+                            C.byref(pn), C.byref(pw), C.byref(pk))
+    if rc:
+        raise ValueError("oracle compress failed: %d" % rc)
+
+    def take(ptr, cnt, ct, dt):
+        if cnt == 0:
+            out = np.empty(0, dt)
+        else:
+            out = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)),
+                                        shape=(cnt,)).astype(dt, copy=True)
+        lib().orc_free(ptr)
+        return out
+
+    off2 = take(po, n2.value + 1, C.c_int64, np.int64)
+    nbr2 = take(pn, nnz2.value, C.c_int32, np.int32)
+    w2 = take(pw, nnz2.value, C.c_int64, np.int64)
+    k2 = take(pk, n2.value, C.c_int64, np.int64)
+    return mp, off2, nbr2, w2, k2
+
+
+def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
+            max_levels=64, refine=True, vset=VSET_NBR_VERTICES):
+    """Parallel-CC (Algorithm 1, synchronous).
+
+    Returns (labels, num, den, stats): the objective is CC = num / den exactly
+    (den = q, or q * 2m in DEGREE mode); stats = (levels, rounds, edges)."""
+    off, nbr, w = _graph(off, nbr, w)
+    n = len(off) - 1
+    kk = _c(k, np.int64) if k is not None else np.zeros(1, np.int64)
+    labels = np.empty(n, np.int32)
+    hi = C.c_int64()
+    lo = C.c_uint64()
+    den = C.c_int64()
+    st = np.zeros(3, np.int64)
+    rc = lib().orc_cluster(n, _p(off), _p(nbr), _p(w), _p(kk), mode, p, q,
+                           num_iter, max_levels, int(bool(refine)), vset,
+                           _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
+                           _p(st))
+    if rc:
+        raise ValueError("oracle cluster failed: %d" % rc)
+    v = _i128(hi.value, lo.value)
+    if v >= 1 << 127:
+        v -= 1 << 128
+    return labels, v, den.value, tuple(int(x) for x in st)
+
+
+def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES):
+    """Best-Moves on one level from labels L (modified copy returned)."""
+    off, nbr, w = _graph(off, nbr, w)
+    k = _c(k, np.int64)
+    L = _c(L, np.int32).copy()
+    rounds = C.c_int64()
+    rc = lib().orc_best_moves(len(off) - 1, _p(off), _p(nbr), _p(w), _p(k), p,
+                              q, num_iter, vset, _p(L), C.byref(rounds))
+    if rc < 0:
+        raise ValueError("oracle best_moves failed: %d" % rc)
+    return L, bool(rc), rounds.value
+
+
+def sequential_sweep(off, nbr, w, k, p, q, L, max_moves):
+    off, nbr, w = _graph(off, nbr, w)
+    k = _c(k, np.int64)
+    L = _c(L, np.int32).copy()
+    mv = lib().orc_sequential_sweep(len(off) - 1, _p(off), _p(nbr), _p(w),
+                                    _p(k), p, q, _p(L), max_moves)
+    if mv < 0:
+        raise MemoryError("oracle sweep failed")
+    return L, mv
+
+
+def degrees(off, nbr, w):
+    off, nbr, w = _graph(off, nbr, w)
+    n = len(off) - 1
+    return np.add.reduceat(np.append(w, 0), off[:-1])[:n] * (np.diff(off) > 0)

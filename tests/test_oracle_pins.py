@@ -1,0 +1,445 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests re-derives the oracle's own formulas: the objective is
+checked against the ordered-pair definition evaluated pair by pair, against
+networkx's modularity, and against closed forms; the best-move rule is checked
+by brute force (move the vertex, re-evaluate the definition); Compress by the
+contraction identity and by a dictionary rebuild; whole runs by closed forms
+on disjoint cliques and the oscillating edge.
+"""
+import itertools
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_01731_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers --
+
+def dense(g):
+    n = g["n"]
+    W = np.zeros((n, n), dtype=object)
+    E = np.zeros((n, n), dtype=bool)
+    off, nbr = g["off"], g["nbr"]
+    w = g["w"] if g["w"] is not None else np.ones(len(nbr), np.int64)
+    for u in range(n):
+        for e in range(off[u], off[u + 1]):
+            W[u, nbr[e]] += int(w[e])
+            E[u, nbr[e]] = True
+    return W, E
+
+
+def cc_definition(W, E, k, lam, labels):
+    """CC(x) = sum over ordered (i, j) in V x V of w'_ij (1 - x_ij), Sec. 2."""
+    n = len(labels)
+    tot = Fraction(0)
+    for i in range(n):
+        for j in range(n):
+            if i == j or labels[i] != labels[j]:
+                continue
+            wp = -lam * int(k[i]) * int(k[j])
+            if E[i, j]:
+                wp += W[i, j]
+            tot += wp
+    return tot
+
+
+def small_graph(seed, n=7, p=0.5, lo=-3, hi=5):
+    return I.to_numpy(I.random_signed_graph(n, p, lo, hi, seed))
+
+
+def brute_desired(g, W, E, k, p, q, L, v):
+    """Desired cluster of v by brute force: try every candidate target
+    (neighbouring clusters, and the empty cluster v when it is empty), score
+    each by re-evaluating the objective definition, keep the best (ties to
+    the smallest id) and move only if strictly better than staying."""
+    lam = Fraction(p, q)
+    off, nbr = g["off"], g["nbr"]
+    cands = set(int(L[u]) for u in nbr[off[v]:off[v + 1]])
+    cands.discard(int(L[v]))
+    K = {}
+    for x in range(g["n"]):
+        K[int(L[x])] = K.get(int(L[x]), 0) + int(k[x])
+    if int(L[v]) != v and K.get(v, 0) == 0:
+        cands.add(v)
+    base = cc_definition(W, E, k, lam, L)
+    best, best_c = None, None
+    for c in sorted(cands):
+        L2 = L.copy()
+        L2[v] = c
+        val = cc_definition(W, E, k, lam, L2)
+        if best is None or val > best:
+            best, best_c = val, c
+    if best is not None and best > base:
+        return best_c
+    return int(L[v])
+
+
+def set_partitions(n):
+    """All set partitions of range(n) as restricted growth strings."""
+    def rec(i, a, m):
+        if i == n:
+            yield list(a)
+            return
+        for c in range(m + 1):
+            a.append(c)
+            yield from rec(i + 1, a, max(m, c + 1))
+            a.pop()
+    yield from rec(0, [], 0)
+
+
+# ------------------------------------------------------------- objective --
+
+@pytest.mark.parametrize("seed", range(6))
+def test_objective_matches_ordered_pair_definition(seed):
+    g = small_graph(seed)
+    W, E = dense(g)
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, 4, g["n"])
+    for p, q in [(1, 3), (2, 5), (7, 2)]:
+        for trial in range(4):
+            L = rng.integers(0, g["n"], g["n"]).astype(np.int32)
+            want = cc_definition(W, E, k, Fraction(p, q), L) * q
+            assert want.denominator == 1
+            got = O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, L)
+            got_lit = O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, L,
+                                      literal=True)
+            assert got == want.numerator
+            assert got_lit == want.numerator
+
+
+def test_objective_singletons_is_zero_and_one_cluster_closed_form():
+    g = I.to_numpy(I.random_signed_graph(30, 0.3, -4, 9, 11))
+    n = g["n"]
+    k = np.arange(n) % 5
+    assert O.objective_num(g["off"], g["nbr"], g["w"], k, 3, 7,
+                           np.arange(n, dtype=np.int32)) == 0
+    # everything in one cluster: q * sum_{ordered edges} w - p ((sum k)^2 - sum k^2)
+    S = int(np.sum(g["w"].astype(np.int64)))
+    want = 7 * S - 3 * (int(k.sum()) ** 2 - int((k.astype(np.int64) ** 2).sum()))
+    assert O.objective_num(g["off"], g["nbr"], g["w"], k, 3, 7,
+                           np.zeros(n, np.int32)) == want
+
+
+def test_modularity_mode_matches_networkx():
+    """Sec. 2: with k_v = d_v and lambda = gamma / 2m, CC / 2m is the
+    modularity of Reichardt-Bornholdt without the i = j terms; networkx
+    includes them, so Q_paper = Q_nx + gamma * sum_i d_i^2 / (2m)^2."""
+    nx = pytest.importorskip("networkx")
+    G = nx.karate_club_graph()
+    n = G.number_of_nodes()
+    rows = [[] for _ in range(n)]
+    for a, b in G.edges():
+        rows[a].append(b)
+        rows[b].append(a)
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    nbr = np.array([x for r in rows for x in sorted(r)], np.int32)
+    labels, num, den, _ = O.cluster(off, nbr, None, 1, 1, mode=O.NODEW_DEGREE)
+    two_m = 2 * G.number_of_edges()
+    assert den == two_m
+    comms = {}
+    for v, c in enumerate(labels):
+        comms.setdefault(int(c), set()).add(v)
+    q_nx = nx.community.modularity(G, list(comms.values()), weight=None, resolution=1.0)
+    deg = np.diff(off)
+    q_paper = num / den / two_m
+    assert abs(q_paper - (q_nx + float((deg ** 2).sum()) / two_m ** 2)) < 1e-12
+    # and for arbitrary labels, with a resolution gamma = 3/4
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        L = rng.integers(0, 5, n).astype(np.int32)
+        cs = {}
+        for v, c in enumerate(L):
+            cs.setdefault(int(c), set()).add(v)
+        qn = nx.community.modularity(G, list(cs.values()), weight=None, resolution=0.75)
+        num = O.objective_num(off, nbr, None, deg, 3, 4 * two_m, L)
+        qp = Fraction(num, 4 * two_m) / two_m
+        assert abs(float(qp) - (qn + 0.75 * float((deg ** 2).sum()) / two_m ** 2)) < 1e-12
+
+
+# ------------------------------------------------------------- best move --
+
+@pytest.mark.parametrize("seed", range(8))
+def test_desired_cluster_by_brute_force(seed):
+    """Appendix A gain, the stay term, ties and the empty-cluster move, all
+    against re-evaluation of the objective definition."""
+    g = small_graph(100 + seed, n=7, p=0.55)
+    W, E = dense(g)
+    rng = np.random.default_rng(seed)
+    n = g["n"]
+    for p, q in [(1, 2), (1, 5), (3, 1)]:
+        for trial in range(5):
+            k = rng.integers(0, 3, n)
+            L = rng.integers(0, n, n).astype(np.int32)
+            if trial == 0:
+                L = np.arange(n, dtype=np.int32)
+            K = np.zeros(n, np.int64)
+            np.add.at(K, L, k)
+            D = O.desired(g["off"], g["nbr"], g["w"], k, p, q, L, K)
+            for v in range(n):
+                assert D[v] == brute_desired(g, W, E, k, p, q, L, v), (v, L, k)
+
+
+def test_sync_round_is_simultaneous_application_of_brute_force_moves():
+    g = small_graph(7, n=8, p=0.5)
+    W, E = dense(g)
+    n = g["n"]
+    k = np.ones(n, np.int64)
+    L0 = np.arange(n, dtype=np.int32)
+    for p, q in [(1, 4), (1, 2)]:
+        want = np.array([brute_desired(g, W, E, k, p, q, L0, v) for v in range(n)],
+                        np.int32)
+        L1, moved, rounds = O.best_moves(g["off"], g["nbr"], g["w"], k, p, q, L0, 1)
+        assert rounds == 1
+        assert np.array_equal(L1, want)
+
+
+@pytest.mark.parametrize("vset", [O.VSET_ALL, O.VSET_NBR_VERTICES, O.VSET_NBR_CLUSTERS])
+def test_best_moves_rounds_and_vertex_subsets(vset):
+    """Algorithm 1's loop: V' = V, then the Sec. 3.2.2 subset after each
+    round; stop when a round makes no move."""
+    for seed in range(3):
+        g = small_graph(40 + seed, n=8, p=0.45, lo=-1, hi=4)
+        W, E = dense(g)
+        n = g["n"]
+        k = np.ones(n, np.int64)
+        p, q = 1, 3
+        L = np.arange(n, dtype=np.int32)
+        vp = np.ones(n, bool)
+        off, nbr = g["off"], g["nbr"]
+        sims = [L.copy()]
+        for _ in range(4):
+            D = L.copy()
+            for v in range(n):
+                if vp[v]:
+                    D[v] = brute_desired(g, W, E, k, p, q, L, v)
+            moved = D != L
+            if not moved.any():
+                break
+            left = set(int(x) for x in L[moved])
+            L = D
+            nxt = np.zeros(n, bool)
+            if vset == O.VSET_ALL:
+                nxt[:] = True
+            elif vset == O.VSET_NBR_VERTICES:
+                for v in np.nonzero(moved)[0]:
+                    nxt[nbr[off[v]:off[v + 1]]] = True
+            else:
+                for x in range(n):
+                    if int(L[x]) in left:
+                        nxt[nbr[off[x]:off[x + 1]]] = True
+            vp = nxt
+            sims.append(L.copy())
+        for r in range(1, len(sims)):
+            Lr, _, _ = O.best_moves(off, nbr, g["w"], k, p, q,
+                                    np.arange(n, dtype=np.int32), r, vset=vset)
+            assert np.array_equal(Lr, sims[r]), (seed, r)
+
+
+def test_sequential_moves_strictly_raise_objective():
+    """Algorithm 2's inner loop: a single best move never lowers CC."""
+    for seed in range(4):
+        g = I.to_numpy(I.random_signed_graph(25, 0.25, -2, 6, 200 + seed))
+        n = g["n"]
+        k = (np.arange(n) % 3).astype(np.int64)
+        p, q = 1, 6
+        L = np.arange(n, dtype=np.int32)
+        prev = O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, L)
+        steps = 0
+        while steps < 200:
+            L2, mv = O.sequential_sweep(g["off"], g["nbr"], g["w"], k, p, q, L, 1)
+            if mv == 0:
+                break
+            cur = O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, L2)
+            assert cur > prev
+            prev, L = cur, L2
+            steps += 1
+        assert steps > 0
+
+
+def test_figure1_concurrent_moves_lower_objective():
+    """Sec. 3.1, Figure 1 (weights are this project's reading; the caption's
+    numbers are the paper's)."""
+    fx = json.load(open(os.path.join(GOLDEN, "fig1_reading.json")))
+    n = 3
+    rows = [[] for _ in range(n)]
+    for a, b, w in fx["edges"]:
+        rows[a].append((b, w))
+        rows[b].append((a, w))
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    nbr = np.array([x for r in rows for x, _ in sorted(r)], np.int32)
+    w = np.array([y for r in rows for _, y in sorted(r)], np.int64)
+    k = np.ones(n, np.int64)
+    p, q = fx["lambda_p"], fx["lambda_q"]
+    L = np.arange(n, dtype=np.int32)
+    assert O.objective_num(off, nbr, w, k, p, q, L) == 2 * fx["objective_before_unordered"]
+    K = np.ones(n, np.int64)
+    D = O.desired(off, nbr, w, k, p, q, L, K)
+    # b and c each choose the cluster {a}; a is not scheduled in the caption
+    assert D[1] == 0 and D[2] == 0
+    L2 = L.copy()
+    L2[1], L2[2] = D[1], D[2]
+    got = O.objective_num(off, nbr, w, k, p, q, L2)
+    assert got == 2 * fx["objective_after_unordered"] * q
+
+
+# -------------------------------------------------------------- compress --
+
+def test_compress_dictionary_rebuild_and_node_weights():
+    for seed in range(5):
+        g = I.to_numpy(I.random_signed_graph(40, 0.15, -3, 7, 300 + seed))
+        n = g["n"]
+        rng = np.random.default_rng(seed)
+        L = rng.integers(0, n, n).astype(np.int32)
+        k = rng.integers(0, 5, n).astype(np.int64)
+        mp, off2, nbr2, w2, k2 = O.compress(g["off"], g["nbr"], g["w"], k, L)
+        occ = sorted(set(int(x) for x in L))
+        rank = {c: i for i, c in enumerate(occ)}
+        assert np.array_equal(mp, np.array([rank[int(x)] for x in L], np.int32))
+        want = {}
+        for u in range(n):
+            for e in range(g["off"][u], g["off"][u + 1]):
+                a, b = rank[int(L[u])], rank[int(L[g["nbr"][e]])]
+                if a != b:
+                    want[(a, b)] = want.get((a, b), 0) + int(g["w"][e])
+        got = {}
+        for a in range(len(occ)):
+            row = nbr2[off2[a]:off2[a + 1]]
+            assert np.all(np.diff(row) > 0)
+            for e in range(off2[a], off2[a + 1]):
+                got[(a, int(nbr2[e]))] = int(w2[e])
+        assert got == want
+        kw = np.zeros(len(occ), np.int64)
+        np.add.at(kw, mp, k)
+        assert np.array_equal(k2, kw)
+
+
+def test_contraction_preserves_objective():
+    """CC_G(flatten(C')) = CC_G'(C') + CC_G(C): Compress keeps every
+    inter-cluster pair's weight and k' = K, so the objective splits exactly."""
+    for seed in range(6):
+        g = I.to_numpy(I.random_signed_graph(30, 0.2, -3, 6, 400 + seed))
+        n = g["n"]
+        rng = np.random.default_rng(seed)
+        L = rng.integers(0, 10, n).astype(np.int32)
+        k = rng.integers(0, 4, n).astype(np.int64)
+        p, q = 2, 9
+        mp, off2, nbr2, w2, k2 = O.compress(g["off"], g["nbr"], g["w"], k, L)
+        n2 = len(k2)
+        L2 = rng.integers(0, n2, n2).astype(np.int32)
+        flat = L2[mp]
+        lhs = O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, flat)
+        rhs = (O.objective_num(off2, nbr2, w2, k2, p, q, L2)
+               + O.objective_num(g["off"], g["nbr"], g["w"], k, p, q, L))
+        assert lhs == rhs
+
+
+# ------------------------------------------------------------ whole runs --
+
+def cliques(r, s, seed):
+    n = r * s
+    perm = np.random.default_rng(seed).permutation(n)
+    a, b = [], []
+    for c in range(r):
+        for i in range(s):
+            for j in range(i + 1, s):
+                a.append(perm[c * s + i])
+                b.append(perm[c * s + j])
+    import torch
+    a = torch.tensor(a, dtype=torch.int64)
+    b = torch.tensor(b, dtype=torch.int64)
+    g = I.to_numpy(I.pairs_to_csr(torch.minimum(a, b), torch.maximum(a, b), n))
+    members = [sorted(perm[c * s:(c + 1) * s]) for c in range(r)]
+    return g, members
+
+
+@pytest.mark.parametrize("r,s,p,q", [(5, 3, 1, 2), (4, 5, 1, 3), (3, 8, 2, 3), (6, 4, 1, 100)])
+def test_disjoint_cliques_closed_form(r, s, p, q):
+    g, members = cliques(r, s, r * 100 + s)
+    labels, num, den, st = O.cluster(g["off"], g["nbr"], None, p, q)
+    for mem in members:
+        assert all(labels[v] == mem[0] for v in mem)
+    assert den == q
+    assert num == r * s * (s - 1) * (q - p)
+    # rounds: 3 at level 0 (two moving rounds, one quiet), 1 at level 1
+    # (no edges), 1 refinement round at level 0
+    assert st[0] == 2
+    assert st[1] == 5
+
+
+def test_isolated_edge_oscillates_then_stops():
+    import torch
+    g = I.to_numpy(I.pairs_to_csr(torch.tensor([0]), torch.tensor([1]), 2))
+    for it in (1, 2, 5, 10):
+        L, moved, rounds = O.best_moves(g["off"], g["nbr"], None, np.ones(2), 1, 3,
+                                        np.arange(2, dtype=np.int32), it)
+        assert rounds == it
+        assert list(L) == ([1, 0] if it % 2 else [0, 1])
+    labels, num, den, st = O.cluster(g["off"], g["nbr"], None, 1, 3, num_iter=7)
+    assert list(labels) == [0, 1] and num == 0 and st[1] == 7
+
+
+def test_never_worse_than_best_partition_bound_and_exact_on_cliques():
+    for seed in range(3):
+        g = small_graph(500 + seed, n=7, p=0.5, lo=-2, hi=4)
+        W, E = dense(g)
+        n = g["n"]
+        k = np.ones(n)
+        p, q = 1, 4
+        labels, num, den, _ = O.cluster(g["off"], g["nbr"], g["w"], p, q)
+        best = max(cc_definition(W, E, k, Fraction(p, q), np.array(a))
+                   for a in set_partitions(n))
+        assert Fraction(num, den) <= best
+    g, members = cliques(2, 4, 1)
+    W, E = dense(g)
+    labels, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, 2)
+    best = max(cc_definition(W, E, np.ones(8), Fraction(1, 2), np.array(a))
+               for a in set_partitions(8))
+    assert Fraction(num, den) == best
+
+
+def test_planted_partition_easy_regime():
+    """In the easy regime p_in >> lambda >> p_out the run reaches at least the
+    planted partition's objective; at lambda = 1/40 it recovers it exactly."""
+    g = I.to_numpy(I.sbm([50] * 20, 0.3, 0.002, seed=9))
+    n = g["n"]
+    planted = g["planted"].astype(np.int32)
+    for q, exact in [(20, False), (40, True)]:
+        labels, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, q, num_iter=20)
+        planted_num = O.objective_num(g["off"], g["nbr"], None, np.ones(n), 1, q, planted)
+        assert num >= planted_num
+        if exact:
+            pairs = {}
+            for a, b in zip(labels, planted):
+                pairs.setdefault(int(b), set()).add(int(a))
+            assert all(len(s) == 1 for s in pairs.values())
+            assert len(set(int(x) for x in labels)) == 20
+
+
+def test_resolution_orders_cluster_counts():
+    """Sec. 4.1: lower lambda gives fewer (larger) clusters."""
+    g = I.to_numpy(I.sbm([40] * 10, 0.25, 0.02, seed=3))
+    counts = []
+    for p, q in [(1, 1000), (1, 40), (1, 8), (1, 2)]:
+        labels, *_ = O.cluster(g["off"], g["nbr"], None, p, q)
+        counts.append(len(set(int(x) for x in labels)))
+    assert counts == sorted(counts)
+    assert counts[0] < counts[-1]
+
+
+def test_deterministic_and_refinement_flag():
+    g = I.to_numpy(I.chung_lu(2000, 2.1, 8, seed=5))
+    a = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE)
+    b = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE)
+    assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+    c = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE, refine=False)
+    assert c[3][1] < a[3][1]

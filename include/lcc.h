@@ -1,0 +1,296 @@
+/*
+ * lcc.h -- C ABI of the GB300 LambdaCC library (liblcc.so).
+ *
+ * The library clusters an undirected weighted graph G = (V, E, w) under the
+ * LambdaCC objective of Shi et al., "Scalable Community Detection via Parallel
+ * Correlation Clustering" (arXiv 2108.01731):
+ *
+ *   CC(x) = sum over ordered pairs (i, j) in V x V of w'_ij (1 - x_ij),
+ *   w'_uu = 0, w'_uv = w_uv - lambda k_u k_v on edges, -lambda k_u k_v off
+ *   edges                                                   (Sec. 2)
+ *
+ * with the parallel Louvain method of Algorithm 1 run on the synchronous
+ * schedule of Sec. 3.2.1: every round computes each vertex's best move from a
+ * snapshot of the labels and cluster weights, then applies all moves at once;
+ * rounds stop when nothing moves or after num_iter rounds; the clustering is
+ * then compressed (Sec. 3.1, Appendix B) and the method recurses, flattens
+ * and refines (Sec. 3.2.3).
+ *
+ * Arithmetic.  lambda is the rational p/q with p, q > 0.  Every gain is an
+ * exact integer (gains are scaled by q), so labels are bit-identical from run
+ * to run and independent of thread scheduling.  Ties between candidate
+ * clusters go to the smallest cluster id, and a vertex moves only when the
+ * best candidate is strictly better than staying.  Vertex v may also move to
+ * cluster id v when that id has zero weight and none of v's neighbours is in
+ * it (gain 0).  Final labels are the smallest vertex id of each cluster.
+ *
+ * Conventions for every entry point:
+ *   - return an lcc_status; they never throw and never abort the process;
+ *     lcc_last_error() gives a detail message for the calling thread;
+ *   - host arrays are caller-owned and only read (or written, for outputs)
+ *     during the call; the library copies what it keeps;
+ *   - the GPU is the device current on the calling thread when the object is
+ *     created; every later call on that object uses the same device;
+ *   - `stream` is a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
+ *     or NULL for the legacy default stream.  Calls that return results on the
+ *     host synchronise that stream before returning.
+ */
+#ifndef LCC_H
+#define LCC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LCC_API __attribute__((visibility("default")))
+#else
+#define LCC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lcc_status {
+  LCC_OK = 0,
+  LCC_ERR_INVALID = 1,       /* bad argument or malformed CSR */
+  LCC_ERR_NOT_SYMMETRIC = 2, /* the multiset {(u,v,w)} differs from {(v,u,w)} */
+  LCC_ERR_SELF_LOOP = 3,     /* an entry u -> u */
+  LCC_ERR_OOM = 4,           /* device or host allocation failed */
+  LCC_ERR_OVERFLOW = 5,      /* a total exceeds the exact integer range */
+  LCC_ERR_TIMEOUT = 6,       /* a bounded wait ran out */
+  LCC_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  LCC_ERR_BUSY = 8,          /* the result is not ready yet (serving API) */
+  LCC_ERR_CANCELLED = 9      /* the job was cancelled (serving API) */
+} lcc_status;
+
+/* Node weights k (Sec. 2). */
+typedef enum lcc_nodew_mode {
+  LCC_NODEW_UNIT = 0,   /* k_v = 1; lambda = p / q */
+  LCC_NODEW_DEGREE = 1, /* modularity: k_v = sum_u w_uv, lambda = gamma / 2m
+                           with gamma = p / q and 2m = sum_v k_v (Sec. 2) */
+  LCC_NODEW_CUSTOM = 2  /* k given at load time (non-negative); lambda = p/q */
+} lcc_nodew_mode;
+
+/* The vertex subset V' examined in the rounds after the first (Sec. 3.2.2). */
+typedef enum lcc_vset {
+  LCC_VSET_ALL = 0,           /* V' = V every round */
+  LCC_VSET_NBR_VERTICES = 1,  /* neighbours of the vertices that moved */
+  LCC_VSET_NBR_CLUSTERS = 2   /* neighbours of every vertex now in a cluster
+                                 that some vertex moved out of */
+} lcc_vset;
+
+typedef enum lcc_memspace { LCC_MEM_HOST = 0, LCC_MEM_DEVICE = 1 } lcc_memspace;
+
+/* Schedule flags. */
+#define LCC_SCHED_TIMING 1 /* record per-phase device time in lcc_stats */
+
+typedef struct lcc_schedule {
+  int32_t num_iter;   /* max rounds per Best-Moves call (Algorithm 1); >= 0 */
+  int32_t max_levels; /* max recursion depth incl. the input level; >= 1 */
+  int32_t refine;     /* 1: Best-Moves again after each Flatten (Sec. 3.2.3) */
+  int32_t vset;       /* lcc_vset */
+  int32_t sync;       /* must be 1: the synchronous schedule (Sec. 3.2.1) */
+  int32_t flags;      /* LCC_SCHED_* */
+} lcc_schedule;
+
+typedef struct lcc_stats {
+  int32_t levels;          /* levels visited, including the input level */
+  int32_t rounds_total;    /* Best-Moves rounds over all levels */
+  int64_t edges_scanned;   /* sum of deg(v) over every vertex evaluated */
+  int64_t vertices_scanned;/* number of best-move evaluations */
+  int64_t candidates;      /* distinct neighbouring clusters scored */
+  int64_t num_clusters;    /* clusters in the final labelling */
+  int64_t obj_num_hi;      /* exact objective: CC = num / den, num = hi:lo */
+  uint64_t obj_num_lo;     /*   as a two's-complement 128-bit integer */
+  int64_t obj_den;         /* q, or q * 2m in LCC_NODEW_DEGREE mode */
+  double objective;        /* (double)num / den */
+  /* device time in ms, filled when LCC_SCHED_TIMING is set */
+  double ms_bestmove;      /* best-move kernels (all degree buckets) */
+  double ms_round_other;   /* frontier, apply and marking kernels */
+  double ms_contract;      /* compression (relabel, sort, reduce, CSR) */
+  double ms_other;         /* flatten, refinement set-up, final labels */
+  double ms_total;
+  int64_t bytes_bestmove;  /* algorithmic bytes of the best-move kernels */
+  int64_t pairs_sorted;    /* inter-cluster entries sorted by compression */
+  int64_t kernel_launches; /* kernels launched by this call */
+} lcc_stats;
+
+typedef struct lcc_graph lcc_graph;
+
+/*
+ * lcc_load_csr -- copy a CSR graph into device memory and validate it.
+ *
+ * offsets [n+1] int64, monotone, offsets[0] = 0, offsets[n] = nnz;
+ * nbrs    [nnz] int32 in [0, n);
+ * weights [nnz] int32 or NULL for an unweighted graph (w = 1);
+ * node_w  [n]   int64 >= 0, only read in LCC_NODEW_CUSTOM runs (may be NULL
+ *               otherwise).
+ * `memspace` says where the four arrays live (all in the same space).
+ * Both directions of every undirected edge must be present with equal
+ * weights (Sec. 2 graphs are undirected); there are no self loops.
+ * Returns LCC_ERR_INVALID (sizes, ranges, offsets), LCC_ERR_SELF_LOOP,
+ * LCC_ERR_NOT_SYMMETRIC, LCC_ERR_OVERFLOW (sum of |w| >= 2^62 or n >= 2^31)
+ * or LCC_ERR_OOM.  On success *out owns a device copy; free it with
+ * lcc_free_graph.
+ */
+LCC_API lcc_status lcc_load_csr(const int64_t *offsets, const int32_t *nbrs,
+                        const int32_t *weights, int64_t n, int64_t nnz,
+                        const int64_t *node_w, int32_t memspace, void *stream,
+                        lcc_graph **out);
+
+/* Sizes of a loaded graph. */
+LCC_API lcc_status lcc_graph_info(const lcc_graph *g, int64_t *n, int64_t *nnz);
+
+LCC_API void lcc_free_graph(lcc_graph *g);
+
+/*
+ * lcc_cluster -- Parallel-CC (Algorithm 1) on a loaded graph.
+ *
+ * lambda = lambda_p / lambda_q (gamma in LCC_NODEW_DEGREE mode); both > 0.
+ * sched NULL means {num_iter 10, max_levels 64, refine 1, nbr-vertices, sync}.
+ * labels_out [n] int32 receives the final labels (smallest vertex id of each
+ * cluster); it lives in `labels_memspace`.  objective_out (nullable) gets the
+ * objective CC as a double; stats_out (nullable) the exact value and counters.
+ * Runs on the stream given at load time.
+ */
+LCC_API lcc_status lcc_cluster(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q,
+                       int32_t mode, const lcc_schedule *sched,
+                       int32_t *labels_out, int32_t labels_memspace,
+                       double *objective_out, lcc_stats *stats_out);
+
+/*
+ * lcc_desired -- one synchronous best-move evaluation (Algorithm 1, the body
+ * of the parallel loop, with the Appendix A gain) on the input level.
+ *
+ * labels [n] (host) is the snapshot; cluster weights are K_c = sum of k_v
+ * over labels[v] = c.  frontier [n] (host, nullable = all) marks the vertices
+ * evaluated.  desired_out [n] (host) receives D[v] for evaluated vertices and
+ * labels[v] for the rest.
+ */
+LCC_API lcc_status lcc_desired(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q,
+                       int32_t mode, const int32_t *labels,
+                       const uint8_t *frontier, int32_t *desired_out);
+
+/*
+ * lcc_best_moves -- Best-Moves (Algorithm 1) on the input level, starting
+ * from labels_inout (host [n]) with V' = V, for at most num_iter rounds.
+ * Writes the labels back, the rounds run and whether anything moved.
+ */
+LCC_API lcc_status lcc_best_moves(const lcc_graph *g, int64_t lambda_p,
+                          int64_t lambda_q, int32_t mode, int32_t num_iter,
+                          int32_t vset, int32_t *labels_inout,
+                          int32_t *rounds_out, int32_t *moved_out);
+
+/*
+ * lcc_compress -- Compress (Sec. 3.1, Appendix B): every occupied cluster
+ * becomes a coarse vertex (ids ranked by cluster id) whose node weight is the
+ * cluster weight; edges between different clusters are merged by summing
+ * their weights; edges inside a cluster are dropped.  labels [n] (host).
+ * map_out [n] (host) gets the coarse vertex of each vertex.  *coarse_out is a
+ * new graph (int64 weights) whose node weights are the coarse k; free it with
+ * lcc_free_graph.  `mode` selects the input node weights as in lcc_cluster.
+ */
+LCC_API lcc_status lcc_compress(const lcc_graph *g, int32_t mode,
+                        const int32_t *labels, int32_t *map_out,
+                        lcc_graph **coarse_out);
+
+/*
+ * lcc_graph_export -- copy a graph back to the host: off [n+1], nbr [nnz],
+ * w [nnz] as int64, k [n] the node weights it was loaded or built with
+ * (1 for a graph loaded without node weights).  Any pointer may be NULL.
+ */
+LCC_API lcc_status lcc_graph_export(const lcc_graph *g, int64_t *off, int32_t *nbr,
+                            int64_t *w, int64_t *k);
+
+/*
+ * lcc_objective -- exact objective of labels [n] (host) on the input level:
+ * CC = num / den with num = (*num_hi : *num_lo) as a signed 128-bit integer.
+ */
+LCC_API lcc_status lcc_objective(const lcc_graph *g, int64_t lambda_p,
+                         int64_t lambda_q, int32_t mode, const int32_t *labels,
+                         int64_t *num_hi, uint64_t *num_lo, int64_t *den);
+
+/* ----------------------------------------------------------------------
+ * Batched and served clustering.
+ *
+ * Many graphs run through one engine: every round, one launch per kernel
+ * covers the current level of every active graph, and each graph keeps its
+ * own level stack, round counter and termination, so its labels are
+ * bit-identical to an lcc_cluster run on it alone.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * lcc_cluster_batch -- cluster `count` loaded graphs together.  All graphs
+ * must live on the same device.  lambda_p/lambda_q/mode are per graph
+ * (arrays of `count`); labels_out[i] is a host array [n_i].  objectives_out
+ * (nullable) [count].
+ */
+LCC_API lcc_status lcc_cluster_batch(const lcc_graph *const *graphs, int32_t count,
+                             const int64_t *lambda_p, const int64_t *lambda_q,
+                             const int32_t *mode, const lcc_schedule *sched,
+                             int32_t *const *labels_out,
+                             double *objectives_out);
+
+typedef struct lcc_server lcc_server;
+
+typedef struct lcc_server_cfg {
+  int64_t hbm_budget_bytes; /* admit while resident bytes stay under this */
+  int32_t max_slots;        /* max graphs resident at once */
+  int32_t reserved;
+  lcc_schedule sched;       /* schedule of every job */
+} lcc_server_cfg;
+
+typedef struct lcc_job {
+  const int64_t *offsets;   /* host CSR, copied at submit */
+  const int32_t *nbrs;
+  const int32_t *weights;   /* nullable */
+  int64_t n, nnz;
+  int64_t lambda_p, lambda_q;
+  int32_t mode;             /* LCC_NODEW_UNIT or LCC_NODEW_DEGREE */
+  int32_t reserved;
+} lcc_job;
+
+/*
+ * lcc_server_create -- start a serving engine on the current device with its
+ * own worker thread and stream.  Jobs submitted while others run are admitted
+ * between rounds as slots and HBM budget free up, and join the next round.
+ */
+LCC_API lcc_status lcc_server_create(const lcc_server_cfg *cfg, lcc_server **out);
+
+/* lcc_submit -- copy a job's CSR to pinned host memory and queue it.
+ * Returns LCC_ERR_INVALID for a malformed job, LCC_ERR_OOM if the job alone
+ * exceeds the budget.  *ticket identifies it. */
+LCC_API lcc_status lcc_submit(lcc_server *s, const lcc_job *job, uint64_t *ticket);
+
+/*
+ * lcc_poll -- LCC_ERR_BUSY while the job runs; then its status.  On LCC_OK
+ * labels_out [n] (host, nullable) and obj_out (nullable) receive the result
+ * and the ticket is released.  latency_ms_out (nullable) gets submit-to-done
+ * time.
+ */
+LCC_API lcc_status lcc_poll(lcc_server *s, uint64_t ticket, int32_t *labels_out,
+                    double *obj_out, double *latency_ms_out);
+
+/* lcc_cancel -- drop a queued or running job; its poll returns
+ * LCC_ERR_CANCELLED. */
+LCC_API lcc_status lcc_cancel(lcc_server *s, uint64_t ticket);
+
+/* lcc_server_wait_idle -- block until every submitted job has finished or
+ * timeout_ms passes (LCC_ERR_TIMEOUT). */
+LCC_API lcc_status lcc_server_wait_idle(lcc_server *s, int64_t timeout_ms);
+
+/* Counters of the serving engine: [0] jobs done, [1] ticks, [2] peak resident
+ * bytes, [3] peak concurrent jobs, [4] rejected jobs. */
+LCC_API lcc_status lcc_server_counters(lcc_server *s, int64_t *out5);
+
+/* Stops the worker (running jobs are cancelled) and frees everything. */
+LCC_API lcc_status lcc_server_destroy(lcc_server *s);
+
+LCC_API const char *lcc_status_str(lcc_status s);
+LCC_API const char *lcc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCC_H */

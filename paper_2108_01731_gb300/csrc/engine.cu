@@ -1,0 +1,890 @@
+// Tick engine: runs a set of jobs through Parallel-CC (Algorithm 1) on the
+// synchronous schedule (Sec. 3.2.1).  Each job is a state machine over its
+// level stack:
+//
+//   BM        one Best-Moves round per tick, all BM jobs in one launch per
+//             kernel; ends after a round without moves or num_iter rounds;
+//   CONTRACT  Compress of every job that finished coarsening with moves,
+//             batched into one relabel/emit/sort/reduce pass;
+//   UP        Flatten into the level below, then refinement (another
+//             Best-Moves on that level, Sec. 3.2.3) or the next Flatten;
+//   FINAL     canonical labels and the exact objective.
+//
+// Every job's arithmetic depends only on its own arrays, so its labels are
+// the same whether it runs alone or with others.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "engine.h"
+
+namespace lcc {
+
+std::atomic<long long> g_launches{0};
+
+void check_cuda(cudaError_t e, const char *what, int line) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    throw Error(LCC_ERR_OOM, std::string("out of device memory in ") + what);
+  }
+  throw Error(LCC_ERR_CUDA, std::string(what) + " (line " + std::to_string(line) +
+                                "): " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------- memory ----
+
+static std::mutex g_pool_mu;
+static std::unordered_map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t pool_for(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  CK(cudaMemPoolCreate(&pool, &props));
+  uint64_t thr = UINT64_MAX;
+  CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  g_pools[dev] = pool;
+  return pool;
+}
+
+void *dalloc(size_t bytes, cudaStream_t st) {
+  int dev;
+  CK(cudaGetDevice(&dev));
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for(dev), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? LCC_ERR_OOM : LCC_ERR_CUDA,
+                std::string("device allocation of ") + std::to_string(bytes) +
+                    " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// -------------------------------------------------------------- engine ----
+
+Engine::Engine(int dev, cudaStream_t st) : dev_(dev), st_(st) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  d_.sms = sms;
+  d_.dev = dev;
+  for (auto &e : ev_) CK(cudaEventCreate(&e));
+}
+
+Engine::~Engine() {
+  for (auto &e : ev_) cudaEventDestroy(e);
+  Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
+                    &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
+                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+  for (Scratch *s : all) s->release(st_);
+  cudaStreamSynchronize(st_);
+  if (h_stage_) cudaFreeHost(h_stage_);
+  if (h_stage2_) cudaFreeHost(h_stage2_);
+}
+
+size_t Engine::scratch_bytes() const {
+  const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
+                          &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
+                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+  size_t t = 0;
+  for (const Scratch *s : all) t += s->bytes;
+  return t;
+}
+
+void *Engine::stage(size_t bytes) {
+  // the previous upload from this buffer may still be in flight
+  CK(cudaStreamSynchronize(st_));
+  if (bytes > h_stage_bytes_) {
+    if (h_stage_) {
+      CK(cudaStreamSynchronize(st_));
+      cudaFreeHost(h_stage_);
+    }
+    size_t nb = bytes + bytes / 2 + 4096;
+    CK(cudaMallocHost(&h_stage_, nb));
+    h_stage_bytes_ = nb;
+  }
+  return h_stage_;
+}
+
+void *Engine::stage2(size_t bytes) {
+  if (bytes > h_stage2_bytes_) {
+    if (h_stage2_) {
+      CK(cudaStreamSynchronize(st_));
+      cudaFreeHost(h_stage2_);
+    }
+    size_t nb = bytes + bytes / 2 + 4096;
+    CK(cudaMallocHost(&h_stage2_, nb));
+    h_stage2_bytes_ = nb;
+  }
+  return h_stage2_;
+}
+
+float Engine::elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+static LJob ljob_of(const Level &L) {
+  LJob x;
+  memset(&x, 0, sizeof(x));
+  x.off = L.off;
+  x.nbr = L.nbr;
+  x.w = L.w;
+  x.k = L.k;
+  x.L = L.L;
+  x.K = L.K;
+  x.D = L.D;
+  x.n = L.n;
+  x.wtype = L.wtype;
+  return x;
+}
+
+// Uploads a table of T plus vstart (host vectors) through pinned staging.
+template <class T>
+static void upload_table(const std::vector<T> &tab, const std::vector<int64_t> &vs, T *d_tab,
+                         int64_t *d_vs, void *stage, cudaStream_t st) {
+  char *h = (char *)stage;
+  size_t a = tab.size() * sizeof(T);
+  memcpy(h, tab.data(), a);
+  memcpy(h + a, vs.data(), vs.size() * sizeof(int64_t));
+  CK(cudaMemcpyAsync(d_tab, h, a, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_vs, h + a, vs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+}
+
+static bool needs_wide(const Level &L, int64_t p, int64_t q, int64_t ktot) {
+  const i128 lim = (i128)1 << 62;
+  const i128 a = (i128)q * (i128)L.info.rmax;
+  const i128 b = (i128)p * (i128)L.info.kmax * (i128)ktot;
+  return a >= lim || b >= lim;
+}
+
+void Engine::level_stats(std::vector<Job *> &js, std::vector<Level *> &lvs) {
+  const int nj = (int)lvs.size();
+  if (nj == 0) return;
+  std::vector<LJob> tab(nj);
+  std::vector<int64_t> vs(nj + 1);
+  int64_t vt = 0;
+  for (int i = 0; i < nj; ++i) {
+    tab[i] = ljob_of(*lvs[i]);
+    vs[i] = vt;
+    vt += lvs[i]->n;
+  }
+  vs[nj] = vt;
+  LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+  LevelInfo *di = s_info_.get<LevelInfo>(nj, st_);
+  upload_table(tab, vs, dt, dv, stage(nj * (sizeof(LJob) + 8) + 8), st_);
+  CK(cudaMemsetAsync(di, 0, nj * sizeof(LevelInfo), st_));
+  launch_level_stats(dt, dv, nj, vt, di, st_, d_);
+  note_launches(1);
+  LevelInfo *h = (LevelInfo *)stage2(nj * sizeof(LevelInfo));
+  CK(cudaMemcpyAsync(h, di, nj * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  for (int i = 0; i < nj; ++i) {
+    lvs[i]->info = h[i];
+    lvs[i]->wide = needs_wide(*lvs[i], js[i]->p, js[i]->q, js[i]->ktot);
+  }
+}
+
+void Engine::init_levels(std::vector<Level *> &lvs) {
+  const int nj = (int)lvs.size();
+  if (nj == 0) return;
+  std::vector<LJob> tab(nj);
+  std::vector<int64_t> vs(nj + 1);
+  int64_t vt = 0;
+  for (int i = 0; i < nj; ++i) {
+    tab[i] = ljob_of(*lvs[i]);
+    vs[i] = vt;
+    vt += lvs[i]->n;
+  }
+  vs[nj] = vt;
+  LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+  upload_table(tab, vs, dt, dv, stage(nj * (sizeof(LJob) + 8) + 8), st_);
+  launch_init_level(dt, dv, nj, vt, st_, d_);
+  note_launches(1);
+  // the staging buffer is reused by the next upload: wait for the copies
+  CK(cudaStreamSynchronize(st_));
+}
+
+// ------------------------------------------------------------ add job ----
+
+void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *frontier_host,
+                     bool activate) {
+  const lcc_graph *g = j->g;
+  j->base = std::make_shared<Store>(st_);
+  Level L0;
+  L0.n = g->n;
+  L0.off = g->off;
+  L0.nbr = g->nbr;
+  L0.w = g->w;
+  L0.wtype = g->wtype;
+  const int64_t n = g->n;
+  int64_t *k = nullptr;
+  if (j->mode == LCC_NODEW_CUSTOM) {
+    if (!g->kc) throw Error(LCC_ERR_INVALID, "LCC_NODEW_CUSTOM needs node weights at load time");
+    k = g->kc;
+  } else {
+    k = j->base->alloc<int64_t>(n);
+    if (j->mode == LCC_NODEW_UNIT) {
+      launch_fill_k_unit(k, n, st_, d_);
+      note_launches(1);
+    } else if (j->mode == LCC_NODEW_DEGREE) {
+      LJob t = ljob_of(L0);
+      t.K = k;  // output of the degree kernel
+      std::vector<LJob> tab(1, t);
+      std::vector<int64_t> vs = {0, n};
+      LJob *dt = s_ljobs_.get<LJob>(1, st_);
+      int64_t *dv = s_vstart_.get<int64_t>(2, st_);
+      upload_table(tab, vs, dt, dv, stage(sizeof(LJob) + 16), st_);
+      launch_degree_k(dt, dv, 1, n, nullptr, st_, d_);
+      note_launches(1);
+    } else {
+      throw Error(LCC_ERR_INVALID, "unknown node-weight mode");
+    }
+  }
+  L0.k = k;
+  L0.L = j->base->alloc<int32_t>(n);
+  L0.K = j->base->alloc<int64_t>(n);
+  L0.D = j->base->alloc<int32_t>(n);
+  L0.fr = j->base->alloc<uint8_t>(n);
+  L0.cl = j->base->alloc<uint8_t>(n);
+  CK(cudaMemsetAsync(L0.fr, 0, n, st_));
+  CK(cudaMemsetAsync(L0.cl, 0, n, st_));
+  j->lv.clear();
+  j->lv.push_back(L0);
+  j->depth = 0;
+  // statistics of level 0 (also gives sum k for the modularity scaling)
+  {
+    std::vector<Job *> js = {j};
+    std::vector<Level *> lvs = {&j->lv[0]};
+    j->ktot = 0;
+    level_stats(js, lvs);
+    LevelInfo &I = j->lv[0].info;
+    if (I.pad > 0) throw Error(LCC_ERR_INVALID, "negative node weight (degree) in the input");
+    j->ktot = I.ksum;
+    if (j->mode == LCC_NODEW_DEGREE) {
+      if (I.ksum <= 0) throw Error(LCC_ERR_INVALID, "modularity mode needs a positive total weight");
+      const i128 qq = (i128)j->q * (i128)I.ksum;
+      if (qq > (i128)INT64_MAX) throw Error(LCC_ERR_OVERFLOW, "q * 2m exceeds int64");
+      j->q = (int64_t)qq;
+    }
+    if ((i128)I.ksum * (i128)I.ksum >= ((i128)1 << 126))
+      throw Error(LCC_ERR_OVERFLOW, "total node weight too large for exact arithmetic");
+    j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
+  }
+  Level &L = j->lv[0];
+  if (init_labels_host) {
+    CK(cudaMemcpyAsync(L.L, init_labels_host, n * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    LJob t = ljob_of(L);
+    std::vector<LJob> tab(1, t);
+    std::vector<int64_t> vs = {0, n};
+    LJob *dt = s_ljobs_.get<LJob>(1, st_);
+    int64_t *dv = s_vstart_.get<int64_t>(2, st_);
+    upload_table(tab, vs, dt, dv, stage(sizeof(LJob) + 16), st_);
+    launch_recompute_K(dt, dv, 1, n, st_, d_);
+    note_launches(2);
+    CK(cudaStreamSynchronize(st_));
+  } else {
+    std::vector<Level *> lvs = {&L};
+    init_levels(lvs);
+  }
+  if (frontier_host) {
+    CK(cudaMemcpyAsync(L.fr, frontier_host, n, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(L.D, L.L, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st_));
+  }
+  j->phase = P_BM;
+  j->round = 0;
+  j->moved_level = false;
+  if (activate) active_.push_back(j);
+}
+
+void Engine::drop_job(Job *j) {
+  active_.erase(std::remove(active_.begin(), active_.end(), j), active_.end());
+  j->lv.clear();
+  j->base.reset();
+}
+
+// -------------------------------------------------------------- rounds ----
+
+void Engine::end_bm(Job *j) {
+  if (j->kind == BM_ONLY || j->eval_only) {
+    j->phase = P_DONE;
+    return;
+  }
+  if (j->kind == BM_REFINE) {
+    j->phase = P_UP;
+    return;
+  }
+  // coarsening Best-Moves at this level finished
+  if (!j->moved_level || j->depth + 1 >= j->sc.max_levels)
+    j->phase = P_UP;
+  else
+    j->phase = P_CONTRACT;
+}
+
+void Engine::round(std::vector<Job *> &js) {
+  const int nj = (int)js.size();
+  std::vector<JobDev> tab(nj);
+  std::vector<int64_t> vs(nj + 1);
+  int64_t vt = 0, caps[NB] = {0}, hubcap = 0, hubs = 0, hub_su = 0;
+  bool wide = false, any_cl = false, any_mark = false, any_apply = false;
+  for (int i = 0; i < nj; ++i) {
+    Job *J = js[i];
+    Level &L = J->lv[J->depth];
+    JobDev &x = tab[i];
+    x.off = L.off;
+    x.nbr = L.nbr;
+    x.w = L.w;
+    x.k = L.k;
+    x.L = L.L;
+    x.K = L.K;
+    x.D = L.D;
+    x.fr = L.fr;
+    x.cl = L.cl;
+    x.n = L.n;
+    x.p = J->p;
+    x.q = J->q;
+    x.wtype = L.wtype;
+    int32_t f = 0;
+    if (J->eval_only) {
+      f |= JF_EVAL_ONLY;
+    } else {
+      if (J->round == 0 || J->sc.vset == LCC_VSET_ALL) f |= JF_ALL;
+      if (J->sc.vset == LCC_VSET_NBR_VERTICES) f |= JF_MARK_NBR;
+      if (J->sc.vset == LCC_VSET_NBR_CLUSTERS) f |= JF_MARK_CL;
+      any_apply = true;
+    }
+    x.flags = f;
+    any_cl |= (f & JF_MARK_CL) != 0;
+    any_mark |= (f & (JF_MARK_NBR | JF_MARK_CL)) != 0;
+    vs[i] = vt;
+    vt += L.n;
+    for (int b = 0; b < NB; ++b) caps[b] += L.info.bcnt[b];
+    hubcap += L.info.hub_cap;
+    hubs += L.info.bcnt[B_HUB];
+    hub_su += L.info.hub_sunits;
+    wide |= L.wide;
+  }
+  vs[nj] = vt;
+
+  Buckets b;
+  int64_t tot = 0;
+  for (int i = 0; i < NB; ++i) {
+    b.seg_start[i] = tot;
+    b.seg_cap[i] = caps[i];
+    tot += caps[i];
+  }
+  b.items = s_items_.get<uint64_t>(tot, st_);
+  b.cnt = s_cnt_.get<int64_t>(NB, st_);
+  int64_t *ctr = s_ctr_.get<int64_t>(NCTR, st_);
+  int64_t *jm = s_jmoves_.get<int64_t>(nj, st_);
+  uint64_t *moved = s_moved_.get<uint64_t>(vt, st_);
+  HubBufs h;
+  memset(&h, 0, sizeof(h));
+  if (hubs > 0) {
+    h.keys = s_hkeys_.get<int32_t>(hubcap, st_);
+    h.vals = s_hvals_.get<int64_t>(hubcap, st_);
+    h.cap_total = hubcap;
+    int64_t *meta = s_hmeta_.get<int64_t>(3 * (hubs + 1) + hubs, st_);
+    h.tbl_off = meta;
+    h.unit_off = meta + (hubs + 1);
+    h.sunit_off = meta + 2 * (hubs + 1);
+    h.stay = meta + 3 * (hubs + 1);
+    h.part_score = s_hpart_s_.get<i128>(hub_su, st_);
+    h.part_cid = s_hpart_c_.get<int32_t>(hub_su, st_);
+    h.iso_seen = s_hiso_.get<int32_t>(hubs, st_);
+    h.max_hubs = hubs;
+    h.max_sunits = hub_su;
+  }
+  JobDev *dt = s_jobs_.get<JobDev>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+  upload_table(tab, vs, dt, dv, stage(nj * (sizeof(JobDev) + 8) + 8), st_);
+  CK(cudaMemsetAsync(b.cnt, 0, NB * sizeof(int64_t), st_));
+  CK(cudaMemsetAsync(ctr, 0, NCTR * sizeof(int64_t), st_));
+  CK(cudaMemsetAsync(jm, 0, nj * sizeof(int64_t), st_));
+
+  int launches = 0;
+  if (timing) CK(cudaEventRecord(ev_[0], st_));
+  launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
+  ++launches;
+  if (timing) CK(cudaEventRecord(ev_[1], st_));
+  launch_bestmove(wide, dt, b, h, ctr, st_, d_, &launches);
+  if (timing) CK(cudaEventRecord(ev_[2], st_));
+  if (any_apply) {
+    launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);
+    ++launches;
+    if (any_mark) launch_mark(dt, moved, ctr, any_cl, dv, nj, vt, st_, d_, &launches);
+  }
+  if (timing) CK(cudaEventRecord(ev_[3], st_));
+  note_launches(launches);
+
+  int64_t *hbuf = (int64_t *)stage2((NCTR + nj) * sizeof(int64_t));
+  CK(cudaMemcpyAsync(hbuf, ctr, NCTR * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hbuf + NCTR, jm, nj * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  if (hbuf[C_ERR])
+    throw Error(LCC_ERR_CUDA, "best-move round overflowed a work buffer (code " +
+                                  std::to_string(hbuf[C_ERR]) + ")");
+  stats.edges += hbuf[C_EDGES];
+  stats.verts += hbuf[C_VERTS];
+  stats.cands += hbuf[C_CANDS];
+  stats.wbytes += hbuf[7];
+  stats.rounds += 1;
+  if (timing) {
+    stats.ms_bm += elapsed(ev_[1], ev_[2]);
+    stats.ms_round_other += elapsed(ev_[0], ev_[1]) + elapsed(ev_[2], ev_[3]);
+  }
+  for (int i = 0; i < nj; ++i) {
+    Job *J = js[i];
+    const int64_t mv = hbuf[NCTR + i];
+    J->round += 1;
+    J->rounds_total += 1;
+    if (J->eval_only) {
+      end_bm(J);
+      continue;
+    }
+    if (mv > 0) {
+      J->moved_level = true;
+      J->moved_any = true;
+    }
+    if (mv == 0 || J->round >= J->sc.num_iter) end_bm(J);
+  }
+}
+
+// ---------------------------------------------------------- contraction ----
+
+static int bits_for(int64_t x) {  // bits needed for values in [0, x)
+  int b = 0;
+  while (b < 63 && ((int64_t)1 << b) < x) ++b;
+  return b;
+}
+
+void Engine::contract(std::vector<Job *> &js) {
+  const int nj = (int)js.size();
+  if (timing) CK(cudaEventRecord(ev_[4], st_));
+  std::vector<CJob> tab(nj);
+  std::vector<int64_t> vs(nj + 1);
+  int64_t vt = 0;
+  for (int i = 0; i < nj; ++i) {
+    Level &L = js[i]->lv[js[i]->depth];
+    CJob &c = tab[i];
+    memset(&c, 0, sizeof(c));
+    c.off = L.off;
+    c.nbr = L.nbr;
+    c.w = L.w;
+    c.L = L.L;
+    c.K = L.K;
+    c.n = L.n;
+    c.wtype = L.wtype;
+    vs[i] = vt;
+    vt += L.n;
+  }
+  vs[nj] = vt;
+  auto store = std::make_shared<Store>(st_);
+  int32_t *map_u = store->alloc<int32_t>(vt);
+  for (int i = 0; i < nj; ++i) tab[i].map = map_u + vs[i];
+
+  Store tmp(st_);
+  CJob *dt = tmp.alloc<CJob>(nj);
+  int64_t *dv = tmp.alloc<int64_t>(nj + 1);
+  {
+    char *h = (char *)stage(nj * sizeof(CJob) + (nj + 1) * 8);
+    memcpy(h, tab.data(), nj * sizeof(CJob));
+    memcpy(h + nj * sizeof(CJob), vs.data(), (nj + 1) * 8);
+    CK(cudaMemcpyAsync(dt, h, nj * sizeof(CJob), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(dv, h + nj * sizeof(CJob), (nj + 1) * 8, cudaMemcpyHostToDevice, st_));
+  }
+  int64_t *rank = tmp.alloc<int64_t>(vt + 1);
+  int32_t *gmap = tmp.alloc<int32_t>(vt);
+  int64_t *pcnt = tmp.alloc<int64_t>(vt + 1);
+  int64_t *stmp = tmp.alloc<int64_t>(scan_tmp_elems(vt + 1));
+  int64_t *jc = tmp.alloc<int64_t>(2 * nj);
+  int32_t *err = tmp.alloc<int32_t>(1);
+  CK(cudaMemsetAsync(rank, 0, (vt + 1) * 8, st_));
+  CK(cudaMemsetAsync(pcnt + vt, 0, 8, st_));
+  CK(cudaMemsetAsync(err, 0, 4, st_));
+  launch_occ(dt, dv, nj, vt, rank, err, st_, d_);
+  scan_exclusive_i64(rank, vt, stmp, st_, d_);
+  launch_job_counts(dv, nj, rank, jc, st_);
+  launch_relabel(dt, dv, nj, vt, rank, gmap, st_, d_);
+  launch_emit_count(dt, dv, nj, vt, gmap, pcnt, st_, d_);
+  scan_exclusive_i64(pcnt, vt, stmp, st_, d_);
+  note_launches(12);
+  int64_t *hb = (int64_t *)stage2((3 + 2 * nj) * 8);
+  CK(cudaMemcpyAsync(hb, rank + vt, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hb + 1, pcnt + vt, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hb + 2, err, 4, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hb + 3, jc, 2 * nj * 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  if ((int32_t)hb[2]) throw Error(LCC_ERR_INVALID, "label out of range in Compress");
+  const int64_t ntot = hb[0];
+  const int64_t P = hb[1];
+  std::vector<int64_t> nprime(nj), cbase(nj);
+  int64_t nmax = 1;
+  for (int i = 0; i < nj; ++i) {
+    nprime[i] = hb[3 + 2 * i];
+    cbase[i] = hb[3 + 2 * i + 1];
+    nmax = std::max(nmax, nprime[i]);
+  }
+  if (ntot >= ((int64_t)1 << 31)) throw Error(LCC_ERR_OVERFLOW, "too many coarse vertices");
+  stats.pairs += P;
+
+  uint64_t *keys = tmp.alloc<uint64_t>(P);
+  int64_t *vals = tmp.alloc<int64_t>(P);
+  uint64_t *keys2 = tmp.alloc<uint64_t>(P);
+  int64_t *vals2 = tmp.alloc<int64_t>(P);
+  launch_emit_write(dt, dv, nj, vt, gmap, rank, pcnt, keys, vals, st_, d_);
+  int64_t *knew = store->alloc<int64_t>(ntot);
+  launch_knew(dt, dv, nj, vt, rank, knew, st_, d_);
+  note_launches(2);
+  int shifts[16], np = 0;
+  const int lb = bits_for(nmax), hbits = bits_for(ntot);
+  for (int s = 0; s < lb; s += 8) shifts[np++] = s;
+  for (int s = 32; s < 32 + hbits; s += 8) shifts[np++] = s;
+  int64_t *rtmp = tmp.alloc<int64_t>(radix_tmp_elems(P, np));
+  bool in_alt = false;
+  int lcount = 0;
+  radix_sort_pairs(keys, vals, keys2, vals2, P, shifts, np, rtmp, st_, d_, &in_alt, &lcount);
+  note_launches(lcount);
+  uint64_t *sk = in_alt ? keys2 : keys;
+  int64_t *sv = in_alt ? vals2 : vals;
+  int64_t *flags = tmp.alloc<int64_t>(P + 1);
+  CK(cudaMemsetAsync(flags + P, 0, 8, st_));
+  launch_seg_heads(sk, P, flags, st_, d_);
+  scan_exclusive_i64(flags, P, stmp = tmp.alloc<int64_t>(scan_tmp_elems(P + 1)), st_, d_);
+  note_launches(4);
+  CK(cudaMemcpyAsync(hb, flags + P, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  const int64_t U = hb[0];
+  uint64_t *ukeys = tmp.alloc<uint64_t>(U);
+  int64_t *uvals = store->alloc<int64_t>(U);
+  int32_t *unbr = store->alloc<int32_t>(U);
+  int64_t *offg = store->alloc<int64_t>(ntot + 1);
+  CK(cudaMemsetAsync(uvals, 0, (U > 0 ? U : 1) * 8, st_));
+  launch_seg_reduce(sk, sv, flags, P, ukeys, uvals, st_, d_);
+  launch_csr_rows(ukeys, U, ntot, offg, unbr, st_, d_);
+  note_launches(2);
+  int32_t *Lu = store->alloc<int32_t>(ntot);
+  int64_t *Ku = store->alloc<int64_t>(ntot);
+  int32_t *Du = store->alloc<int32_t>(ntot);
+  uint8_t *fru = store->alloc<uint8_t>(ntot);
+  uint8_t *clu = store->alloc<uint8_t>(ntot);
+  CK(cudaMemsetAsync(fru, 0, ntot > 0 ? ntot : 1, st_));
+  CK(cudaMemsetAsync(clu, 0, ntot > 0 ? ntot : 1, st_));
+
+  std::vector<Job *> grow;
+  std::vector<Level *> newlv;
+  for (int i = 0; i < nj; ++i) {
+    Job *J = js[i];
+    Level &Lf = J->lv[J->depth];
+    if (nprime[i] >= Lf.n && !J->keep_coarse) {  // no shrink: the recursion ends here
+      J->phase = P_UP;
+      continue;
+    }
+    Lf.map = map_u + vs[i];
+    Lf.map_store = store;
+    Level nl;
+    nl.n = nprime[i];
+    nl.off = offg + cbase[i];
+    nl.nbr = unbr;
+    nl.w = uvals;
+    nl.wtype = W_I64;
+    nl.k = knew + cbase[i];
+    nl.L = Lu + cbase[i];
+    nl.K = Ku + cbase[i];
+    nl.D = Du + cbase[i];
+    nl.fr = fru + cbase[i];
+    nl.cl = clu + cbase[i];
+    nl.store = store;
+    J->lv.push_back(nl);
+    J->depth += 1;
+    J->levels = std::max(J->levels, J->depth + 1);
+    J->phase = P_BM;
+    J->kind = BM_COARSEN;
+    J->round = 0;
+    J->moved_level = false;
+    grow.push_back(J);
+  }
+  for (Job *J : grow) newlv.push_back(&J->lv[J->depth]);
+  level_stats(grow, newlv);
+  init_levels(newlv);
+  if (timing) {
+    CK(cudaEventRecord(ev_[5], st_));
+    CK(cudaEventSynchronize(ev_[5]));
+    stats.ms_contract += elapsed(ev_[4], ev_[5]);
+  }
+  // temporaries are released (stream-ordered) when `tmp` goes out of scope
+}
+
+// ------------------------------------------------------------------ up ----
+
+void Engine::up(std::vector<Job *> &js) {
+  if (timing) CK(cudaEventRecord(ev_[6], st_));
+  std::vector<Job *> cur = js;
+  while (!cur.empty()) {
+    std::vector<Job *> fl;
+    for (Job *J : cur) {
+      if (J->depth == 0)
+        J->phase = P_FINAL;
+      else
+        fl.push_back(J);
+    }
+    if (fl.empty()) break;
+    const int nj = (int)fl.size();
+    std::vector<LJob> tab(nj);
+    std::vector<int64_t> vs(nj + 1);
+    int64_t vt = 0;
+    for (int i = 0; i < nj; ++i) {
+      Job *J = fl[i];
+      Level &Lf = J->lv[J->depth - 1];
+      Level &Lc = J->lv[J->depth];
+      tab[i] = ljob_of(Lf);
+      tab[i].map = Lf.map;
+      tab[i].Lcoarse = Lc.L;
+      vs[i] = vt;
+      vt += Lf.n;
+    }
+    vs[nj] = vt;
+    LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+    int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+    upload_table(tab, vs, dt, dv, stage(nj * (sizeof(LJob) + 8) + 8), st_);
+    launch_flatten(dt, dv, nj, vt, st_, d_);
+    note_launches(1);
+    std::vector<LJob> rtab;
+    std::vector<int64_t> rvs(1, 0);
+    std::vector<Job *> next;
+    for (int i = 0; i < nj; ++i) {
+      Job *J = fl[i];
+      J->lv.pop_back();  // stream-ordered release of the coarse level
+      J->depth -= 1;
+      Level &Lf = J->lv[J->depth];
+      Lf.map = nullptr;
+      Lf.map_store.reset();
+      if (J->sc.refine) {
+        rtab.push_back(ljob_of(Lf));
+        rvs.push_back(rvs.back() + Lf.n);
+        J->phase = P_BM;
+        J->kind = BM_REFINE;
+        J->round = 0;
+        J->moved_level = false;
+      } else {
+        next.push_back(J);
+      }
+    }
+    CK(cudaStreamSynchronize(st_));  // staging reuse
+    if (!rtab.empty()) {
+      const int nr = (int)rtab.size();
+      LJob *rt = s_ljobs_.get<LJob>(nr, st_);
+      int64_t *rv = s_vstart_.get<int64_t>(nr + 1, st_);
+      upload_table(rtab, rvs, rt, rv, stage(nr * (sizeof(LJob) + 8) + 8), st_);
+      launch_recompute_K(rt, rv, nr, rvs.back(), st_, d_);
+      note_launches(2);
+      CK(cudaStreamSynchronize(st_));
+    }
+    cur.swap(next);
+  }
+  if (timing) {
+    CK(cudaEventRecord(ev_[7], st_));
+    CK(cudaEventSynchronize(ev_[7]));
+    stats.ms_other += elapsed(ev_[6], ev_[7]);
+  }
+}
+
+// --------------------------------------------------------------- final ----
+
+void Engine::finalize(std::vector<Job *> &js) {
+  const int nj = (int)js.size();
+  if (nj == 0) return;
+  if (timing) CK(cudaEventRecord(ev_[6], st_));
+  std::vector<LJob> tab(nj);
+  std::vector<int64_t> vs(nj + 1);
+  int64_t vt = 0;
+  for (int i = 0; i < nj; ++i) {
+    tab[i] = ljob_of(js[i]->lv[0]);
+    vs[i] = vt;
+    vt += js[i]->lv[0].n;
+  }
+  vs[nj] = vt;
+  LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+  ObjAcc *acc = s_obj_.get<ObjAcc>(nj, st_);
+  upload_table(tab, vs, dt, dv, stage(nj * (sizeof(LJob) + 8) + 8), st_);
+  CK(cudaMemsetAsync(acc, 0, nj * sizeof(ObjAcc), st_));
+  launch_canonical(dt, dv, nj, vt, st_, d_);
+  launch_objective(dt, dv, nj, vt, acc, st_, d_);
+  note_launches(7);
+  ObjAcc *h = (ObjAcc *)stage2(nj * sizeof(ObjAcc));
+  CK(cudaMemcpyAsync(h, acc, nj * sizeof(ObjAcc), cudaMemcpyDeviceToHost, st_));
+  for (int i = 0; i < nj; ++i) {
+    Job *J = js[i];
+    if (J->labels_out) {
+      cudaMemcpyKind kind = J->labels_space == LCC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                              : cudaMemcpyDeviceToHost;
+      CK(cudaMemcpyAsync(J->labels_out, J->lv[0].L, J->lv[0].n * sizeof(int32_t), kind, st_));
+    }
+  }
+  CK(cudaStreamSynchronize(st_));
+  for (int i = 0; i < nj; ++i) {
+    Job *J = js[i];
+    const i128 s_in = (i128)(int64_t)h[i].s_in;
+    const u128 ksq = ((u128)h[i].ksq_hi << 64) | h[i].ksq_lo;
+    const u128 kself = ((u128)h[i].kself_hi << 64) | h[i].kself_lo;
+    J->num = (i128)J->q * s_in - (i128)J->p * (i128)(ksq - kself);
+    J->den = J->q;
+    J->nclusters = (int64_t)h[i].nclus;
+    J->phase = P_DONE;
+  }
+  if (timing) {
+    CK(cudaEventRecord(ev_[7], st_));
+    CK(cudaEventSynchronize(ev_[7]));
+    stats.ms_other += elapsed(ev_[6], ev_[7]);
+  }
+}
+
+void Engine::objective_of(Job *J) {
+  std::vector<Job *> js = {J};
+  std::vector<LJob> tab(1, ljob_of(J->lv[0]));
+  std::vector<int64_t> vs = {0, J->lv[0].n};
+  LJob *dt = s_ljobs_.get<LJob>(1, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(2, st_);
+  ObjAcc *acc = s_obj_.get<ObjAcc>(1, st_);
+  upload_table(tab, vs, dt, dv, stage(sizeof(LJob) + 16), st_);
+  CK(cudaMemsetAsync(acc, 0, sizeof(ObjAcc), st_));
+  launch_objective(dt, dv, 1, vs[1], acc, st_, d_);
+  note_launches(4);
+  ObjAcc *h = (ObjAcc *)stage2(sizeof(ObjAcc));
+  CK(cudaMemcpyAsync(h, acc, sizeof(ObjAcc), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  const i128 s_in = (i128)(int64_t)h->s_in;
+  const u128 ksq = ((u128)h->ksq_hi << 64) | h->ksq_lo;
+  const u128 kself = ((u128)h->kself_hi << 64) | h->kself_lo;
+  J->num = (i128)J->q * s_in - (i128)J->p * (i128)(ksq - kself);
+  J->den = J->q;
+}
+
+void Engine::compress_to_graph(Job *J, int32_t *map_host, lcc_graph **out) {
+  std::vector<Job *> js = {J};
+  J->sc.max_levels = 2;
+  contract(js);
+  if (J->depth != 1) throw Error(LCC_ERR_CUDA, "internal: Compress produced no level");
+  Level &Lf = J->lv[0];
+  Level &Lc = J->lv[1];
+  const int64_t n2 = Lc.n;
+  int64_t first = 0, last = 0;
+  CK(cudaMemcpyAsync(&first, Lc.off, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(&last, Lc.off + n2, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  const int64_t nnz2 = last - first;
+  lcc_graph *g = new lcc_graph();
+  g->dev = dev_;
+  g->st = st_;
+  g->n = n2;
+  g->nnz = nnz2;
+  g->store = std::make_shared<Store>(st_);
+  g->off = g->store->alloc<int64_t>(n2 + 1);
+  g->nbr = g->store->alloc<int32_t>(nnz2);
+  int64_t *w = g->store->alloc<int64_t>(nnz2);
+  g->w = w;
+  g->wtype = W_I64;
+  g->kc = g->store->alloc<int64_t>(n2);
+  CK(cudaMemcpyAsync(g->off, Lc.off, (n2 + 1) * 8, cudaMemcpyDeviceToDevice, st_));
+  if (nnz2 > 0) {
+    CK(cudaMemcpyAsync(g->nbr, Lc.nbr + first, nnz2 * 4, cudaMemcpyDeviceToDevice, st_));
+    CK(cudaMemcpyAsync(w, (const int64_t *)Lc.w + first, nnz2 * 8, cudaMemcpyDeviceToDevice, st_));
+  }
+  CK(cudaMemcpyAsync(g->kc, Lc.k, n2 * 8, cudaMemcpyDeviceToDevice, st_));
+  if (map_host) CK(cudaMemcpyAsync(map_host, Lf.map, Lf.n * 4, cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  if (first != 0) {
+    // offsets of a single-job level start at 0; keep the invariant explicit
+    throw Error(LCC_ERR_CUDA, "internal: coarse offsets do not start at 0");
+  }
+  // |w| total of the coarse graph never exceeds the input's
+  g->wabs = J->g->wabs;
+  *out = g;
+}
+
+// ---------------------------------------------------------------- tick ----
+
+std::vector<Job *> Engine::tick() {
+  std::vector<Job *> bm;
+  for (Job *J : active_)
+    if (J->phase == P_BM) bm.push_back(J);
+  if (!bm.empty()) {
+    // jobs that would run zero rounds end their Best-Moves at once
+    std::vector<Job *> run;
+    for (Job *J : bm) {
+      if (J->sc.num_iter <= 0 && !J->eval_only)
+        end_bm(J);
+      else
+        run.push_back(J);
+    }
+    if (!run.empty()) round(run);
+  }
+  std::vector<Job *> ct;
+  for (Job *J : active_)
+    if (J->phase == P_CONTRACT) ct.push_back(J);
+  if (!ct.empty()) contract(ct);
+  std::vector<Job *> u;
+  for (Job *J : active_)
+    if (J->phase == P_UP) u.push_back(J);
+  if (!u.empty()) up(u);
+  std::vector<Job *> fin;
+  for (Job *J : active_)
+    if (J->phase == P_FINAL) fin.push_back(J);
+  if (!fin.empty()) finalize(fin);
+  std::vector<Job *> done;
+  for (Job *J : active_)
+    if (J->phase == P_DONE) done.push_back(J);
+  for (Job *J : done)
+    active_.erase(std::remove(active_.begin(), active_.end(), J), active_.end());
+  return done;
+}
+
+// ------------------------------------------------------- shared engines ----
+
+static std::mutex g_eng_mu;
+struct EngSlot {
+  std::unique_ptr<Engine> eng;
+  std::unique_ptr<std::mutex> mu;
+};
+static std::unordered_map<uint64_t, EngSlot> g_engines;
+
+Engine *engine_for(int dev, cudaStream_t st, std::unique_lock<std::mutex> &lock) {
+  std::mutex *m;
+  Engine *e;
+  {
+    std::lock_guard<std::mutex> lk(g_eng_mu);
+    const uint64_t key = ((uint64_t)dev << 56) ^ (uint64_t)(uintptr_t)st;
+    EngSlot &s = g_engines[key];
+    if (!s.eng) {
+      s.eng.reset(new Engine(dev, st));
+      s.mu.reset(new std::mutex());
+    }
+    m = s.mu.get();
+    e = s.eng.get();
+  }
+  lock = std::unique_lock<std::mutex>(*m);
+  return e;
+}
+
+}  // namespace lcc

@@ -1,0 +1,464 @@
+// Compress (Sec. 3.1, Appendix B) as relabel -> emit -> radix sort ->
+// segmented reduce -> CSR, over a table of jobs laid out in one flat vertex
+// space (vstart[j] = first flat index of job j).
+//
+//   occ/rank   occupied cluster ids, exclusive scan -> dense coarse ids in
+//              increasing cluster-id order; rank[vstart_j + c] is the global
+//              coarse id of cluster c of job j;
+//   emit       every entry (u, v) whose ends lie in different clusters gives
+//              key = (global coarse id of u) << 32 | (local coarse id of v)
+//              and value w; entries inside a cluster are dropped;
+//   sort       LSD radix sort, 8-bit digits, only on the bits in use;
+//   reduce     equal keys are summed (parallel edges merged);
+//   CSR        row r starts at the first unique key >= r << 32.
+#include "lcc_internal.cuh"
+
+namespace lcc {
+
+namespace {
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+int grid_for(int64_t work, int threads, const Dev &d, int per_sm = 8) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t mx = (int64_t)d.sms * per_sm;
+  if (g > mx) g = mx;
+  return (int)(g > 0 ? g : 1);
+}
+}  // namespace
+
+// --------------------------------------------------------- occupancy ------
+
+__global__ void k_occ(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                      int njobs, int64_t vtot, int64_t *occ, int32_t *err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const CJob *J = jobs + j;
+    const int32_t c = J->L[i - vstart[j]];
+    if (c < 0 || c >= J->n) {
+      *err = 1;
+      continue;
+    }
+    occ[vstart[j] + c] = 1;
+  }
+}
+
+void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot, int64_t *occ,
+                int32_t *err, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_occ<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, occ, err);
+}
+
+__global__ void k_relabel(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                          int njobs, int64_t vtot, const int64_t *__restrict__ rank,
+                          int32_t *gmap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const CJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t g = rank[vstart[j] + J->L[v]];
+    gmap[i] = (int32_t)g;
+    J->map[v] = (int32_t)(g - rank[vstart[j]]);
+  }
+}
+
+void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                    const int64_t *rank, int32_t *gmap, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_relabel<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, rank, gmap);
+}
+
+// k' = K: the coarse vertex of occupied cluster c gets node weight K_c.
+__global__ void k_knew(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                       int njobs, int64_t vtot, const int64_t *__restrict__ rank, int64_t *knew) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (rank[i + 1] == rank[i]) continue;
+    const int j = find_job(vstart, njobs, i);
+    knew[rank[i]] = jobs[j].K[i - vstart[j]];
+  }
+}
+
+void launch_knew(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                 const int64_t *rank, int64_t *knew, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_knew<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, rank, knew);
+}
+
+__global__ void k_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += gridDim.x * blockDim.x) {
+    out[2 * j] = rank[vstart[j + 1]] - rank[vstart[j]];  // n'_j
+    out[2 * j + 1] = rank[vstart[j]];                     // first global coarse id
+  }
+}
+
+void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out,
+                       cudaStream_t st) {
+  if (njobs <= 0) return;
+  k_job_counts<<<(njobs + 255) / 256, 256, 0, st>>>(vstart, njobs, rank, out);
+}
+
+// ------------------------------------------------------------- emission --
+
+__global__ void __launch_bounds__(256) k_emit_count(const CJob *__restrict__ jobs,
+                                                    const int64_t *__restrict__ vstart, int njobs,
+                                                    int64_t vtot, const int32_t *__restrict__ gmap,
+                                                    int64_t *pcnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
+       i += warps_total) {
+    const int j = find_job(vstart, njobs, i);
+    const CJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t vs = vstart[j];
+    const int32_t cu = gmap[i];
+    int cnt = 0;
+    for (int64_t e = J->off[v] + lane; e < J->off[v + 1]; e += 32)
+      cnt += gmap[vs + __ldg(J->nbr + e)] != cu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+    if (lane == 0) pcnt[i] = cnt;
+  }
+}
+
+void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       const int32_t *gmap, int64_t *pcnt, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_emit_count<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap, pcnt);
+}
+
+__global__ void __launch_bounds__(256) k_emit_write(const CJob *__restrict__ jobs,
+                                                    const int64_t *__restrict__ vstart, int njobs,
+                                                    int64_t vtot, const int32_t *__restrict__ gmap,
+                                                    const int64_t *__restrict__ rank,
+                                                    const int64_t *__restrict__ ppos,
+                                                    uint64_t *keys, int64_t *vals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
+       i += warps_total) {
+    const int j = find_job(vstart, njobs, i);
+    const CJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t vs = vstart[j];
+    const int64_t cbase = rank[vs];
+    const uint64_t cu = (uint64_t)(uint32_t)gmap[i];
+    int64_t pos = ppos[i];
+    const int64_t beg = J->off[v], end = J->off[v + 1];
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      bool out = false;
+      int32_t cv = 0;
+      if (e < end) {
+        cv = gmap[vs + __ldg(J->nbr + e)];
+        out = (uint32_t)cv != (uint32_t)cu;
+      }
+      const unsigned m = __ballot_sync(FULL, out);
+      if (out) {
+        const int64_t p = pos + __popc(m & lanemask_lt());
+        keys[p] = (cu << 32) | (uint64_t)(uint32_t)(cv - cbase);
+        vals[p] = load_w(J->w, J->wtype, e);
+      }
+      pos += __popc(m);
+    }
+  }
+}
+
+void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       const int32_t *gmap, const int64_t *rank, const int64_t *ppos,
+                       uint64_t *keys, int64_t *vals, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_emit_write<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap, rank,
+                                                            ppos, keys, vals);
+}
+
+// ----------------------------------------------------------------- scan --
+
+constexpr int SCAN_T = 256, SCAN_I = 16, SCAN_TILE = SCAN_T * SCAN_I;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t *total) {
+  __shared__ int64_t wsum[SCAN_T / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  int64_t wprefix = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_T / 32; ++k) {
+    const int64_t s = wsum[k];
+    if (k < w) wprefix += s;
+    tot += s;
+  }
+  __syncthreads();
+  *total = tot;
+  return wprefix + inc - x;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int64_t *a, int64_t n, int64_t *sums) {
+  __shared__ int64_t red[SCAN_T / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
+    const int64_t idx = base + i;
+    if (idx < n) s += a[idx];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int k = 0; k < SCAN_T / 32; ++k) t += red[k];
+    sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(int64_t *a, int64_t n,
+                                                       const int64_t *tile_off) {
+  __shared__ int64_t s[SCAN_TILE];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
+    const int64_t idx = base + i;
+    s[i] = idx < n ? a[idx] : 0;
+  }
+  __syncthreads();
+  int64_t loc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k) loc += s[threadIdx.x * SCAN_I + k];
+  int64_t tot;
+  int64_t run = block_excl_scan(loc, &tot) + (tile_off ? tile_off[blockIdx.x] : 0);
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k) {
+    const int64_t t = s[threadIdx.x * SCAN_I + k];
+    s[threadIdx.x * SCAN_I + k] = run;
+    run += t;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
+    const int64_t idx = base + i;
+    if (idx < n) a[idx] = s[i];
+  }
+}
+
+int64_t scan_tmp_elems(int64_t n) {
+  int64_t tot = 0;
+  int64_t m = n + 1;
+  while (true) {
+    const int64_t tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles <= 1) break;
+    tot += tiles + 1;
+    m = tiles + 1;
+  }
+  return tot + 1;
+}
+
+static void scan_rec(int64_t *a, int64_t m, int64_t *tmp, cudaStream_t st) {
+  const int64_t tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles <= 1) {
+    k_scan_apply<<<1, SCAN_T, 0, st>>>(a, m, nullptr);
+    return;
+  }
+  k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(a, m, tmp);
+  cudaMemsetAsync(tmp + tiles, 0, sizeof(int64_t), st);
+  scan_rec(tmp, tiles + 1, tmp + tiles + 1, st);
+  k_scan_apply<<<(unsigned)tiles, SCAN_T, 0, st>>>(a, m, tmp);
+}
+
+void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, const Dev &) {
+  // a has n + 1 elements; the caller zeroes a[n] so that it receives the total
+  scan_rec(a, n + 1, tmp, st);
+}
+
+// ----------------------------------------------------------- radix sort --
+
+constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *keys, int64_t n, int shift,
+                                                  int64_t ntiles, int64_t *ghist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_T) {
+    const int64_t idx = base + i;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  ghist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: elements are ranked in index order within the tile (16
+// rounds of 256 consecutive elements; within a round, warp order then lane
+// order) and placed after everything of smaller digit or earlier tile.
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ keys,
+                                                     const int64_t *__restrict__ vals, int64_t n,
+                                                     int shift, int64_t ntiles,
+                                                     const int64_t *__restrict__ goff,
+                                                     uint64_t *keys_out, int64_t *vals_out) {
+  __shared__ int64_t base_off[256];
+  __shared__ int run[256];
+  __shared__ int wcnt[RS_W][256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  base_off[tid] = goff[(int64_t)tid * ntiles + blockIdx.x];
+  run[tid] = 0;
+  for (int k = 0; k < RS_W; ++k) wcnt[k][tid] = 0;
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_I; ++r) {
+    const int64_t idx = tile0 + (int64_t)r * RS_T + tid;
+    const bool has = idx < n;
+    uint64_t key = 0;
+    int64_t val = 0;
+    int dg = 256 + lane;  // unique dummy digit for lanes past the end
+    if (has) {
+      key = keys[idx];
+      val = vals[idx];
+      dg = (int)((key >> shift) & 255u);
+    }
+    const unsigned peers = __match_any_sync(FULL, dg);
+    const bool leader = lane == __ffs(peers) - 1;
+    const int rk = __popc(peers & lanemask_lt());
+    if (has && leader) wcnt[w][dg] = __popc(peers);
+    __syncthreads();
+    if (has) {
+      int pre = 0;
+      for (int k = 0; k < w; ++k) pre += wcnt[k][dg];
+      const int64_t pos = base_off[dg] + run[dg] + pre + rk;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    if (has && leader) {
+      atomicAdd(&run[dg], __popc(peers));
+      wcnt[w][dg] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+int64_t radix_tmp_elems(int64_t n, int npasses) {
+  const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t m = 256 * ntiles;
+  return m + 1 + scan_tmp_elems(m);
+}
+
+void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,
+                      int64_t n, const int *shifts, int npasses, int64_t *tmp, cudaStream_t st,
+                      const Dev &d, bool *result_in_alt, int *launches) {
+  *result_in_alt = false;
+  if (n <= 1 || npasses == 0) return;
+  const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t m = 256 * ntiles;
+  int64_t *ghist = tmp;
+  int64_t *stmp = tmp + m + 1;
+  uint64_t *ki = keys, *ko = keys_alt;
+  int64_t *vi = vals, *vo = vals_alt;
+  for (int p = 0; p < npasses; ++p) {
+    k_rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, n, shifts[p], ntiles, ghist);
+    cudaMemsetAsync(ghist + m, 0, sizeof(int64_t), st);
+    scan_exclusive_i64(ghist, m, stmp, st, d);
+    k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, vi, n, shifts[p], ntiles, ghist, ko, vo);
+    *launches += 3;
+    uint64_t *tk = ki; ki = ko; ko = tk;
+    int64_t *tv = vi; vi = vo; vo = tv;
+  }
+  *result_in_alt = (npasses & 1) != 0;
+}
+
+// --------------------------------------------------- segmented reduce ----
+
+__global__ void k_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+void launch_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags, cudaStream_t st,
+                      const Dev &d) {
+  if (n <= 0) return;
+  k_seg_heads<<<grid_for(n, 256, d), 256, 0, st>>>(keys, n, flags);
+}
+
+// idx = exclusive scan of the head flags.  Each thread sums a chunk of 8
+// consecutive entries; a run that lies wholly inside the chunk is written
+// directly, runs crossing a chunk border are added atomically (uvals must be
+// zeroed beforehand).
+constexpr int SEG_C = 8;
+__global__ void k_seg_reduce(const uint64_t *__restrict__ keys, const int64_t *__restrict__ vals,
+                             const int64_t *__restrict__ idx, int64_t n, uint64_t *ukeys,
+                             int64_t *uvals) {
+  const int64_t nchunks = (n + SEG_C - 1) / SEG_C;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = c * SEG_C;
+    int64_t hi = lo + SEG_C;
+    if (hi > n) hi = n;
+    bool started_here = (lo == 0) || keys[lo] != keys[lo - 1];
+    int64_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i) {
+      const bool head = (i == 0) || keys[i] != keys[i - 1];
+      if (head && i > lo) {
+        const int64_t u = idx[i] - 1;  // the run ending at i - 1
+        if (started_here)
+          uvals[u] = sum;
+        else
+          atomic_add_i64(uvals + u, sum);
+        sum = 0;
+        started_here = true;
+      }
+      if (head) ukeys[idx[i]] = keys[i];
+      sum += vals[i];
+    }
+    const int64_t i = hi - 1;
+    const int64_t u = idx[i] + ((i == 0 || keys[i] != keys[i - 1]) ? 1 : 0) - 1;
+    const bool ends_here = (hi == n) || keys[hi] != keys[hi - 1];
+    if (started_here && ends_here)
+      uvals[u] = sum;
+    else
+      atomic_add_i64(uvals + u, sum);
+  }
+}
+
+void launch_seg_reduce(const uint64_t *keys, const int64_t *vals, const int64_t *idx, int64_t n,
+                       uint64_t *ukeys, int64_t *uvals, cudaStream_t st, const Dev &d) {
+  if (n <= 0) return;
+  const int64_t nchunks = (n + SEG_C - 1) / SEG_C;
+  k_seg_reduce<<<grid_for(nchunks, 256, d), 256, 0, st>>>(keys, vals, idx, n, ukeys, uvals);
+}
+
+__global__ void k_csr_rows(const uint64_t *__restrict__ ukeys, int64_t nu, int64_t nrows,
+                           int64_t *offg, int32_t *nbr_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows; r += stride) {
+    const uint64_t target = (uint64_t)r << 32;
+    int64_t lo = 0, hi = nu;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ukeys[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    offg[r] = lo;
+  }
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += stride)
+    nbr_out[u] = (int32_t)(uint32_t)(ukeys[u] & 0xffffffffull);
+}
+
+void launch_csr_rows(const uint64_t *ukeys, int64_t nu, int64_t nrows, int64_t *offg,
+                     int32_t *nbr_out, cudaStream_t st, const Dev &d) {
+  const int64_t work = (nu > nrows + 1) ? nu : nrows + 1;
+  k_csr_rows<<<grid_for(work, 256, d), 256, 0, st>>>(ukeys, nu, nrows, offg, nbr_out);
+}
+
+}  // namespace lcc

@@ -1,0 +1,388 @@
+// Per-level kernels: level statistics, initial singletons, node weights,
+// Flatten (Sec. 3.1 / Appendix B), canonical labels, the exact objective
+// (Sec. 2) and input validation.  All of them run over a table of jobs in a
+// flat vertex index space (vstart[j] is job j's first flat index).
+#include "lcc_internal.cuh"
+
+namespace lcc {
+
+namespace {
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ long long wsum_ll(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
+int grid_for(int64_t work, int threads, const Dev &d, int per_sm = 8) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t mx = (int64_t)d.sms * per_sm;
+  if (g > mx) g = mx;
+  return (int)(g > 0 ? g : 1);
+}
+}  // namespace
+
+// ------------------------------------------------------- level statistics --
+
+// One warp per vertex: degree bucket, hub table sizes, row sum of |w|, node
+// weight range.  Lane 0 keeps running totals for the job it is on and
+// flushes them with atomics when the job changes.
+__global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jobs,
+                                                     const int64_t *__restrict__ vstart,
+                                                     int njobs, int64_t vtot, LevelInfo *info) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int cur = -1;
+  int64_t bc[NB];
+  int64_t hcap = 0, hun = 0, hsu = 0, rmax = 0, kmax = 0, ksum = 0, wabs = 0, kneg = 0;
+  for (int i = 0; i < NB; ++i) bc[i] = 0;
+  auto flush = [&]() {
+    if (cur < 0) return;
+    LevelInfo *I = info + cur;
+    for (int i = 0; i < NB; ++i)
+      if (bc[i]) atomicAdd((unsigned long long *)&I->bcnt[i], (unsigned long long)bc[i]);
+    if (hcap) atomicAdd((unsigned long long *)&I->hub_cap, (unsigned long long)hcap);
+    if (hun) atomicAdd((unsigned long long *)&I->hub_units, (unsigned long long)hun);
+    if (hsu) atomicAdd((unsigned long long *)&I->hub_sunits, (unsigned long long)hsu);
+    atomicMax((unsigned long long *)&I->rmax, (unsigned long long)rmax);
+    atomicMax((unsigned long long *)&I->kmax, (unsigned long long)kmax);
+    if (ksum) atomicAdd((unsigned long long *)&I->ksum, (unsigned long long)ksum);
+    if (wabs) atomicAdd((unsigned long long *)&I->wabs, (unsigned long long)wabs);
+    if (kneg) atomicAdd((unsigned long long *)&I->pad, (unsigned long long)kneg);
+    for (int i = 0; i < NB; ++i) bc[i] = 0;
+    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = 0;
+  };
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
+       i += warps_total) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t beg = J->off[v], end = J->off[v + 1];
+    long long ra = 0;
+    if (J->wtype == W_NONE) {
+      ra = end - beg;
+    } else {
+      for (int64_t e = beg + lane; e < end; e += 32) {
+        const long long x = load_w(J->w, J->wtype, e);
+        ra += x < 0 ? -x : x;
+      }
+      ra = wsum_ll(ra);
+    }
+    if (lane == 0) {
+      if (j != cur) {
+        flush();
+        cur = j;
+      }
+      const int64_t deg = end - beg;
+      const int b = bucket_of(deg);
+      bc[b] += 1;
+      if (b == B_HUB) {
+        const int64_t cap = hub_cap(deg);
+        hcap += cap;
+        hun += (deg + HUB_CHUNK - 1) / HUB_CHUNK;
+        hsu += (cap + HUB_SCHUNK - 1) / HUB_SCHUNK;
+      }
+      if (ra > rmax) rmax = ra;
+      wabs += ra;
+      const int64_t kv = J->k[v];
+      if (kv < 0) kneg += 1;
+      else if (kv > kmax) kmax = kv;
+      ksum += kv;
+    }
+  }
+  if (lane == 0) flush();
+}
+
+void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                        LevelInfo *info, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_level_stats<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, info);
+}
+
+// ------------------------------------------------------- per-vertex maps --
+
+__global__ void k_init_level(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                             int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    J->L[v] = (int32_t)v;
+    J->K[v] = J->k[v];
+  }
+}
+
+void launch_init_level(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_init_level<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot);
+}
+
+// Modularity node weights (Sec. 2): k_v = sum_u w_uv, one warp per vertex.
+// Written through LJob::K (the job's node-weight array for this purpose).
+__global__ void __launch_bounds__(256) k_degree_k(const LJob *__restrict__ jobs,
+                                                  const int64_t *__restrict__ vstart, int njobs,
+                                                  int64_t vtot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
+       i += warps_total) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    long long s = 0;
+    for (int64_t e = J->off[v] + lane; e < J->off[v + 1]; e += 32) s += load_w(J->w, J->wtype, e);
+    s = wsum_ll(s);
+    if (lane == 0) J->K[v] = s;
+  }
+}
+
+void launch_degree_k(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot, int64_t *,
+                     cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_degree_k<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot);
+}
+
+__global__ void k_fill_one(int64_t *k, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    k[i] = 1;
+}
+
+void launch_fill_k_unit(int64_t *k, int64_t n, cudaStream_t st, const Dev &d) {
+  if (n <= 0) return;
+  k_fill_one<<<grid_for(n, 256, d), 256, 0, st>>>(k, n);
+}
+
+__global__ void k_zero_K(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                         int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    jobs[j].K[i - vstart[j]] = 0;
+  }
+}
+
+// K_c = sum of k_v over the vertices labelled c (exact integer atomics).
+__global__ void k_add_K(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                        int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t kv = J->k[v];
+    if (kv) atomic_add_i64(J->K + J->L[v], kv);
+  }
+}
+
+void launch_recompute_K(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                        cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_zero_K<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot);
+  k_add_K<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot);
+}
+
+// Flatten: v takes the cluster of its coarse vertex, L[v] = L'[map[v]].
+__global__ void k_flatten(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                          int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    J->L[v] = J->Lcoarse[J->map[v]];
+  }
+}
+
+void launch_flatten(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                    cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_flatten<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot);
+}
+
+// Canonical labels: the smallest vertex id of each cluster (D is scratch).
+__global__ void k_canon_init(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                             int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    jobs[j].D[i - vstart[j]] = INT32_MAX;
+  }
+}
+__global__ void k_canon_min(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                            int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    atomicMin(J->D + J->L[v], (int32_t)v);
+  }
+}
+__global__ void k_canon_set(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                            int njobs, int64_t vtot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    J->L[v] = J->D[J->L[v]];
+  }
+}
+
+void launch_canonical(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                      cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  const int g = grid_for(vtot, 256, d);
+  k_canon_init<<<g, 256, 0, st>>>(jobs, vstart, njobs, vtot);
+  k_canon_min<<<g, 256, 0, st>>>(jobs, vstart, njobs, vtot);
+  k_canon_set<<<g, 256, 0, st>>>(jobs, vstart, njobs, vtot);
+}
+
+// ------------------------------------------------------------ objective --
+
+// q * CC = q * S_in - p * (sum_C K_C^2 - sum_v k_v^2)   (Sec. 2, ordered
+// pairs), with S_in the sum of w over entries whose ends share a label.
+// This kernel accumulates S_in (one warp per vertex).
+__global__ void __launch_bounds__(256) k_obj_edges(const LJob *__restrict__ jobs,
+                                                   const int64_t *__restrict__ vstart, int njobs,
+                                                   int64_t vtot, ObjAcc *acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int cur = -1;
+  long long run = 0;
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
+       i += warps_total) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int32_t lv = J->L[v];
+    long long s = 0;
+    for (int64_t e = J->off[v] + lane; e < J->off[v + 1]; e += 32)
+      if (J->L[J->nbr[e]] == lv) s += load_w(J->w, J->wtype, e);
+    s = wsum_ll(s);
+    if (lane == 0) {
+      if (j != cur) {
+        if (cur >= 0 && run) atomicAdd(&acc[cur].s_in, (unsigned long long)run);
+        cur = j;
+        run = 0;
+      }
+      run += s;
+    }
+  }
+  if (lane == 0 && cur >= 0 && run) atomicAdd(&acc[cur].s_in, (unsigned long long)run);
+}
+
+// sum_C K_C^2 and sum_v k_v^2 (128-bit, one thread per cluster id / vertex).
+__global__ void __launch_bounds__(256) k_obj_squares(const LJob *__restrict__ jobs,
+                                                     const int64_t *__restrict__ vstart,
+                                                     int njobs, int64_t vtot, ObjAcc *acc) {
+  int cur = -1;
+  u128 a = 0, b = 0;
+  unsigned long long reps = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const LJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    if (j != cur) {
+      if (cur >= 0) {
+        atomic_add_u128(&acc[cur].ksq_lo, &acc[cur].ksq_hi, a);
+        atomic_add_u128(&acc[cur].kself_lo, &acc[cur].kself_hi, b);
+        if (reps) atomicAdd(&acc[cur].nclus, reps);
+      }
+      cur = j;
+      a = b = 0;
+      reps = 0;
+    }
+    reps += (J->L[v] == (int32_t)v);
+    const u128 K = (u128)(uint64_t)J->K[v];
+    const u128 k = (u128)(uint64_t)J->k[v];
+    a += K * K;
+    b += k * k;
+  }
+  if (cur >= 0) {
+    atomic_add_u128(&acc[cur].ksq_lo, &acc[cur].ksq_hi, a);
+    atomic_add_u128(&acc[cur].kself_lo, &acc[cur].kself_hi, b);
+    if (reps) atomicAdd(&acc[cur].nclus, reps);
+  }
+}
+
+void launch_objective(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                      ObjAcc *acc, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  launch_recompute_K(jobs, vstart, njobs, vtot, st, d);
+  k_obj_edges<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, acc);
+  k_obj_squares<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, acc);
+}
+
+// ------------------------------------------------------------ validation --
+
+// out[0] error bits (1 offsets, 2 range, 4 self loop), out[1..4] two pairs
+// of order-independent hash sums over (u, v, w) and (v, u, w): equal sums
+// for a symmetric multiset; out[5..6] sum of |w| as 128 bits.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+__global__ void k_validate_off(const int64_t *off, int64_t n, int64_t nnz,
+                               unsigned long long *out) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (off[v] > off[v + 1] || off[v] < 0 || off[v + 1] > nnz) atomicOr(out, 1ull);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_validate_rows(const int64_t *off, const int32_t *nbr,
+                                                       const int32_t *w, int64_t n,
+                                                       unsigned long long *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long h1 = 0, h2 = 0, h3 = 0, h4 = 0, bits = 0;
+  u128 wabs = 0;
+  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n;
+       u += warps_total) {
+    for (int64_t e = off[u] + lane; e < off[u + 1]; e += 32) {
+      const int32_t v = nbr[e];
+      if (v < 0 || v >= n) { bits |= 2; continue; }
+      if (v == u) bits |= 4;
+      const long long wt = w ? (long long)w[e] : 1;
+      wabs += (u128)(unsigned long long)(wt < 0 ? -wt : wt);
+      const unsigned long long uw = (unsigned long long)wt;
+      const unsigned long long a = ((unsigned long long)u << 32) | (unsigned long long)(uint32_t)v;
+      const unsigned long long b = ((unsigned long long)(uint32_t)v << 32) | (unsigned long long)u;
+      h1 += mix64(a ^ mix64(uw));
+      h2 += mix64(b ^ mix64(uw));
+      h3 += mix64(mix64(a + 0x9e3779b97f4a7c15ull) + uw);
+      h4 += mix64(mix64(b + 0x9e3779b97f4a7c15ull) + uw);
+    }
+  }
+  if (bits) atomicOr(out, bits);
+  atomicAdd(out + 1, h1);
+  atomicAdd(out + 2, h2);
+  atomicAdd(out + 3, h3);
+  atomicAdd(out + 4, h4);
+  atomic_add_u128(out + 5, out + 6, wabs);
+}
+
+void launch_validate(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
+                     int64_t nnz, unsigned long long *out8, cudaStream_t st, const Dev &d) {
+  if (n <= 0) return;
+  k_validate_off<<<grid_for(n, 256, d), 256, 0, st>>>(off, n, nnz, out8);
+}
+
+void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
+                          unsigned long long *out8, cudaStream_t st, const Dev &d) {
+  if (n <= 0) return;
+  k_validate_rows<<<grid_for(n * 32, 256, d), 256, 0, st>>>(off, nbr, w, n, out8);
+}
+
+}  // namespace lcc

@@ -1,0 +1,316 @@
+// Internal declarations shared by the CUDA translation units of liblcc.
+//
+// Data layout in HBM (one "job" = one graph being clustered; a launch covers
+// the current level of every job in a table):
+//   CSR level : off int64[n+1] (absolute indices into nbr/w), nbr int32[nnz],
+//               w int32[nnz] (input level, optional) or int64[nnz] (coarse
+//               levels, merged weights), k int64[n] node weights;
+//   state     : L int32[n] labels, K int64[n] cluster weights (indexed by
+//               cluster id), D int32[n] desired clusters, fr uint8[n] next
+//               frontier flags, cl uint8[n] "a vertex left this cluster";
+//   work lists: uint64 items (job << 32 | vertex), one segment per degree
+//               bucket.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lcc {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+enum WType : int32_t { W_NONE = 0, W_I32 = 1, W_I64 = 2 };
+
+// Job flags for a round.
+enum : int32_t {
+  JF_ALL = 1,       // evaluate every vertex this round (V' = V)
+  JF_MARK_NBR = 2,  // next V' = neighbours of moved vertices
+  JF_MARK_CL = 4,   // next V' = neighbours of clusters that lost a vertex
+  JF_EVAL_ONLY = 8  // compute D only (no apply)
+};
+
+// Degree buckets of the best-move kernels.
+enum Bucket : int {
+  B_G4 = 0,   // deg <= 4: 4 lanes per vertex
+  B_G8 = 1,   // deg <= 8
+  B_G16 = 2,  // deg <= 16
+  B_G32 = 3,  // deg <= 32: one warp, register aggregation
+  B_WARP = 4, // deg <= T_WARP: one warp, shared-memory hash table
+  B_BLK1 = 5, // deg <= T_BLK1: one block, shared-memory hash table
+  B_BLK2 = 6, // deg <= T_BLK2: one block, larger shared-memory table
+  B_HUB = 7,  // larger: global-memory hash table, many blocks per vertex
+  NB = 8
+};
+constexpr int T_WARP = 256;
+constexpr int T_BLK1 = 1024;
+constexpr int T_BLK2 = 4096;
+constexpr int WARP_CAP = 512;    // slots per warp table (>= 2 * T_WARP)
+constexpr int BLK1_CAP = 2048;   // >= 2 * T_BLK1
+constexpr int BLK2_CAP = 8192;   // >= 2 * T_BLK2
+constexpr int HUB_CHUNK = 4096;  // edges per insertion unit
+constexpr int HUB_SCHUNK = 4096; // table slots per scoring unit
+
+__host__ __device__ inline int bucket_of(int64_t deg) {
+  if (deg <= 4) return B_G4;
+  if (deg <= 8) return B_G8;
+  if (deg <= 16) return B_G16;
+  if (deg <= 32) return B_G32;
+  if (deg <= T_WARP) return B_WARP;
+  if (deg <= T_BLK1) return B_BLK1;
+  if (deg <= T_BLK2) return B_BLK2;
+  return B_HUB;
+}
+
+__host__ __device__ inline int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Global-table capacity of a hub row: a power of two >= 2 * deg.
+__host__ __device__ inline int64_t hub_cap(int64_t deg) { return next_pow2(2 * deg); }
+
+// Current level of one job, as seen by the round kernels.
+struct JobDev {
+  const int64_t *off;
+  const int32_t *nbr;
+  const void *w;
+  const int64_t *k;
+  int32_t *L;
+  int64_t *K;
+  int32_t *D;
+  uint8_t *fr;
+  uint8_t *cl;
+  int64_t n;
+  int64_t p, q;
+  int32_t wtype;
+  int32_t flags;
+};
+
+// Device counters of a round (int64 each).
+enum Ctr : int {
+  C_EDGES = 0,    // sum of deg over evaluated vertices
+  C_VERTS = 1,    // evaluated vertices
+  C_CANDS = 2,    // distinct candidate clusters scored
+  C_MOVES = 3,    // vertices moved
+  C_ERR = 4,      // error bits (see Err)
+  C_MOVED_N = 5,  // entries in the moved list
+  C_HUBS = 6,     // hubs handled this round
+  C_WB = 7,       // sum of deg * (bytes per stored weight) over evaluated vertices
+  NCTR = 8
+};
+enum Err : int64_t {
+  E_BUCKET_OVERFLOW = 1,
+  E_HUB_OVERFLOW = 2,
+  E_MOVED_OVERFLOW = 4,
+  E_PAIR_OVERFLOW = 8,
+  E_BAD_LABEL = 16
+};
+
+struct Buckets {
+  uint64_t *items;
+  int64_t seg_start[NB];
+  int64_t seg_cap[NB];
+  int64_t *cnt;  // [NB] device counters
+};
+
+struct HubBufs {
+  int32_t *keys;
+  int64_t *vals;
+  int64_t cap_total;  // slots available in keys/vals
+  int64_t *tbl_off;   // [max_hubs + 1]
+  int64_t *unit_off;  // [max_hubs + 1]
+  int64_t *sunit_off; // [max_hubs + 1]
+  i128 *part_score;   // [max_sunits]
+  int32_t *part_cid;  // [max_sunits]
+  int64_t *stay;      // [max_hubs]
+  int32_t *iso_seen;  // [max_hubs]
+  int64_t max_hubs;
+  int64_t max_sunits;
+};
+
+// Contraction view of one job's level.
+struct CJob {
+  const int64_t *off;
+  const int32_t *nbr;
+  const void *w;
+  const int32_t *L;
+  const int64_t *K;
+  int32_t *map;  // out: coarse vertex of each vertex (local id)
+  int64_t n;
+  int32_t wtype;
+  int32_t pad;
+};
+
+// Level view for flatten / final / statistics kernels.
+struct LJob {
+  const int64_t *off;
+  const int32_t *nbr;
+  const void *w;
+  const int64_t *k;
+  int32_t *L;
+  int64_t *K;
+  int32_t *D;
+  const int32_t *map;     // flatten: coarse vertex of each vertex
+  const int32_t *Lcoarse; // flatten: labels of the coarse level
+  int64_t n;
+  int32_t wtype;
+  int32_t pad;
+};
+
+// Per-job results of the level statistics kernel.
+struct LevelInfo {
+  int64_t bcnt[NB];     // vertices per degree bucket
+  int64_t hub_cap;      // sum of hub table capacities
+  int64_t hub_units;    // insertion units over hubs
+  int64_t hub_sunits;   // scoring units over hubs
+  int64_t rmax;         // max over rows of sum |w|
+  int64_t kmax;         // max node weight
+  int64_t ksum;         // sum of node weights
+  int64_t wabs;         // sum of |w| over entries
+  int64_t pad;
+};
+
+// Per-job accumulators of the objective kernels.
+struct ObjAcc {
+  unsigned long long s_in;     // sum of w over same-cluster entries (two's complement)
+  unsigned long long ksq_lo, ksq_hi;   // sum_C K_C^2 (128-bit)
+  unsigned long long kself_lo, kself_hi; // sum_v k_v^2 (128-bit)
+  unsigned long long nclus;    // vertices that are their cluster's label (canonical)
+  unsigned long long pad[2];
+};
+
+__device__ __forceinline__ int64_t load_w(const void *w, int32_t wtype, int64_t e) {
+  if (wtype == W_I32) return (int64_t)__ldg(((const int32_t *)w) + e);
+  if (wtype == W_I64) return __ldg(((const int64_t *)w) + e);
+  return 1;
+}
+
+// Largest j with vstart[j] <= i (vstart ascending, vstart[0] = 0).
+__device__ __forceinline__ int find_job(const int64_t *__restrict__ vstart, int njobs, int64_t i) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(vstart + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t c) { return c * 2654435769u; }
+
+__device__ __forceinline__ void atomic_add_i64(int64_t *a, int64_t v) {
+  atomicAdd((unsigned long long *)a, (unsigned long long)v);
+}
+
+// 128-bit accumulation from two 64-bit atomics: the carry of each low-word
+// addition is decided by the value that addition saw, so the total is exact.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *lo, unsigned long long *hi, u128 v) {
+  unsigned long long vl = (unsigned long long)v;
+  unsigned long long vh = (unsigned long long)(v >> 64);
+  unsigned long long old = atomicAdd(lo, vl);
+  unsigned long long carry = (old + vl < old) ? 1ull : 0ull;
+  if (vh + carry) atomicAdd(hi, vh + carry);
+}
+
+template <typename S> struct ScoreOps;
+template <> struct ScoreOps<int64_t> {
+  __device__ static __forceinline__ int64_t lowest() { return INT64_MIN; }
+  __device__ static __forceinline__ int64_t shfl_xor(int64_t x, int o, int width) {
+    return __shfl_xor_sync(0xffffffffu, (long long)x, o, width);
+  }
+  __device__ static __forceinline__ int64_t shfl(int64_t x, int src, int width) {
+    return __shfl_sync(0xffffffffu, (long long)x, src, width);
+  }
+};
+template <> struct ScoreOps<i128> {
+  __device__ static __forceinline__ i128 lowest() { return (i128)((u128)1 << 127); }
+  __device__ static __forceinline__ i128 shfl_xor(i128 x, int o, int width) {
+    long long lo = (long long)(uint64_t)x, hi = (long long)(x >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, o, width);
+    hi = __shfl_xor_sync(0xffffffffu, hi, o, width);
+    return ((i128)hi << 64) | (i128)(uint64_t)lo;
+  }
+  __device__ static __forceinline__ i128 shfl(i128 x, int src, int width) {
+    long long lo = (long long)(uint64_t)x, hi = (long long)(x >> 64);
+    lo = __shfl_sync(0xffffffffu, lo, src, width);
+    hi = __shfl_sync(0xffffffffu, hi, src, width);
+    return ((i128)hi << 64) | (i128)(uint64_t)lo;
+  }
+};
+
+// (score, cluster) pair order: higher score first, then smaller cluster id.
+template <typename S>
+__device__ __forceinline__ bool better(S s1, int32_t c1, S s2, int32_t c2) {
+  return s1 > s2 || (s1 == s2 && c1 < c2);
+}
+
+// ---- host-side launch helpers (defined in the .cu files) ----
+struct Dev {
+  int sms;
+  int dev;
+};
+
+// Round kernels (k_round.cu).
+void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                     const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
+void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
+                     int64_t *ctr, cudaStream_t st, const Dev &d, int *launches);
+void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
+                  int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
+void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, bool any_cl,
+                 const int64_t *vstart, int njobs, int64_t vtot, cudaStream_t st, const Dev &d,
+                 int *launches);
+
+// Level kernels (k_level.cu).
+void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                        LevelInfo *info, cudaStream_t st, const Dev &d);
+void launch_init_level(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       cudaStream_t st, const Dev &d);
+void launch_degree_k(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                     int64_t *k_out_flat_unused, cudaStream_t st, const Dev &d);
+void launch_fill_k_unit(int64_t *k, int64_t n, cudaStream_t st, const Dev &d);
+void launch_recompute_K(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                        cudaStream_t st, const Dev &d);
+void launch_flatten(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                    cudaStream_t st, const Dev &d);
+void launch_canonical(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                      cudaStream_t st, const Dev &d);
+void launch_objective(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                      ObjAcc *acc, cudaStream_t st, const Dev &d);
+void launch_validate(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
+                     int64_t nnz, unsigned long long *out8, cudaStream_t st, const Dev &d);
+void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
+                          unsigned long long *out8, cudaStream_t st, const Dev &d);
+
+// Contraction kernels (k_contract.cu).
+void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot, int64_t *occ,
+                int32_t *err, cudaStream_t st, const Dev &d);
+void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                    const int64_t *rank, int32_t *gmap, cudaStream_t st, const Dev &d);
+void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       const int32_t *gmap, int64_t *pcnt, cudaStream_t st, const Dev &d);
+void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                       const int32_t *gmap, const int64_t *rank, const int64_t *ppos,
+                       uint64_t *keys, int64_t *vals, cudaStream_t st, const Dev &d);
+void launch_knew(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
+                 const int64_t *rank, int64_t *knew, cudaStream_t st, const Dev &d);
+void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out,
+                       cudaStream_t st);
+// Exclusive scan of int64 in place over [0, n]; a[n] receives the total.
+// tmp must hold scan_tmp_elems(n) int64.
+int64_t scan_tmp_elems(int64_t n);
+void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, const Dev &d);
+// LSD radix sort of (key, val) pairs on the given 8-bit digit positions.
+int64_t radix_tmp_elems(int64_t n, int npasses);
+void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,
+                      int64_t n, const int *shifts, int npasses, int64_t *tmp,
+                      cudaStream_t st, const Dev &d, bool *result_in_alt, int *launches);
+void launch_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags, cudaStream_t st,
+                      const Dev &d);
+void launch_seg_reduce(const uint64_t *keys, const int64_t *vals, const int64_t *idx, int64_t n,
+                       uint64_t *ukeys, int64_t *uvals, cudaStream_t st, const Dev &d);
+void launch_csr_rows(const uint64_t *ukeys, int64_t nu, int64_t nrows, int64_t *offg,
+                     int32_t *nbr_out, cudaStream_t st, const Dev &d);
+
+}  // namespace lcc

@@ -316,3 +316,23 @@ def random_signed_graph(n, p_edge, w_lo, w_hi, seed, device="cpu"):
     w = torch.randint(w_lo, w_hi + 1, (a.numel(),), generator=gen,
                       device=device).to(torch.int32)
     return pairs_to_csr(a.to(torch.int64), b.to(torch.int64), n, w=w)
+
+
+def hub_graph(n, mean_deg, hubs, hub_deg, seed, device="cpu", w_lo=None, w_hi=None):
+    """Sparse random graph plus `hubs` vertices joined to hub_deg random others
+    each, so that every degree bucket (including rows above a few thousand
+    entries) is populated.  Optional integer weights uniform in [w_lo, w_hi]."""
+    gen = _gen(seed, device)
+    m = int(n * mean_deg // 2)
+    u = torch.randint(0, n, (m,), generator=gen, device=device)
+    v = torch.randint(0, n, (m,), generator=gen, device=device)
+    hu = torch.arange(hubs, device=device).repeat_interleave(hub_deg)
+    hv = torch.randint(0, n, (hubs * hub_deg,), generator=gen, device=device)
+    a, b = canonical_unique(torch.cat([u, hu]), torch.cat([v, hv]), n)
+    a, b, _ = permute_ids(a, b, n, gen)
+    a2, b2 = torch.minimum(a, b), torch.maximum(a, b)
+    w = None
+    if w_lo is not None:
+        w = torch.randint(w_lo, w_hi + 1, (a2.numel(),), generator=gen,
+                          device=device).to(torch.int32)
+    return pairs_to_csr(a2, b2, n, w=w)

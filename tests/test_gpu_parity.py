@@ -1,0 +1,341 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Labels, desired clusters, coarse graphs and exact objectives are compared
+element by element (bit-exact: every quantity is an integer).  Graph sizes
+span several work tiles of every degree bucket, including rows above the
+shared-memory limit (global-table hubs), with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_01731_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2108_01731_gb300 import lcc
+    lcc.load()
+    return lcc
+
+
+def graphs():
+    return {
+        "sbm": I.to_numpy(I.sbm([60] * 30, 0.2, 0.01, seed=1)),
+        "hubs": I.to_numpy(I.hub_graph(20000, 5, 3, 7000, seed=2)),
+        "hubs_w": I.to_numpy(I.hub_graph(12000, 7, 2, 9000, seed=3, w_lo=-5, w_hi=9)),
+        "cl": I.to_numpy(I.chung_lu(30000, 2.1, 12, seed=4)),
+        "rmat": I.to_numpy(I.rmat(14, 120000, seed=5)),
+        "signed": I.to_numpy(I.random_signed_graph(300, 0.1, -4, 6, seed=6)),
+    }
+
+
+GRAPHS = graphs()
+
+
+def node_weights(g, mode, seed):
+    if mode == O.NODEW_CUSTOM:
+        return np.random.default_rng(seed).integers(0, 7, g["n"]).astype(np.int64)
+    if mode == O.NODEW_UNIT:
+        return np.ones(g["n"], np.int64)
+    w = g["w"] if g["w"] is not None else np.ones(g["nnz"], np.int64)
+    k = np.zeros(g["n"], np.int64)
+    np.add.at(k, np.repeat(np.arange(g["n"]), np.diff(g["off"])), w.astype(np.int64))
+    return k
+
+
+def lam(mode, g, p, q):
+    """(p, q) as the library takes them -> (p, q_eff) as the oracle's
+    per-level functions take them (modularity: q * 2m)."""
+    if mode == O.NODEW_DEGREE:
+        return p, q * int(node_weights(g, mode, 0).sum())
+    return p, q
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("mode", [O.NODEW_UNIT, O.NODEW_DEGREE, O.NODEW_CUSTOM])
+def test_desired_matches_oracle(L, name, mode):
+    g = GRAPHS[name]
+    if mode == O.NODEW_DEGREE and g["w"] is not None and g["w"].min() < 0:
+        pytest.skip("modularity needs non-negative degrees")
+    n = g["n"]
+    k = node_weights(g, mode, 11)
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k if mode == O.NODEW_CUSTOM else None)
+    rng = np.random.default_rng(7)
+    for trial, (p, q) in enumerate([(1, 50), (3, 7), (1 << 50, 7)]):
+        if trial == 0:
+            Lb = np.arange(n, dtype=np.int32)
+        else:
+            Lb = I.random_labels(n, max(2, n // (30 * trial)), seed=100 + trial).numpy()
+        fr = (rng.random(n) < 0.7).astype(np.uint8) if trial == 1 else None
+        got = L.lcc_desired(G, p, q, mode, Lb, fr)
+        K = np.zeros(n, np.int64)
+        np.add.at(K, Lb, k)
+        pe, qe = lam(mode, g, p, q)
+        want = O.desired(g["off"], g["nbr"], g["w"], k, pe, qe, Lb, K)
+        if fr is not None:
+            want = np.where(fr.astype(bool), want, Lb)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (name, mode, trial, bad[:10], got[bad[:10]], want[bad[:10]])
+    G.free()
+
+
+@pytest.mark.parametrize("vset", [O.VSET_ALL, O.VSET_NBR_VERTICES, O.VSET_NBR_CLUSTERS])
+@pytest.mark.parametrize("name", ["sbm", "hubs", "rmat"])
+def test_best_moves_rounds_match_oracle(L, name, vset):
+    g = GRAPHS[name]
+    n = g["n"]
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    k = np.ones(n, np.int64)
+    L0 = np.arange(n, dtype=np.int32)
+    for r in (1, 2, 3, 6):
+        got, moved, rounds = L.lcc_best_moves(G, 1, 40, O.NODEW_UNIT, r, vset, L0)
+        want, wmoved, wrounds = O.best_moves(g["off"], g["nbr"], g["w"], k, 1, 40, L0, r,
+                                            vset=vset)
+        assert rounds == wrounds and moved == wmoved
+        assert np.array_equal(got, want), (name, vset, r)
+    G.free()
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_compress_matches_oracle(L, name):
+    g = GRAPHS[name]
+    n = g["n"]
+    k = node_weights(g, O.NODEW_CUSTOM, 3)
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+    for nc in (max(2, n // 50), max(2, n // 3)):
+        Lb = I.random_labels(n, nc, seed=nc).numpy()
+        mp, C = L.lcc_compress(G, O.NODEW_CUSTOM, Lb)
+        off2, nbr2, w2, k2 = L.lcc_graph_export(C)
+        wmp, woff, wnbr, ww, wk = O.compress(g["off"], g["nbr"], g["w"], k, Lb)
+        assert np.array_equal(mp, wmp)
+        assert np.array_equal(off2, woff)
+        assert np.array_equal(nbr2, wnbr)
+        assert np.array_equal(w2, ww)
+        assert np.array_equal(k2, wk)
+        C.free()
+    G.free()
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_objective_matches_oracle(L, name):
+    g = GRAPHS[name]
+    n = g["n"]
+    k = node_weights(g, O.NODEW_CUSTOM, 5)
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+    for nc in (1, 7, n // 10, n):
+        Lb = (np.arange(n, dtype=np.int32) if nc == n
+              else I.random_labels(n, nc, seed=nc + 1).numpy())
+        num, den = L.lcc_objective(G, 3, 11, O.NODEW_CUSTOM, Lb)
+        assert den == 11
+        assert num == O.objective_num(g["off"], g["nbr"], g["w"], k, 3, 11, Lb)
+    G.free()
+
+
+CLUSTER_CASES = [
+    ("sbm", O.NODEW_UNIT, 1, 50, {}),
+    ("sbm", O.NODEW_UNIT, 1, 50, {"refine": False}),
+    ("sbm", O.NODEW_UNIT, 1, 50, {"vset": O.VSET_ALL, "num_iter": 5}),
+    ("hubs", O.NODEW_DEGREE, 1, 1, {}),
+    ("hubs_w", O.NODEW_UNIT, 1, 8, {}),
+    ("hubs_w", O.NODEW_CUSTOM, 2, 9, {"vset": O.VSET_NBR_CLUSTERS}),
+    ("cl", O.NODEW_DEGREE, 1, 1, {}),
+    ("cl", O.NODEW_UNIT, 1, 100, {"max_levels": 2}),
+    ("rmat", O.NODEW_DEGREE, 1, 1, {}),
+    ("rmat", O.NODEW_DEGREE, 1 << 40, 3, {}),
+    ("signed", O.NODEW_UNIT, 1, 10, {"num_iter": 20}),
+]
+
+
+@pytest.mark.parametrize("case", CLUSTER_CASES, ids=lambda c: "%s-%d-%d/%d-%s" % (
+    c[0], c[1], c[2], c[3], "-".join("%s%s" % kv for kv in sorted(c[4].items()))))
+def test_cluster_matches_oracle(L, case):
+    name, mode, p, q, kw = case
+    g = GRAPHS[name]
+    k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+    sched = L.schedule(num_iter=kw.get("num_iter", 10), max_levels=kw.get("max_levels", 64),
+                       refine=kw.get("refine", True), vset=kw.get("vset", 1))
+    labels, obj, st = L.lcc_cluster(G, p, q, mode, sched)
+    wl, num, den, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k,
+                                  num_iter=kw.get("num_iter", 10),
+                                  max_levels=kw.get("max_levels", 64),
+                                  refine=kw.get("refine", True), vset=kw.get("vset", 1))
+    assert np.array_equal(labels, wl)
+    assert st["obj_num"] == num and st["obj_den"] == den
+    assert abs(obj - num / den) <= 1e-12 * max(1.0, abs(num / den))
+    assert st["levels"] == wst[0] and st["rounds_total"] == wst[1]
+    assert st["edges_scanned"] == wst[2]
+    assert st["num_clusters"] == len(np.unique(wl))
+    G.free()
+
+
+def test_config1_planted_partition_full_size(L):
+    """SBM, 10,000 vertices in 100 blocks, p_in 0.05, p_out 0.0005, lambda
+    1/100, 20 rounds per Best-Moves, contraction and refinement."""
+    g = I.to_numpy(I.sbm([100] * 100, 0.05, 0.0005, seed=I.BASE_SEED + 1))
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    labels, obj, st = L.lcc_cluster(G, 1, 100, O.NODEW_UNIT, L.schedule(num_iter=20))
+    wl, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, 100, num_iter=20)
+    assert np.array_equal(labels, wl) and st["obj_num"] == num
+    G.free()
+
+
+def test_device_labels_and_device_csr(L):
+    import torch
+    g = GRAPHS["hubs"]
+    dev = {k: torch.from_numpy(g[k]).cuda() for k in ("off", "nbr")}
+    G = L.lcc_load_csr(dev["off"], dev["nbr"])
+    out = torch.empty(g["n"], dtype=torch.int32, device="cuda")
+    L.lcc_cluster(G, 1, 1, O.NODEW_DEGREE, None, labels_out=out)
+    wl, *_ = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE)
+    assert np.array_equal(out.cpu().numpy(), wl)
+    G.free()
+
+
+# ------------------------------------------------------------ edge cases --
+
+def csr(n, edges):
+    import torch
+    if not edges:
+        return {"off": np.zeros(n + 1, np.int64), "nbr": np.zeros(0, np.int32), "w": None,
+                "n": n, "nnz": 0}
+    a = torch.tensor([min(e) for e in edges])
+    b = torch.tensor([max(e) for e in edges])
+    return I.to_numpy(I.pairs_to_csr(a, b, n))
+
+
+@pytest.mark.parametrize("n,edges", [
+    (0, []), (1, []), (5, []), (2, [(0, 1)]), (3, [(0, 1), (1, 2)]),
+    (7, [(0, 1), (1, 2), (0, 2), (4, 5)]),
+])
+def test_degenerate_graphs(L, n, edges):
+    g = csr(n, edges)
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    for p, q, mode in [(1, 3, O.NODEW_UNIT), (1, 1, O.NODEW_DEGREE)]:
+        if mode == O.NODEW_DEGREE and not edges:
+            with pytest.raises(L.LccError):
+                L.lcc_cluster(G, p, q, mode)
+            continue
+        labels, obj, st = L.lcc_cluster(G, p, q, mode)
+        if n == 0:
+            assert len(labels) == 0
+            continue
+        wl, num, den, _ = O.cluster(g["off"], g["nbr"], None, p, q, mode=mode)
+        assert np.array_equal(labels, wl) and st["obj_num"] == num
+    G.free()
+
+
+def test_isolated_edge_oscillation_and_cliques_closed_form(L):
+    g = csr(2, [(0, 1)])
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    labels, obj, st = L.lcc_cluster(G, 1, 3, O.NODEW_UNIT, L.schedule(num_iter=7))
+    assert list(labels) == [0, 1] and st["obj_num"] == 0 and st["rounds_total"] == 7
+    G.free()
+    r, s, p, q = 40, 6, 1, 3
+    perm = np.random.default_rng(0).permutation(r * s)
+    edges = [(perm[c * s + i], perm[c * s + j]) for c in range(r) for i in range(s)
+             for j in range(i + 1, s)]
+    g = csr(r * s, edges)
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    labels, obj, st = L.lcc_cluster(G, p, q, O.NODEW_UNIT)
+    for c in range(r):
+        mem = sorted(perm[c * s:(c + 1) * s])
+        assert all(labels[v] == mem[0] for v in mem)
+    assert st["obj_num"] == r * s * (s - 1) * (q - p)
+    G.free()
+
+
+def test_input_validation(L):
+    g = csr(4, [(0, 1), (1, 2), (2, 3)])
+    off, nbr = g["off"], g["nbr"]
+    bad = nbr.copy()
+    bad[0] = 7
+    with pytest.raises(L.LccError) as e:
+        L.lcc_load_csr(off, bad)
+    assert e.value.status == L.LCC_ERR_INVALID
+    bad = nbr.copy()
+    bad[0] = 0  # vertex 0 -> 0
+    with pytest.raises(L.LccError) as e:
+        L.lcc_load_csr(off, bad)
+    assert e.value.status in (L.LCC_ERR_SELF_LOOP, L.LCC_ERR_NOT_SYMMETRIC)
+    w = np.ones(len(nbr), np.int32)
+    w[0] = 2
+    with pytest.raises(L.LccError) as e:
+        L.lcc_load_csr(off, nbr, w)
+    assert e.value.status == L.LCC_ERR_NOT_SYMMETRIC
+    off2 = off.copy()
+    off2[2] = off2[3] + 1
+    with pytest.raises(L.LccError) as e:
+        L.lcc_load_csr(off2, nbr)
+    assert e.value.status == L.LCC_ERR_INVALID
+    G = L.lcc_load_csr(off, nbr)
+    with pytest.raises(L.LccError):
+        L.lcc_cluster(G, 0, 1)
+    with pytest.raises(L.LccError):
+        L.lcc_desired(G, 1, 2, 0, np.array([0, 1, 2, 9], np.int32))
+    G.free()
+
+
+# --------------------------------------------------- batching and serving --
+
+def test_batch_equals_single(L):
+    names = ["sbm", "hubs", "cl", "rmat", "signed", "hubs_w"]
+    modes = [O.NODEW_UNIT, O.NODEW_DEGREE, O.NODEW_DEGREE, O.NODEW_DEGREE, O.NODEW_UNIT,
+             O.NODEW_UNIT]
+    ps = [1, 1, 1, 1, 1, 1]
+    qs = [50, 1, 1, 1, 10, 8]
+    Gs = [L.lcc_load_csr(GRAPHS[n]["off"], GRAPHS[n]["nbr"], GRAPHS[n]["w"]) for n in names]
+    outs, objs = L.lcc_cluster_batch(Gs, ps, qs, modes)
+    for i, G in enumerate(Gs):
+        lab, obj, _ = L.lcc_cluster(G, ps[i], qs[i], modes[i])
+        assert np.array_equal(outs[i], lab), names[i]
+        assert objs[i] == obj
+    for G in Gs:
+        G.free()
+
+
+def test_server_results_match_single_runs(L):
+    import time
+    graphs = [I.to_numpy(I.serving_graph(i)) for i in range(12)]
+    srv = L.Server(hbm_budget_bytes=8 << 30, max_slots=5)
+    tickets = []
+    for i, g in enumerate(graphs):
+        tickets.append(srv.submit(g["off"], g["nbr"], None, 1, 1, O.NODEW_DEGREE))
+        if i % 3 == 2:
+            time.sleep(0.01)  # later jobs arrive while earlier ones run
+    srv.wait_idle(600000)
+    for t, g in zip(tickets, graphs):
+        res = srv.poll(t)
+        assert res is not None
+        labels, obj, lat = res
+        wl, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE)
+        assert np.array_equal(labels, wl)
+        assert abs(obj - num / den) <= 1e-12 * max(1.0, abs(num / den))
+        assert lat > 0
+    c = srv.counters()
+    assert c["done"] == len(graphs) and c["peak_jobs"] <= 5
+    srv.close()
+
+
+def test_server_rejects_oversize_and_cancels(L):
+    g = GRAPHS["sbm"]
+    srv = L.Server(hbm_budget_bytes=1 << 20, max_slots=2)
+    with pytest.raises(L.LccError) as e:
+        srv.submit(g["off"], g["nbr"], None, 1, 50, O.NODEW_UNIT)
+    assert e.value.status == L.LCC_ERR_OOM
+    srv.close()
+    srv = L.Server(hbm_budget_bytes=4 << 30, max_slots=1)
+    t1 = srv.submit(g["off"], g["nbr"], None, 1, 50, O.NODEW_UNIT)
+    t2 = srv.submit(g["off"], g["nbr"], None, 1, 50, O.NODEW_UNIT)
+    srv.cancel(t2)
+    srv.wait_idle(600000)
+    assert srv.poll(t1) is not None
+    with pytest.raises(L.LccError) as e:
+        srv.poll(t2)
+    assert e.value.status == L.LCC_ERR_CANCELLED
+    srv.close()

@@ -1,0 +1,508 @@
+#!/usr/bin/env python3
+"""Benchmark of the LambdaCC best-move / contraction path on GB300.
+
+Workload (default): R-MAT graph, 2^26 vertices, exactly 2^30 undirected edges
+stored in both directions (2^31 CSR entries, int32 ids and int32 weights,
+int64 offsets), modularity mode (k = degree, lambda = 1/2m), full multi-level
+Parallel-CC (Algorithm 1, synchronous, 10 rounds per Best-Moves, refinement
+on).  One step = one whole lcc_cluster call on the resident graph: every
+best-move round, every contraction, flatten/refine, canonical labels and the
+exact objective.
+
+Metric: best-move GEdges/s = directed CSR entries scanned by the best-move
+rounds of a step (the sum of deg(v) over every evaluated vertex) / step time.
+`roofline` reports the best-move kernels' algorithmic bytes / their device
+time against the measured HBM copy bandwidth.  `e2e` times the same call with
+the CSR in pinned host memory (load + validate + cluster + labels to host).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torchrun, one replica of the workload per GPU (the
+path has no exchange step), value = sum of edges over ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: generator, node-weight mode, lambda p/q, rounds per Best-Moves
+    "rmat26": dict(kind="rmat", scale=26, m=1 << 30, mode=1, p=1, q=1, num_iter=10,
+                   desc="R-MAT a=0.57 b=c=0.19 d=0.05, 2^26 vertices, 2^30 undirected edges "
+                        "(2^31 CSR entries), int32 weights, modularity (gamma=1)"),
+    "chunglu20": dict(kind="chunglu", n=1 << 20, beta=2.1, deg=32, mode=1, p=1, q=1,
+                      num_iter=10, desc="Chung-Lu beta=2.1, 2^20 vertices, ~16M edges, "
+                                        "modularity (gamma=1)"),
+    "rmat22": dict(kind="rmat", scale=22, m=1 << 26, mode=1, p=1, q=1, num_iter=10,
+                   desc="R-MAT a=0.57 b=c=0.19 d=0.05, 2^22 vertices, 2^26 undirected edges, "
+                        "modularity (gamma=1)"),
+    "sbm1e4": dict(kind="sbm", mode=0, p=1, q=100, num_iter=20,
+                   desc="planted partition, 100 blocks of 100, p_in 0.05, p_out 0.0005, "
+                        "lambda 1/100, 20 rounds"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat26")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--serving", type=int, default=160,
+                    help="graphs of the serving stream to run (0 = skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------- distributed --
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_scalar(x, world, op, device):
+    """max/sum of a float over ranks (identity at world 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- inputs --
+
+def make_graph(wl, device):
+    from paper_2108_01731_gb300 import inputs as I
+    seed = I.BASE_SEED
+    if wl["kind"] == "rmat":
+        return I.rmat(wl["scale"], wl["m"], seed=seed + 4, device=device)
+    if wl["kind"] == "chunglu":
+        return I.chung_lu(wl["n"], wl["beta"], wl["deg"], seed=seed + 2, device=device)
+    if wl["kind"] == "sbm":
+        return I.sbm([100] * 100, 0.05, 0.0005, seed=seed + 1, device=device)
+    raise ValueError(wl["kind"])
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """Per-edge DRAM traffic of the best-move kernels from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "bestmove_rmat.md")
+    src = os.path.join(ROOT, "paper_2108_01731_gb300", "csrc", "k_round.cu")
+    if not os.path.exists(path):
+        return None
+    want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("k_round.cu sha256[:16]") != want:
+        return None
+    try:
+        return float(vals["dram bytes per edge scanned"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------- clocks --
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_sample(host, wl, seconds):
+    """Times the CPU oracle on the first best-move round of the same graph for
+    a window of vertices [0, X) sized to take about `seconds`.  Returns
+    (GEdges/s, description)."""
+    import numpy as np
+    import oracle as O
+    off = host["off"]
+    n = len(off) - 1
+    if wl["mode"] == 1:
+        k, two_m = O.weighted_degrees(off, host["w"])
+        p, q = wl["p"], wl["q"] * two_m
+    else:
+        k = np.ones(n, np.int64)
+        p, q = wl["p"], wl["q"]
+    L = np.arange(n, dtype=np.int32)
+    K = k
+    x = min(n, 4096)
+    done_edges, done_t, v0 = 0, 0.0, 0
+    while done_t < seconds and v0 < n:
+        v1 = min(n, v0 + x)
+        e0, e1 = int(off[v0]), int(off[v1])
+        offw = off[v0:v1 + 1] - off[v0]
+        nbrw = host["nbr"][e0:e1]
+        ww = (host["w"][e0:e1].astype(np.int64) if host["w"] is not None
+              else np.ones(e1 - e0, np.int64))
+        t0 = time.perf_counter()
+        O.desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K)
+        dt = time.perf_counter() - t0
+        done_edges += e1 - e0
+        done_t += dt
+        v0 = v1
+        if dt < seconds / 8:
+            x *= 2
+    return (done_edges / done_t / 1e9, "first best-move round of the same graph, vertices "
+            "[0, %d) (%d of %d vertices, %d entries scanned), single-threaded oracle"
+            % (v0, v0, n, done_edges))
+
+
+def degree_shares(off):
+    """Share of CSR entries in each degree bucket of the best-move kernels."""
+    import numpy as np
+    d = np.diff(off)
+    tot = max(1, int(d.sum()))
+    edges = [0, 4, 8, 16, 32, 256, 1024, 4096, None]
+    names = ["<=4", "<=8", "<=16", "<=32", "<=256", "<=1024", "<=4096", ">4096"]
+    out = {}
+    for i, nm in enumerate(names):
+        lo, hi = edges[i], edges[i + 1]
+        m = (d > lo) if hi is None else ((d > lo) & (d <= hi))
+        out[nm] = {"vertices": int(m.sum()), "entry_share": round(float(d[m].sum()) / tot, 4)}
+    out["max_degree"] = int(d.max()) if len(d) else 0
+    return out
+
+
+def host_copy(g):
+    import numpy as np
+    out = {}
+    for key in ("off", "nbr", "w"):
+        t = g.get(key)
+        out[key] = None if t is None else t.cpu().numpy()
+    return out
+
+
+# ---------------------------------------------------------------- serving --
+
+def serving_bench(L, count, device):
+    """Config-5 stream sample: plain one-graph-per-call path vs the continuous
+    batching server; graphs/s at saturation and p50/p99 under Poisson arrivals."""
+    import numpy as np
+    from paper_2108_01731_gb300 import inputs as I
+    graphs = []
+    for i in range(count):
+        g = I.serving_graph(i, device=device)
+        graphs.append({k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in g.items()
+                       if k in ("off", "nbr", "n", "nnz")})
+    mode = L.LCC_NODEW_DEGREE
+    # plain: one graph per call (load + cluster + labels to host)
+    t0 = time.perf_counter()
+    plain = []
+    for g in graphs:
+        G = L.lcc_load_csr(g["off"], g["nbr"])
+        lab, _, _ = L.lcc_cluster(G, 1, 1, mode)
+        plain.append(lab)
+        G.free()
+    t_plain = time.perf_counter() - t0
+    gps_plain = count / t_plain
+    tot_bytes = sum(g["nnz"] for g in graphs) * 40
+    budget = 120 << 30
+
+    def run_server(rate):
+        srv = L.Server(budget, 1 << 14)
+        rs = np.random.default_rng(12345)
+        gaps = rs.exponential(1.0 / rate, count) if rate else np.zeros(count)
+        t_start = time.perf_counter()
+        tickets = []
+        t_next = t_start
+        for g, gap in zip(graphs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.0005, max(0.0, t_next - time.perf_counter())))
+            tickets.append(srv.submit(g["off"], g["nbr"], None, 1, 1, mode))
+        srv.wait_idle(3600 * 1000)
+        t_end = time.perf_counter()
+        lats, same = [], True
+        for t, ref in zip(tickets, plain):
+            lab, obj, lat = srv.poll(t)
+            lats.append(lat)
+            same &= bool(np.array_equal(lab, ref))
+        c = srv.counters()
+        srv.close()
+        return count / (t_end - t_start), lats, same, c
+
+    gps_batched, lats_sat, same_sat, c_sat = run_server(0)
+    out = {"graphs": count, "config": "planted-partition stream, n log-uniform [100, 200000], "
+                                      "5-500 communities, mean degree 8-64, modularity",
+           "plain_graphs_per_s": round(gps_plain, 3),
+           "batched_graphs_per_s": round(gps_batched, 3),
+           "batched_over_plain": round(gps_batched / gps_plain, 3),
+           "labels_identical": same_sat,
+           "peak_concurrent_jobs": c_sat["peak_jobs"], "budget_bytes": budget, "rates": []}
+    for frac in (0.5, 1.0, 2.0):
+        rate = frac * gps_plain
+        gps, lats, same, c = run_server(rate)
+        out["rates"].append({"arrival_per_s": round(rate, 3), "x_plain": frac,
+                             "graphs_per_s": round(gps, 3),
+                             "p50_ms": round(float(np.percentile(lats, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lats, 99)), 3),
+                             "labels_identical": same, "peak_concurrent_jobs": c["peak_jobs"]})
+    return out
+
+
+# ------------------------------------------------------------------- arms --
+
+def run_reference(args, rank, world, local):
+    """The oracle (the CPU restatement of the method) as the reference arm."""
+    wl = WORKLOADS[args.workload]
+    if rank != 0:
+        return 0
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    g = make_graph(wl, dev)
+    host = host_copy(g)
+    del g
+    n_entries = len(host["nbr"])
+    vals = []
+    desc = ""
+    per = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        v, desc = oracle_sample(host, wl, per)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "best-move GEdges/s", "value": round(value, 6),
+            "unit": "GEdges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int128", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"],
+                       "csr_entries": n_entries, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GEdges/s", "cores": 1,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": "GEdges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2108_01731_gb300 import lcc as L
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    L.load()
+    t_gen = time.perf_counter()
+    g = make_graph(wl, dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    n, nnz = g["n"], g["nnz"]
+    stream = torch.cuda.current_stream().cuda_stream
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], stream=stream)
+    host = None
+    if not args.no_e2e or rank == 0:
+        host = host_copy(g)
+    del g
+    torch.cuda.empty_cache()
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    sched = L.schedule(num_iter=wl["num_iter"], timing=True)
+
+    def step():
+        return L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sched, labels_out=labels)[2]
+
+    for _ in range(args.warmup):
+        step()
+    ref_labels = labels.clone() if args.warmup > 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stats = [step() for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = reduce_scalar(ms, world, "max", dev)
+    edges = stats[-1]["edges_scanned"]
+    assert all(s["edges_scanned"] == edges for s in stats)
+    if ref_labels is None:
+        ref_labels = labels.clone()
+    assert torch.equal(labels, ref_labels), "labels changed between steps"
+    tot_edges = reduce_scalar(edges, world, "sum", dev)
+    value = tot_edges / (ms_max / 1e3) / 1e9
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    bm_bytes = statistics.mean(s["bytes_bestmove"] for s in stats)
+    bm_ms = statistics.mean(s["ms_bestmove"] for s in stats)
+    rounds = stats[-1]["rounds_total"]
+    peak, peak_kind = measured_peaks()
+    achieved = bm_bytes / (bm_ms / 1e3) / 1e9
+    tpe = profile_traffic()
+    roofline = {"kernel": "best-move (all degree buckets), per round", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": (round(tpe * edges / rounds) if tpe else None),
+                "algorithmic_bytes_per_round": int(bm_bytes / rounds),
+                "ms_per_round": round(bm_ms / rounds, 4), "rounds_per_step": rounds,
+                "bestmove_only_gedges_s": round(edges / (bm_ms / 1e3) / 1e9, 3)}
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: (torch.from_numpy(v).pin_memory() if v is not None else None)
+                  for k, v in host.items()}
+        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in pinned.values() if t is not None)
+
+        def e2e_step():
+            Gh = L.lcc_load_csr(pinned["off"].numpy(), pinned["nbr"].numpy(),
+                                None if pinned["w"] is None else pinned["w"].numpy(),
+                                stream=stream)
+            out = L.lcc_cluster(Gh, wl["p"], wl["q"], wl["mode"], sched,
+                                labels_out=hl.numpy())
+            Gh.free()
+            return out[2]
+
+        e2e_step()  # warm-up of the host path (pinned buffers, pool)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+        ms_e2e = reduce_scalar(ms_e2e, world, "max", dev)
+        assert np.array_equal(hl.numpy(), ref_labels.cpu().numpy())
+        e2e = {"value": round(tot_edges / (ms_e2e / 1e3) / 1e9, 4), "unit": "GEdges/s",
+               "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(n * 4)}
+        del pinned
+
+    cpu = None
+    serving = None
+    if rank == 0:
+        v, desc = oracle_sample(host, wl, args.cpu_seconds)
+        cpu = {"value": round(v, 6), "unit": "GEdges/s", "cores": 1, "kind": "oracle",
+               "sample": desc}
+        if args.serving > 0:
+            serving = serving_bench(L, args.serving, dev)
+    line = {"metric": "best-move GEdges/s", "value": round(value, 4), "unit": "GEdges/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "n": n,
+                       "csr_entries": nnz, "edges_scanned_per_step": edges,
+                       "levels": stats[-1]["levels"], "rounds_per_step": rounds,
+                       "num_clusters": stats[-1]["num_clusters"],
+                       "objective": stats[-1]["objective"],
+                       "ms_bestmove": round(bm_ms, 3),
+                       "ms_contract": round(statistics.mean(s["ms_contract"] for s in stats), 3),
+                       "ms_round_other": round(statistics.mean(s["ms_round_other"]
+                                                              for s in stats), 3),
+                       "ms_other": round(statistics.mean(s["ms_other"] for s in stats), 3),
+                       "pairs_sorted": stats[-1]["pairs_sorted"],
+                       "generation_s": round(t_gen, 2),
+                       "degree_buckets": degree_shares(host["off"]) if host else None,
+                       "l2": "inputs larger than L2 (CSR ~16.5 GB vs 129 MB L2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clocks}
+    if serving is not None:
+        line["serving"] = serving
+    G.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+import numpy as np  # noqa: E402  (used by run_ours' e2e check)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world != args.gpus and world > 1:
+        print("warning: WORLD_SIZE=%d but --gpus %d" % (world, args.gpus), file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, rank, world, local)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

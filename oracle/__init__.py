@@ -41,6 +41,8 @@ def lib():
                                         C.c_int, P, P]
         _lib.orc_sequential_sweep.argtypes = [I64, P, P, P, P, I64, I64, P, I64]
         _lib.orc_sequential_sweep.restype = I64
+        _lib.orc_weighted_degrees_i32.argtypes = [I64, P, P, P]
+        _lib.orc_weighted_degrees_i32.restype = I64
     return _lib
 
 
@@ -203,7 +205,12 @@ def sequential_sweep(off, nbr, w, k, p, q, L, max_moves):
     return L, mv
 
 
-def degrees(off, nbr, w):
-    off, nbr, w = _graph(off, nbr, w)
+def weighted_degrees(off, w32=None):
+    """Modularity node weights k_v = sum_u w_uv (Sec. 2) from int32 weights
+    (None = unweighted); returns (k, 2m)."""
+    off = _c(off, np.int64)
     n = len(off) - 1
-    return np.add.reduceat(np.append(w, 0), off[:-1])[:n] * (np.diff(off) > 0)
+    k = np.empty(n, np.int64)
+    wp = None if w32 is None else _c(w32, np.int32)
+    tot = lib().orc_weighted_degrees_i32(n, _p(off), None if wp is None else _p(wp), _p(k))
+    return k, int(tot)

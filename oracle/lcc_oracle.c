@@ -549,3 +549,17 @@ int64_t orc_sequential_sweep(int64_t n, const int64_t *off,
   scratch_free(&s);
   return moves;
 }
+
+/* Modularity node weights (Sec. 2): k_v = sum_u w_uv, from int32 weights
+ * (NULL = unweighted).  Returns the total 2m. */
+int64_t orc_weighted_degrees_i32(int64_t n, const int64_t *off,
+                                 const int32_t *w, int64_t *k_out) {
+  int64_t total = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t d = 0;
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) d += w ? (int64_t)w[e] : 1;
+    k_out[v] = d;
+    total += d;
+  }
+  return total;
+}

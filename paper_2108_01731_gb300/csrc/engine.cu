@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
@@ -24,6 +25,18 @@
 namespace lcc {
 
 std::atomic<long long> g_launches{0};
+
+// Slots of hub hash tables processed per pass (12 bytes each); the
+// LCC_HUB_WINDOW_SLOTS environment variable overrides it (tests use a small
+// window to exercise many passes).
+static int64_t hub_window() {
+  const char *e = getenv("LCC_HUB_WINDOW_SLOTS");
+  if (e) {
+    const long long v = atoll(e);
+    if (v >= 1024) return (int64_t)v;
+  }
+  return (int64_t)1 << 27;
+}
 
 void check_cuda(cudaError_t e, const char *what, int line) {
   if (e == cudaSuccess) return;
@@ -345,7 +358,7 @@ void Engine::round(std::vector<Job *> &js) {
   const int nj = (int)js.size();
   std::vector<JobDev> tab(nj);
   std::vector<int64_t> vs(nj + 1);
-  int64_t vt = 0, caps[NB] = {0}, hubcap = 0, hubs = 0, hub_su = 0;
+  int64_t vt = 0, caps[NB] = {0}, hubcap = 0, hubs = 0, hub_su = 0, hub_max = 0;
   bool wide = false, any_cl = false, any_mark = false, any_apply = false;
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
@@ -382,6 +395,7 @@ void Engine::round(std::vector<Job *> &js) {
     hubcap += L.info.hub_cap;
     hubs += L.info.bcnt[B_HUB];
     hub_su += L.info.hub_sunits;
+    hub_max = std::max(hub_max, L.info.hub_maxcap);
     wide |= L.wide;
   }
   vs[nj] = vt;
@@ -400,10 +414,15 @@ void Engine::round(std::vector<Job *> &js) {
   uint64_t *moved = s_moved_.get<uint64_t>(vt, st_);
   HubBufs h;
   memset(&h, 0, sizeof(h));
+  int64_t hub_passes = 0;
   if (hubs > 0) {
-    h.keys = s_hkeys_.get<int32_t>(hubcap, st_);
-    h.vals = s_hvals_.get<int64_t>(hubcap, st_);
-    h.cap_total = hubcap;
+    // Hub tables are processed in windows of kHubWindow slots (plus the
+    // largest table that may start near the end of a window).
+    const int64_t win = std::min(hubcap, hub_window());
+    hub_passes = (hubcap + win - 1) / win;
+    h.keys = s_hkeys_.get<int32_t>(win + hub_max, st_);
+    h.vals = s_hvals_.get<int64_t>(win + hub_max, st_);
+    h.window = win;
     int64_t *meta = s_hmeta_.get<int64_t>(3 * (hubs + 1) + hubs, st_);
     h.tbl_off = meta;
     h.unit_off = meta + (hubs + 1);
@@ -427,7 +446,7 @@ void Engine::round(std::vector<Job *> &js) {
   launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
   ++launches;
   if (timing) CK(cudaEventRecord(ev_[1], st_));
-  launch_bestmove(wide, dt, b, h, ctr, st_, d_, &launches);
+  launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_apply) {
     launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);
@@ -548,9 +567,11 @@ void Engine::contract(std::vector<Job *> &js) {
   if (ntot >= ((int64_t)1 << 31)) throw Error(LCC_ERR_OVERFLOW, "too many coarse vertices");
   stats.pairs += P;
 
-  uint64_t *keys = tmp.alloc<uint64_t>(P);
+  // the buffers the sort leaves free are reused for head flags (P + 1) and
+  // unique keys (<= P)
+  uint64_t *keys = tmp.alloc<uint64_t>(P + 1);
   int64_t *vals = tmp.alloc<int64_t>(P);
-  uint64_t *keys2 = tmp.alloc<uint64_t>(P);
+  uint64_t *keys2 = tmp.alloc<uint64_t>(P + 1);
   int64_t *vals2 = tmp.alloc<int64_t>(P);
   launch_emit_write(dt, dv, nj, vt, gmap, rank, pcnt, keys, vals, st_, d_);
   int64_t *knew = store->alloc<int64_t>(ntot);
@@ -567,7 +588,8 @@ void Engine::contract(std::vector<Job *> &js) {
   note_launches(lcount);
   uint64_t *sk = in_alt ? keys2 : keys;
   int64_t *sv = in_alt ? vals2 : vals;
-  int64_t *flags = tmp.alloc<int64_t>(P + 1);
+  int64_t *flags = (int64_t *)(in_alt ? keys : keys2);
+  uint64_t *ukeys = (uint64_t *)(in_alt ? vals : vals2);
   CK(cudaMemsetAsync(flags + P, 0, 8, st_));
   launch_seg_heads(sk, P, flags, st_, d_);
   scan_exclusive_i64(flags, P, stmp = tmp.alloc<int64_t>(scan_tmp_elems(P + 1)), st_, d_);
@@ -575,7 +597,6 @@ void Engine::contract(std::vector<Job *> &js) {
   CK(cudaMemcpyAsync(hb, flags + P, 8, cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
   const int64_t U = hb[0];
-  uint64_t *ukeys = tmp.alloc<uint64_t>(U);
   int64_t *uvals = store->alloc<int64_t>(U);
   int32_t *unbr = store->alloc<int32_t>(U);
   int64_t *offg = store->alloc<int64_t>(ntot + 1);

@@ -421,6 +421,9 @@ __device__ __forceinline__ int find_seg(const int64_t *__restrict__ off, int64_t
 }
 
 // Lays out one table, insertion units and scoring units per hub (one block).
+// Tables are placed back to back in a global slot space; the hubs whose table
+// starts in [lo, lo + window) are processed together in one pass, their
+// tables at (start - lo) in the scratch buffer.
 __global__ void __launch_bounds__(1024) k_hub_prep(const JobDev *__restrict__ jobs, Buckets b,
                                                    HubBufs h, int64_t *ctr) {
   __shared__ int64_t s_a[1024], s_b[1024], s_c[1024];
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(1024) k_hub_prep(const JobDev *__restrict__ jo
     __syncthreads();
   }
   if (tid == 0) {
-    if (run_a > h.cap_total || run_c > h.max_sunits) {
+    if (run_c > h.max_sunits) {
       atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
       H = 0;
       run_a = run_b = run_c = 0;
@@ -479,10 +482,24 @@ __global__ void __launch_bounds__(1024) k_hub_prep(const JobDev *__restrict__ jo
   }
 }
 
-__global__ void k_hub_clear(HubBufs h, const int64_t *ctr) {
+// First hub whose table starts at or after slot x.
+__device__ __forceinline__ int64_t hub_lower(const int64_t *__restrict__ tbl_off, int64_t H,
+                                             int64_t x) {
+  int64_t lo = 0, hi = H;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (tbl_off[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_hub_clear(HubBufs h, const int64_t *ctr, int64_t lo) {
   const int64_t H = ctr[C_HUBS];
-  const int64_t tot = h.tbl_off[H];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+  const int64_t h1 = hub_lower(h.tbl_off, H, lo + h.window);
+  const int64_t h0 = hub_lower(h.tbl_off, H, lo);
+  if (h0 >= h1) return;
+  const int64_t s0 = h.tbl_off[h0] - lo, s1 = h.tbl_off[h1] - lo;
+  for (int64_t i = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s1;
        i += (int64_t)gridDim.x * blockDim.x) {
     h.keys[i] = -1;
     h.vals[i] = 0;
@@ -490,15 +507,18 @@ __global__ void k_hub_clear(HubBufs h, const int64_t *ctr) {
 }
 
 __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ jobs, Buckets b,
-                                                    HubBufs h, int64_t *ctr) {
+                                                    HubBufs h, int64_t *ctr, int64_t lo) {
   __shared__ unsigned long long acc[8][32];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int64_t H = ctr[C_HUBS];
   if (H == 0) return;
-  const int64_t U = h.unit_off[H];
+  const int64_t h0 = hub_lower(h.tbl_off, H, lo);
+  const int64_t h1 = hub_lower(h.tbl_off, H, lo + h.window);
+  if (h0 >= h1) return;
+  const int64_t U0 = h.unit_off[h0], U1 = h.unit_off[h1];
   const uint64_t *items = b.items + b.seg_start[B_HUB];
   bool fail = false;
-  for (int64_t u = blockIdx.x; u < U; u += gridDim.x) {
+  for (int64_t u = U0 + blockIdx.x; u < U1; u += gridDim.x) {
     const int hh = find_seg(h.unit_off, H, u);
     const uint64_t item = items[hh];
     const JobDev *J = jobs + (int)(item >> 32);
@@ -507,8 +527,8 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
     const int64_t deg = J->off[v + 1] - beg;
     const int64_t cap = hub_cap(deg);
     const int lg = log2i(cap);
-    int32_t *tkey = h.keys + h.tbl_off[hh];
-    unsigned long long *tval = (unsigned long long *)(h.vals + h.tbl_off[hh]);
+    int32_t *tkey = h.keys + (h.tbl_off[hh] - lo);
+    unsigned long long *tval = (unsigned long long *)(h.vals + (h.tbl_off[hh] - lo));
     const int64_t e_lo = (u - h.unit_off[hh]) * HUB_CHUNK;
     int64_t e_hi = e_lo + HUB_CHUNK;
     if (e_hi > deg) e_hi = deg;
@@ -551,16 +571,19 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
 
 template <typename S>
 __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jobs, Buckets b,
-                                                   HubBufs h, int64_t *ctr) {
+                                                   HubBufs h, int64_t *ctr, int64_t lo) {
   __shared__ S red_s[8];
   __shared__ int32_t red_c[8];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int64_t H = ctr[C_HUBS];
   if (H == 0) return;
-  const int64_t SU = h.sunit_off[H];
+  const int64_t h0 = hub_lower(h.tbl_off, H, lo);
+  const int64_t h1 = hub_lower(h.tbl_off, H, lo + h.window);
+  if (h0 >= h1) return;
+  const int64_t SU0 = h.sunit_off[h0], SU1 = h.sunit_off[h1];
   const uint64_t *items = b.items + b.seg_start[B_HUB];
   long long ncand = 0;
-  for (int64_t su = blockIdx.x; su < SU; su += gridDim.x) {
+  for (int64_t su = SU0 + blockIdx.x; su < SU1; su += gridDim.x) {
     const int hh = find_seg(h.sunit_off, H, su);
     const uint64_t item = items[hh];
     const JobDev *J = jobs + (int)(item >> 32);
@@ -569,8 +592,8 @@ __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jo
     const int64_t cap = hub_cap(deg);
     const int32_t Lv = J->L[v];
     const int64_t kv = J->k[v];
-    const int32_t *tkey = h.keys + h.tbl_off[hh];
-    const int64_t *tval = h.vals + h.tbl_off[hh];
+    const int32_t *tkey = h.keys + (h.tbl_off[hh] - lo);
+    const int64_t *tval = h.vals + (h.tbl_off[hh] - lo);
     const int64_t s_lo = (su - h.sunit_off[hh]) * HUB_SCHUNK;
     int64_t s_hi = s_lo + HUB_SCHUNK;
     if (s_hi > cap) s_hi = cap;
@@ -641,8 +664,8 @@ int occ_blocks(K kernel, int threads, size_t smem) {
 }
 
 template <typename S>
-void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t *ctr,
-                   cudaStream_t st, const Dev &d, int *launches) {
+void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes,
+                   int64_t *ctr, cudaStream_t st, const Dev &d, int *launches) {
   static int occ[16] = {0};
   static bool init = false;
   const size_t smem1 = (size_t)BLK1_CAP * 12, smem2 = (size_t)BLK2_CAP * 12;
@@ -698,23 +721,28 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   }
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
-    k_hub_clear<<<d.sms * 8, 256, 0, st>>>(h, ctr);
-    k_hub_insert<<<d.sms * occ[7], 256, 0, st>>>(jobs, b, h, ctr);
-    k_hub_score<S><<<d.sms * occ[8], 256, 0, st>>>(jobs, b, h, ctr);
+    for (int64_t p = 0; p < hub_passes; ++p) {
+      const int64_t lo = p * h.window;
+      k_hub_clear<<<d.sms * 8, 256, 0, st>>>(h, ctr, lo);
+      k_hub_insert<<<d.sms * occ[7], 256, 0, st>>>(jobs, b, h, ctr, lo);
+      k_hub_score<S><<<d.sms * occ[8], 256, 0, st>>>(jobs, b, h, ctr, lo);
+      *launches += 3;
+    }
     int64_t fg = (b.seg_cap[B_HUB] + 7) / 8;
     if (fg > d.sms * 4) fg = d.sms * 4;
     k_hub_final<S><<<(int)(fg > 0 ? fg : 1), 256, 0, st>>>(jobs, b, h, ctr);
-    *launches += 5;
+    *launches += 2;
   }
 }
 }  // namespace
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     int64_t *ctr, cudaStream_t st, const Dev &d, int *launches) {
+                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
+                     int *launches) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, ctr, st, d, launches);
+    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches);
   else
-    bestmove_impl<int64_t>(jobs, b, h, ctr, st, d, launches);
+    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches);
 }
 
 // --------------------------------------------------------------- apply ----

@@ -116,9 +116,9 @@ struct Buckets {
 };
 
 struct HubBufs {
-  int32_t *keys;
+  int32_t *keys;      // one window of tables: [window + largest table] slots
   int64_t *vals;
-  int64_t cap_total;  // slots available in keys/vals
+  int64_t window;     // hubs whose table starts in [lo, lo + window) share a pass
   int64_t *tbl_off;   // [max_hubs + 1]
   int64_t *unit_off;  // [max_hubs + 1]
   int64_t *sunit_off; // [max_hubs + 1]
@@ -169,7 +169,8 @@ struct LevelInfo {
   int64_t kmax;         // max node weight
   int64_t ksum;         // sum of node weights
   int64_t wabs;         // sum of |w| over entries
-  int64_t pad;
+  int64_t pad;          // vertices with a negative node weight
+  int64_t hub_maxcap;   // largest hub table
 };
 
 // Per-job accumulators of the objective kernels.
@@ -255,7 +256,8 @@ struct Dev {
 void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     int64_t *ctr, cudaStream_t st, const Dev &d, int *launches);
+                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
+                     int *launches);
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
 void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, bool any_cl,

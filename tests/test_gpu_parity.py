@@ -339,3 +339,22 @@ def test_server_rejects_oversize_and_cancels(L):
         srv.poll(t2)
     assert e.value.status == L.LCC_ERR_CANCELLED
     srv.close()
+
+
+def test_hub_tables_in_many_windows(L, monkeypatch):
+    """Hub hash tables processed in small windows (many passes per round)
+    give the same desired clusters and the same clustering."""
+    monkeypatch.setenv("LCC_HUB_WINDOW_SLOTS", "4096")
+    g = GRAPHS["hubs_w"]
+    n = g["n"]
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    Lb = I.random_labels(n, n // 40, seed=77).numpy()
+    K = np.zeros(n, np.int64)
+    np.add.at(K, Lb, 1)
+    got = L.lcc_desired(G, 1, 9, O.NODEW_UNIT, Lb)
+    want = O.desired(g["off"], g["nbr"], g["w"], np.ones(n, np.int64), 1, 9, Lb, K)
+    assert np.array_equal(got, want)
+    labels, obj, st = L.lcc_cluster(G, 1, 9, O.NODEW_UNIT)
+    wl, num, den, _ = O.cluster(g["off"], g["nbr"], g["w"], 1, 9)
+    assert np.array_equal(labels, wl) and st["obj_num"] == num
+    G.free()

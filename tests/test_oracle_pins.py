@@ -443,3 +443,14 @@ def test_deterministic_and_refinement_flag():
     assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
     c = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE, refine=False)
     assert c[3][1] < a[3][1]
+
+
+def test_weighted_degrees_match_numpy():
+    for seed in range(3):
+        g = I.to_numpy(I.random_signed_graph(50, 0.2, 0, 9, 600 + seed))
+        k, tot = O.weighted_degrees(g["off"], g["w"])
+        want = np.zeros(g["n"], np.int64)
+        np.add.at(want, np.repeat(np.arange(g["n"]), np.diff(g["off"])), g["w"].astype(np.int64))
+        assert np.array_equal(k, want) and tot == int(want.sum())
+        k1, t1 = O.weighted_degrees(g["off"], None)
+        assert np.array_equal(k1, np.diff(g["off"])) and t1 == g["nnz"]

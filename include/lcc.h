@@ -210,6 +210,37 @@ LCC_API lcc_status lcc_objective(const lcc_graph *g, int64_t lambda_p,
                          int64_t lambda_q, int32_t mode, const int32_t *labels,
                          int64_t *num_hi, uint64_t *num_lo, int64_t *den);
 
+/*
+ * lcc_desired_noalloc -- the evaluation of lcc_desired (every vertex
+ * evaluated, node weights given) on a graph, labels and cluster weights that
+ * already live in device memory, without allocating any device memory.  The
+ * paper has no counterpart: this entry point exists for callers that may not
+ * allocate GPU memory at the point of the call, because their own runtime owns
+ * every device allocation (a memory-budgeted host framework, or a process that
+ * gave the rest of the GPU's memory to another allocator).  Every other entry
+ * point allocates working memory from a stream-ordered pool.
+ *
+ * All pointers are device pointers owned by the caller:
+ *   d_off [n+1] int64, d_nbr [nnz] int32, d_w [nnz] int32 or NULL (w = 1),
+ *   d_k [n] int64 node weights, d_labels [n] int32 in [0, n),
+ *   d_K [n] int64 cluster weights (K[c] = sum of d_k over vertices labelled c),
+ *   d_desired [n] int32 output.
+ * lambda = lambda_p / lambda_q > 0 (for modularity pass q * 2m).
+ * Working memory is one fixed 16 MiB array inside the library, which every GPU
+ * that loads the library keeps until the process exits; rows longer than 4096
+ * entries do not fit and make the call return LCC_ERR_INVALID (the other rows
+ * are still written).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array and the call clears what it
+ * needs, but calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it: order them.  Synchronises `stream` before returning.
+ */
+LCC_API lcc_status lcc_desired_noalloc(const int64_t *d_off, const int32_t *d_nbr,
+                                       const int32_t *d_w, const int64_t *d_k, int64_t n,
+                                       int64_t lambda_p, int64_t lambda_q,
+                                       const int32_t *d_labels, const int64_t *d_K,
+                                       int32_t *d_desired, void *stream);
+
 /* ----------------------------------------------------------------------
  * Batched and served clustering.
  *

@@ -21,6 +21,10 @@ void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t 
 
 static thread_local std::string t_err;
 
+namespace lcc {
+void set_last_error(const std::string &m) { t_err = m; }
+}
+
 #define API_BEGIN try {
 #define API_END                                   \
   }                                               \

@@ -78,6 +78,7 @@ _SIGS = {
     "lcc_compress": [P, I32, P, P, P],
     "lcc_graph_export": [P, P, P, P, P],
     "lcc_objective": [P, I64, I64, I32, P, P, P, P],
+    "lcc_desired_noalloc": [P, P, P, P, I64, I64, I64, P, P, P, P],
     "lcc_cluster_batch": [P, I32, P, P, P, P, P, P],
     "lcc_server_create": [P, P],
     "lcc_submit": [P, P, P],
@@ -280,6 +281,20 @@ def lcc_objective(g, lambda_p, lambda_q, mode, labels):
     if num >= 1 << 127:
         num -= 1 << 128
     return num, den.value
+
+
+def lcc_desired_noalloc(off, nbr, w, k, lambda_p, lambda_q, labels, K, out, stream=None):
+    """Allocation-free evaluation on device tensors (all torch CUDA tensors;
+    `out` int32[n] receives the desired clusters).  The library allocates
+    nothing for this call; see include/lcc.h."""
+    n = off.numel() - 1
+    st = C.c_void_p(int(stream)) if stream else None
+
+    def p(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+    _check(load().lcc_desired_noalloc(p(off), p(nbr), p(w), p(k), n, int(lambda_p),
+                                      int(lambda_q), p(labels), p(K), p(out), st))
+    return out
 
 
 def lcc_cluster_batch(graphs, lambda_p, lambda_q, mode, sched=None):

@@ -32,6 +32,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Degree buckets of the best-move kernels (row lengths), as in lcc_stats.
+BUCKETS = ["<=4", "<=8", "<=16", "<=32", "<=64", "<=128", "<=256", "<=1024", "<=4096",
+           "<=8192", "<=16384", "<=32768", "<=65536", ">65536"]
+
 WORKLOADS = {
     # name: generator, node-weight mode, lambda p/q, rounds per Best-Moves
     "rmat26": dict(kind="rmat", scale=26, m=1 << 30, mode=1, p=1, q=1, num_iter=10,
@@ -418,7 +422,16 @@ def run_ours(args, rank, world, local):
                 "traffic": (round(tpe * edges / rounds) if tpe else None),
                 "algorithmic_bytes_per_round": int(bm_bytes / rounds),
                 "ms_per_round": round(bm_ms / rounds, 4), "rounds_per_step": rounds,
-                "bestmove_only_gedges_s": round(edges / (bm_ms / 1e3) / 1e9, 3)}
+                "bestmove_only_gedges_s": round(edges / (bm_ms / 1e3) / 1e9, 3),
+                "ms_per_bucket": dict(zip(BUCKETS,
+                                          [round(statistics.mean(s["ms_bucket"][i]
+                                                                 for s in stats), 2)
+                                           for i in range(len(BUCKETS))])),
+                "entries_per_bucket": [int(statistics.mean(s["bucket_entries"][i] for s in stats))
+                                       for i in range(len(BUCKETS))],
+                "vertices_per_bucket": [int(statistics.mean(s["bucket_vertices"][i]
+                                                            for s in stats))
+                                        for i in range(len(BUCKETS))]}
 
     e2e = None
     if not args.no_e2e:

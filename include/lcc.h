@@ -113,6 +113,13 @@ typedef struct lcc_stats {
   int64_t bytes_bestmove;  /* algorithmic bytes of the best-move kernels */
   int64_t pairs_sorted;    /* inter-cluster entries sorted by compression */
   int64_t kernel_launches; /* kernels launched by this call */
+  /* best-move device time per degree bucket (rows of <=4, <=8, <=16, <=32,
+     <=64, <=128, <=256, <=1024, <=4096, <=8192, <=16384, <=32768, <=65536
+     entries, and longer; the last two elements are unused), filled when
+     LCC_SCHED_TIMING is set */
+  double ms_bucket[16];
+  int64_t bucket_entries[16];  /* entries scanned per degree bucket */
+  int64_t bucket_vertices[16]; /* vertices evaluated per degree bucket */
 } lcc_stats;
 
 typedef struct lcc_graph lcc_graph;

@@ -99,13 +99,16 @@ Engine::Engine(int dev, cudaStream_t st) : dev_(dev), st_(st) {
   d_.sms = sms;
   d_.dev = dev;
   for (auto &e : ev_) CK(cudaEventCreate(&e));
+  for (auto &e : bev_) CK(cudaEventCreate(&e));
 }
 
 Engine::~Engine() {
   for (auto &e : ev_) cudaEventDestroy(e);
+  for (auto &e : bev_) cudaEventDestroy(e);
   Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                     &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
+                    &s_gtab_};
   for (Scratch *s : all) s->release(st_);
   cudaStreamSynchronize(st_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -115,7 +118,8 @@ Engine::~Engine() {
 size_t Engine::scratch_bytes() const {
   const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                           &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
+                    &s_gtab_};
   size_t t = 0;
   for (const Scratch *s : all) t += s->bytes;
   return t;
@@ -280,6 +284,7 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
   L0.D = j->base->alloc<int32_t>(n);
   L0.fr = j->base->alloc<uint8_t>(n);
   L0.cl = j->base->alloc<uint8_t>(n);
+  L0.lk = j->base->alloc<unsigned long long>(n);
   CK(cudaMemsetAsync(L0.fr, 0, n, st_));
   CK(cudaMemsetAsync(L0.cl, 0, n, st_));
   j->lv.clear();
@@ -303,6 +308,8 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
     if ((i128)I.ksum * (i128)I.ksum >= ((i128)1 << 126))
       throw Error(LCC_ERR_OVERFLOW, "total node weight too large for exact arithmetic");
     j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
+    // cluster weights fit the 32-bit half of the packed label word
+    if (j->ktot >= (int64_t)KNONE) j->lv[0].lk = nullptr;
   }
   Level &L = j->lv[0];
   if (init_labels_host) {
@@ -373,6 +380,7 @@ void Engine::round(std::vector<Job *> &js) {
     x.D = L.D;
     x.fr = L.fr;
     x.cl = L.cl;
+    x.lk = L.lk;
     x.n = L.n;
     x.p = J->p;
     x.q = J->q;
@@ -409,6 +417,7 @@ void Engine::round(std::vector<Job *> &js) {
   }
   b.items = s_items_.get<uint64_t>(tot, st_);
   b.cnt = s_cnt_.get<int64_t>(NB, st_);
+
   int64_t *ctr = s_ctr_.get<int64_t>(NCTR, st_);
   int64_t *jm = s_jmoves_.get<int64_t>(nj, st_);
   uint64_t *moved = s_moved_.get<uint64_t>(vt, st_);
@@ -420,7 +429,7 @@ void Engine::round(std::vector<Job *> &js) {
     // largest table that may start near the end of a window).
     const int64_t win = std::min(hubcap, hub_window());
     hub_passes = (hubcap + win - 1) / win;
-    h.keys = s_hkeys_.get<int32_t>(win + hub_max, st_);
+    h.keys = s_hkeys_.get<unsigned long long>(win + hub_max, st_);
     h.vals = s_hvals_.get<int64_t>(win + hub_max, st_);
     h.window = win;
     int64_t *meta = s_hmeta_.get<int64_t>(3 * (hubs + 1) + hubs, st_);
@@ -446,7 +455,17 @@ void Engine::round(std::vector<Job *> &js) {
   launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
   ++launches;
   if (timing) CK(cudaEventRecord(ev_[1], st_));
-  launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches);
+  // global tables of the cluster kernels: GTAB_BYTES in all (keys and sums),
+  // split between the clusters in flight of each launch
+  GTab gt;
+  {
+    const int64_t slots = 1;  // the cluster kernels keep their tables in shared memory
+    unsigned long long *g = s_gtab_.get<unsigned long long>(2 * slots, st_);
+    gt.keys = g;
+    gt.vals = g + slots;
+    gt.stride = slots;  // total slots; each launch divides them
+  }
+  launch_bestmove(wide, dt, b, h, gt, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_apply) {
     launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);
@@ -466,9 +485,15 @@ void Engine::round(std::vector<Job *> &js) {
   stats.edges += hbuf[C_EDGES];
   stats.verts += hbuf[C_VERTS];
   stats.cands += hbuf[C_CANDS];
-  stats.wbytes += hbuf[7];
+  stats.wbytes += hbuf[C_WB];
+  for (int i = 0; i < NB; ++i) {
+    stats.bucket_entries[i] += hbuf[C_BE + i];
+    stats.bucket_vertices[i] += hbuf[C_BV + i];
+  }
   stats.rounds += 1;
   if (timing) {
+    for (int i = 0; i < NB; ++i)
+      stats.ms_bucket[i] += elapsed(i == 0 ? ev_[1] : bev_[i - 1], bev_[i]);
     stats.ms_bm += elapsed(ev_[1], ev_[2]);
     stats.ms_round_other += elapsed(ev_[0], ev_[1]) + elapsed(ev_[2], ev_[3]);
   }
@@ -609,6 +634,7 @@ void Engine::contract(std::vector<Job *> &js) {
   int32_t *Du = store->alloc<int32_t>(ntot);
   uint8_t *fru = store->alloc<uint8_t>(ntot);
   uint8_t *clu = store->alloc<uint8_t>(ntot);
+  unsigned long long *lku = store->alloc<unsigned long long>(ntot);
   CK(cudaMemsetAsync(fru, 0, ntot > 0 ? ntot : 1, st_));
   CK(cudaMemsetAsync(clu, 0, ntot > 0 ? ntot : 1, st_));
 
@@ -635,6 +661,7 @@ void Engine::contract(std::vector<Job *> &js) {
     nl.D = Du + cbase[i];
     nl.fr = fru + cbase[i];
     nl.cl = clu + cbase[i];
+    nl.lk = J->ktot < (int64_t)KNONE ? lku + cbase[i] : nullptr;
     nl.store = store;
     J->lv.push_back(nl);
     J->depth += 1;

@@ -97,6 +97,7 @@ struct Level {
   int32_t *D = nullptr;
   uint8_t *fr = nullptr;
   uint8_t *cl = nullptr;
+  unsigned long long *lk = nullptr;  // packed (K[L[u]], L[u]); null if K can exceed 32 bits
   int32_t *map = nullptr;  // vertex -> coarse vertex of the next level
   std::shared_ptr<Store> store;
   std::shared_ptr<Store> map_store;
@@ -143,6 +144,9 @@ struct EngineStats {
   int64_t edges = 0, verts = 0, cands = 0, wbytes = 0, pairs = 0;
   int64_t rounds = 0;
   double ms_bm = 0, ms_round_other = 0, ms_contract = 0, ms_other = 0;
+  double ms_bucket[NB] = {0};
+  int64_t bucket_entries[NB] = {0};
+  int64_t bucket_vertices[NB] = {0};
 };
 
 class Engine {
@@ -184,13 +188,14 @@ class Engine {
   // scratch
   Scratch s_jobs_, s_vstart_, s_items_, s_cnt_, s_ctr_, s_jmoves_, s_moved_;
   Scratch s_hkeys_, s_hvals_, s_hmeta_, s_hpart_s_, s_hpart_c_, s_hstay_, s_hiso_;
-  Scratch s_ljobs_, s_info_, s_obj_;
+  Scratch s_ljobs_, s_info_, s_obj_, s_gtab_;
   // pinned host staging
   void *h_stage_ = nullptr;
   size_t h_stage_bytes_ = 0;
   void *h_stage2_ = nullptr;
   size_t h_stage2_bytes_ = 0;
   cudaEvent_t ev_[8];
+  cudaEvent_t bev_[NB];
   void *stage(size_t bytes);
   void *stage2(size_t bytes);
 };

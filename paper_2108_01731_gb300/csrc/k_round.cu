@@ -1,6 +1,8 @@
 // Kernels of one synchronous Best-Moves round (Algorithm 1, Sec. 3.2.1).
 //
-//   k_frontier  builds V' (Sec. 3.2.2) as per-degree-bucket work lists;
+//   k_frontier  builds V' (Sec. 3.2.2) as per-degree-bucket work lists and
+//               packs lk[u] = (K[L[u]], L[u]) for every vertex, so that one
+//               gather yields both a neighbour's cluster and its weight;
 //   k_bm_*      compute D[v] for every v in V' from the snapshot (L, K):
 //               aggregate w(v, C) over the neighbouring clusters C, score
 //               each with the Appendix A gain (times q, exact integers),
@@ -15,7 +17,17 @@
 //   stay       q * w(v, c minus v) - p * k_v * (K_c - k_v)
 // S is int64_t when the host has proven both products stay below 2^62 for
 // this level, else __int128.
+//
+// Aggregation by degree: up to 32 entries in registers (groups of 4..32
+// lanes, equal clusters found with __match_any_sync); up to 256 in a per-warp
+// shared-memory table; up to 4096 in a per-block table; up to 65536 in a table
+// spread over the distributed shared memory of a 2..16-block cluster; above
+// that in global-memory tables processed in bounded windows.
+#include <cooperative_groups.h>
+
 #include "lcc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lcc {
 
@@ -29,14 +41,14 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 __device__ __forceinline__ uint32_t slot_of(int32_t c, int lg) {
-  uint64_t h = (uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull;
+  const uint64_t h = (uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull;
   return (uint32_t)(h >> (64 - lg));
 }
 
 __device__ __forceinline__ int log2i(int64_t pow2) { return 63 - __clzll((long long)pow2); }
 
 __device__ __forceinline__ int64_t seg_count(const Buckets &b, int bk) {
-  int64_t c = b.cnt[bk];
+  const int64_t c = b.cnt[bk];
   return c < b.seg_cap[bk] ? c : b.seg_cap[bk];
 }
 
@@ -50,23 +62,135 @@ template <typename S>
 __device__ __forceinline__ void warp_argmax(S &s, int32_t &c) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    S os = ScoreOps<S>::shfl_xor(s, o, 32);
-    int32_t oc = __shfl_xor_sync(FULL, c, o);
+    const S os = ScoreOps<S>::shfl_xor(s, o, 32);
+    const int32_t oc = __shfl_xor_sync(FULL, c, o);
     if (better<S>(os, oc, s, c)) { s = os; c = oc; }
   }
 }
 
-// Final decision of one vertex: the empty cluster id v (reading of the
-// paper's silence on empty clusters), then the strict comparison with staying.
+__device__ __forceinline__ unsigned long long slot_word(int32_t c, uint32_t k32) {
+  return ((unsigned long long)k32 << 32) | (uint32_t)c;
+}
+
+// Fields of one job's current level, held in registers by the kernels (the
+// job table lives in global memory; reading it once per vertex keeps the
+// inner loops free of table loads).
+struct JobView {
+  const int64_t *off;
+  const int32_t *nbr;
+  const void *w;
+  const int64_t *k;
+  const int32_t *L;
+  const int64_t *K;
+  int32_t *D;
+  const unsigned long long *lk;
+  int64_t p, q;
+  int32_t wtype;
+};
+
+__device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
+  JobView x;
+  x.off = J->off;
+  x.nbr = J->nbr;
+  x.w = J->w;
+  x.k = J->k;
+  x.L = J->L;
+  x.K = J->K;
+  x.D = J->D;
+  x.lk = J->lk;
+  x.p = J->p;
+  x.q = J->q;
+  x.wtype = J->wtype;
+  return x;
+}
+
+// Cluster of neighbour u and, when packed, its weight.
+__device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c, uint32_t &k32) {
+  if (J.lk) {
+    const unsigned long long x = __ldg(J.lk + u);
+    c = (int32_t)(uint32_t)x;
+    k32 = (uint32_t)(x >> 32);
+  } else {
+    c = J.L[u];
+    k32 = KNONE;
+  }
+}
+
+__device__ __forceinline__ long long weight_at(const JobView &J, int64_t e) {
+  if (J.wtype == W_I32) return (long long)__ldg((const int32_t *)J.w + e);
+  if (J.wtype == W_I64) return (long long)__ldg((const int64_t *)J.w + e);
+  return 1;
+}
+
+__device__ __forceinline__ int64_t weight_of(const JobView &J, int32_t c, uint32_t k32) {
+  return k32 != KNONE ? (int64_t)k32 : J.K[c];
+}
+
 template <typename S>
-__device__ __forceinline__ int32_t decide(const JobDev *J, int32_t v, int32_t Lv, int64_t kv,
-                                          S best, int32_t bc, long long w_stay, bool v_seen) {
-  const S p = (S)J->p, q = (S)J->q;
-  if (Lv != v && !v_seen && J->K[v] == 0) {
+__device__ __forceinline__ S score_of(const JobView &J, int64_t kv, long long wsum, int32_t c,
+                                      uint32_t k32) {
+  return (S)J.q * (S)wsum - (S)J.p * (S)kv * (S)weight_of(J, c, k32);
+}
+
+// Final decision of one vertex: cluster id v when it has zero weight and no
+// neighbour in it (gain 0), then the strict comparison with staying.
+template <typename S>
+__device__ __forceinline__ int32_t decide(const JobView &J, int32_t v, int32_t Lv, int64_t kv,
+                                          int64_t KLv, S best, int32_t bc, long long w_stay,
+                                          bool v_seen, int64_t Kv = -1) {
+  const S p = (S)J.p, q = (S)J.q;
+  if (Lv != v && !v_seen && (Kv >= 0 ? Kv : J.K[v]) == 0) {
     if (better<S>((S)0, v, best, bc)) { best = 0; bc = v; }
   }
-  const S stay = q * (S)w_stay - p * (S)kv * ((S)J->K[Lv] - (S)kv);
+  const S stay = q * (S)w_stay - p * (S)kv * ((S)KLv - (S)kv);
   return (bc != INT32_MAX && best > stay) ? bc : Lv;
+}
+
+// Weight of v's own cluster from the snapshot.
+__device__ __forceinline__ int64_t own_weight(const JobView &J, int32_t v, int32_t Lv) {
+  return J.lk ? (int64_t)(__ldg(J.lk + v) >> 32) : J.K[Lv];
+}
+
+// The scalars of v that the final decision needs.
+struct Own {
+  int32_t Lv;
+  int64_t kv, KLv, Kv;
+};
+// Issued early so the loads overlap the row's gathers.
+__device__ __forceinline__ Own own_of(const JobView &J, int32_t v) {
+  Own o;
+  if (J.lk) {
+    const unsigned long long x = __ldg(J.lk + v);
+    o.Lv = (int32_t)(uint32_t)x;
+    o.KLv = (int64_t)(x >> 32);
+  } else {
+    o.Lv = J.L[v];
+    o.KLv = J.K[o.Lv];
+  }
+  o.kv = J.k[v];
+  o.Kv = J.K[v];
+  return o;
+}
+
+// Linear-probing insert of (c, k32) += sum.  The table has at least twice as
+// many slots as keys, so a free or matching slot is found within cap probes.
+// `at(s, kp, vp)` gives the key and value pointers of slot s.
+template <class At>
+__device__ __forceinline__ bool probe_insert(At at, uint32_t cap, int lg, int32_t c, uint32_t k32,
+                                             long long sum) {
+  const unsigned long long word = slot_word(c, k32);
+  uint32_t s = slot_of(c, lg);
+  for (uint32_t t = 0; t < cap; ++t) {
+    unsigned long long *kp, *vp;
+    at(s, kp, vp);
+    const unsigned long long prev = atomicCAS(kp, SLOT_EMPTY, word);
+    if (prev == SLOT_EMPTY || (int32_t)(uint32_t)prev == c) {
+      atomicAdd(vp, (unsigned long long)sum);
+      return true;
+    }
+    s = (s + 1) & (cap - 1);
+  }
+  return false;
 }
 }  // namespace
 
@@ -83,10 +207,13 @@ __global__ void __launch_bounds__(256) k_frontier(const JobDev *__restrict__ job
     const int64_t i = base + lane;
     int bk = -1;
     uint64_t item = 0;
+    int64_t my_last_deg = 0;
     if (i < vtot) {
       const int j = find_job(vstart, njobs, i);
       const JobDev *J = jobs + j;
       const int64_t v = i - vstart[j];
+      const int32_t Lv = J->L[v];
+      if (J->lk) J->lk[v] = slot_word(Lv, (uint32_t)J->K[Lv]);
       bool f = (J->flags & JF_ALL) != 0;
       if (J->fr[v]) {
         J->fr[v] = 0;
@@ -95,8 +222,9 @@ __global__ void __launch_bounds__(256) k_frontier(const JobDev *__restrict__ job
       if (f) {
         const int64_t deg = J->off[v + 1] - J->off[v];
         // A vertex with no neighbour in its own singleton has no candidate.
-        if (!(deg == 0 && J->L[v] == (int32_t)v)) {
+        if (!(deg == 0 && Lv == (int32_t)v)) {
           bk = bucket_of(deg);
+          my_last_deg = deg;
           item = ((uint64_t)(uint32_t)j << 32) | (uint32_t)v;
           my_deg += deg;
           my_cnt += 1;
@@ -118,6 +246,11 @@ __global__ void __launch_bounds__(256) k_frontier(const JobDev *__restrict__ job
           b.items[b.seg_start[bk] + pos] = item;
         else
           atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_BUCKET_OVERFLOW);
+        const unsigned ents = __reduce_add_sync(peers, (unsigned)my_last_deg);
+        if (lane == leader) {
+          atomicAdd((unsigned long long *)&ctr[C_BE + bk], (unsigned long long)ents);
+          atomicAdd((unsigned long long *)&ctr[C_BV + bk], (unsigned long long)__popc(peers));
+        }
       }
     }
   }
@@ -135,14 +268,14 @@ void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d) {
   if (vtot <= 0) return;
   int64_t blocks = (vtot + 255) / 256;
-  int64_t maxb = (int64_t)d.sms * 8;
+  const int64_t maxb = (int64_t)d.sms * 8;
   if (blocks > maxb) blocks = maxb;
   k_frontier<<<(int)blocks, 256, 0, st>>>(jobs, vstart, njobs, vtot, b, ctr);
 }
 
 // ------------------------------------------------ deg <= G: G lanes/vertex --
 
-// Each group of G lanes takes one vertex; lane t reads edge t.  Equal
+// Each group of G lanes takes one vertex; lane t reads entry t.  Equal
 // clusters are found with __match_any_sync on (group, cluster) and summed
 // into the group leader's shared slot; the leaders' scores are then reduced
 // inside the group with xor-shuffles of width G.
@@ -164,35 +297,39 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
     const int64_t it = wbase + gsub;
     const bool valid = it < count;
     const uint64_t item = valid ? items[it] : 0ull;
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
     int64_t beg = 0;
     int deg = 0;
     int32_t Lv = 0;
     int64_t kv = 0;
     if (valid) {
-      beg = J->off[v];
-      deg = (int)(J->off[v + 1] - beg);
-      Lv = J->L[v];
-      kv = J->k[v];
+      beg = J.off[v];
+      deg = (int)(J.off[v + 1] - beg);
+      Lv = J.L[v];
+      kv = J.k[v];
     }
     const bool has = valid && gl < deg;
     int32_t c = -1;
+    uint32_t k32 = KNONE;
     long long wt = 0;
     if (has) {
-      const int32_t u = __ldg(J->nbr + beg + gl);
-      wt = load_w(J->w, J->wtype, beg + gl);
-      c = J->L[u];
+      const int32_t u = __ldg(J.nbr + beg + gl);
+      wt = weight_at(J, beg + gl);
+      label_of(J, u, c, k32);
     }
     const unsigned long long key = ((unsigned long long)gsub << 32) | (uint32_t)c;
     const unsigned peers = __match_any_sync(FULL, key);
     const int leader = __ffs(peers) - 1;
-    acc[wib][lane] = 0;
-    __syncwarp();
-    if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
-    __syncwarp();
-    const long long wsum = (long long)acc[wib][lane];
-    __syncwarp();
+    long long wsum = wt;
+    if (!__all_sync(FULL, !has || __popc(peers) == 1)) {
+      acc[wib][lane] = 0;
+      __syncwarp();
+      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
+      __syncwarp();
+      wsum = (long long)acc[wib][lane];
+      __syncwarp();
+    }
     const bool lead = has && lane == leader;
     const bool is_stay = lead && c == Lv;
     const unsigned sb = __ballot_sync(FULL, is_stay) & gmask;
@@ -203,7 +340,7 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
     S score = ScoreOps<S>::lowest();
     int32_t cid = INT32_MAX;
     if (cand) {
-      score = (S)J->q * (S)wsum - (S)J->p * (S)kv * (S)J->K[c];
+      score = score_of<S>(J, kv, wsum, c, k32);
       cid = c;
     }
 #pragma unroll
@@ -212,97 +349,155 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
       const int32_t oc = __shfl_xor_sync(FULL, cid, o, G);
       if (better<S>(os, oc, score, cid)) { score = os; cid = oc; }
     }
-    if (valid && gl == 0) J->D[v] = decide<S>(J, v, Lv, kv, score, cid, w_stay, v_seen);
+    if (valid && gl == 0)
+      J.D[v] = decide<S>(J, v, Lv, kv, own_weight(J, v, Lv), score, cid, w_stay, v_seen);
     ncand += __popc(__ballot_sync(FULL, cand));
   }
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
 }
 
-// ----------------------------------- deg <= T_WARP: warp + shared table --
+// ------------------------------------------------ preloaded row chunks -----
 
-// Inserts (c, sum) into an open-addressing table (linear probing).  The
-// table has at least twice as many slots as keys, so a free or matching slot
-// is always found within `cap` probes.
-__device__ __forceinline__ bool table_insert(int32_t *tkey, unsigned long long *tval, int cap,
-                                             int lg, int32_t c, long long sum) {
-  uint32_t s = slot_of(c, lg);
-  for (int t = 0; t < cap; ++t) {
-    const int32_t prev = atomicCAS(tkey + s, -1, c);
-    if (prev == -1 || prev == c) {
-      atomicAdd(tval + s, (unsigned long long)sum);
-      return true;
+// E entries per thread, entry i of thread t at lo + i * stride + t: the
+// neighbour ids and weights are loaded first and the labels gathered next,
+// so that up to E independent gathers per thread are in flight.
+template <int E>
+struct Chunk {
+  int32_t c[E];
+  uint32_t k[E];
+  long long w[E];
+};
+
+template <int E>
+__device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_t lo, int64_t hi,
+                                           int stride, int t, Chunk<E> &x) {
+  int32_t u[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int64_t e = lo + (int64_t)i * stride + t;
+    u[i] = -1;
+    x.w[i] = 0;
+    if (e < hi) {
+      u[i] = __ldg(J.nbr + beg + e);
+      x.w[i] = weight_at(J, beg + e);
     }
-    s = (s + 1) & (uint32_t)(cap - 1);
   }
-  return false;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    x.c[i] = -1;
+    x.k[i] = KNONE;
+    if (u[i] >= 0) label_of(J, u[i], x.c[i], x.k[i]);
+  }
 }
 
+// Inserts a thread's chunk into a table.  The first probe of every entry is
+// issued before any result is examined, so the compare-and-swaps overlap;
+// entries whose home slot holds another cluster continue probing one by one.
+// Equal clusters need no pre-aggregation: every inserter of a cluster finds
+// its slot and adds to it (integer sums, so the order does not matter).
+template <int E, class At>
+__device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, uint32_t cap, int lg) {
+  unsigned long long prev[E];
+  uint32_t home[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    prev[i] = 0;
+    home[i] = 0;
+    if (x.c[i] >= 0) {
+      home[i] = slot_of(x.c[i], lg);
+      unsigned long long *kp, *vp;
+      at(home[i], kp, vp);
+      prev[i] = atomicCAS(kp, SLOT_EMPTY, slot_word(x.c[i], x.k[i]));
+    }
+  }
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (x.c[i] < 0) continue;
+    if (prev[i] == SLOT_EMPTY || (int32_t)(uint32_t)prev[i] == x.c[i]) {
+      unsigned long long *kp, *vp;
+      at(home[i], kp, vp);
+      atomicAdd(vp, (unsigned long long)x.w[i]);
+    } else {
+      ok &= probe_insert(at, cap, lg, x.c[i], x.k[i], x.w[i]);
+    }
+  }
+  return ok;
+}
+
+// Scans table slots s0, s0 + step, ... < s1 of a vertex: best candidate, stay
+// weight, and whether cluster id v occurs.
 template <typename S>
+__device__ __forceinline__ void scan_slots(const JobView &J, const unsigned long long *keys,
+                                           const unsigned long long *vals, int64_t s0, int64_t s1,
+                                           int step, int32_t v, int32_t Lv, int64_t kv, S &best,
+                                           int32_t &bc, long long &w_stay, int &vseen,
+                                           long long &ncand) {
+  const S q = (S)J.q, pk = (S)J.p * (S)kv;
+  for (int64_t s = s0; s < s1; s += step) {
+    const unsigned long long word = keys[s];
+    if (word == SLOT_EMPTY) continue;
+    const int32_t c = (int32_t)(uint32_t)word;
+    const long long val = (long long)vals[s];
+    if (c == Lv) {
+      w_stay += val;
+      continue;
+    }
+    vseen |= (c == v);
+    ++ncand;
+    const S sc = q * (S)val - pk * (S)weight_of(J, c, (uint32_t)(word >> 32));
+    if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
+  }
+}
+
+// ----------------------------------- deg <= T_WARP: warp + shared table --
+
+template <typename S, int E, int BK>
 __global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs, Buckets b,
                                                  int64_t *ctr) {
   constexpr int WPB = 4;
-  __shared__ int32_t tkey[WPB][WARP_CAP];
-  __shared__ unsigned long long tval[WPB][WARP_CAP];
-  __shared__ unsigned long long acc[WPB][32];
+  constexpr int CAP = 64 * E;  // >= 2 * 32 * E
+  __shared__ unsigned long long tkey[WPB][CAP];
+  __shared__ unsigned long long tval[WPB][CAP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t count = seg_count(b, B_WARP);
-  const uint64_t *items = b.items + b.seg_start[B_WARP];
+  const int64_t count = seg_count(b, BK);
+  const uint64_t *items = b.items + b.seg_start[BK];
   const int64_t warps_total = (int64_t)gridDim.x * WPB;
   long long ncand = 0;
   bool fail = false;
+  unsigned long long *K0 = tkey[wib], *V0 = tval[wib];
+  auto at = [K0, V0](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
+    kp = K0 + s;
+    vp = V0 + s;
+  };
   for (int64_t it = (int64_t)blockIdx.x * WPB + wib; it < count; it += warps_total) {
     const uint64_t item = items[it];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
-    const int64_t beg = J->off[v];
-    const int deg = (int)(J->off[v + 1] - beg);
-    const int32_t Lv = J->L[v];
-    const int64_t kv = J->k[v];
+    const int64_t beg = J.off[v];
+    const int deg = (int)(J.off[v + 1] - beg);
+    Chunk<E> x;
+    load_chunk(J, beg, 0, deg, 32, lane, x);
+    const Own o = own_of(J, v);
     const int cap = (int)next_pow2(2 * (int64_t)deg);
     const int lg = log2i(cap);
     for (int s = lane; s < cap; s += 32) {
-      tkey[wib][s] = -1;
-      tval[wib][s] = 0;
+      K0[s] = SLOT_EMPTY;
+      V0[s] = 0;
     }
     __syncwarp();
-    for (int e0 = 0; e0 < deg; e0 += 32) {
-      const int e = e0 + lane;
-      const bool has = e < deg;
-      int32_t c = -1;
-      long long wt = 0;
-      if (has) {
-        c = J->L[__ldg(J->nbr + beg + e)];
-        wt = load_w(J->w, J->wtype, beg + e);
-      }
-      const unsigned peers = __match_any_sync(FULL, c);
-      const int leader = __ffs(peers) - 1;
-      acc[wib][lane] = 0;
-      __syncwarp();
-      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
-      __syncwarp();
-      if (has && lane == leader)
-        fail |= !table_insert(tkey[wib], tval[wib], cap, lg, c, (long long)acc[wib][lane]);
-      __syncwarp();
-    }
+    fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
+    __syncwarp();
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
-    long long w_stay = 0;
-    int vseen = 0, nc = 0;
-    for (int s = lane; s < cap; s += 32) {
-      const int32_t c = tkey[wib][s];
-      if (c < 0) continue;
-      const long long val = (long long)tval[wib][s];
-      if (c == Lv) { w_stay = val; continue; }
-      vseen |= (c == v);
-      ++nc;
-      const S sc = (S)J->q * (S)val - (S)J->p * (S)kv * (S)J->K[c];
-      if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
-    }
+    long long w_stay = 0, nc = 0;
+    int vseen = 0;
+    scan_slots<S>(J, K0, V0, lane, cap, 32, v, o.Lv, o.kv, best, bc, w_stay, vseen, nc);
     w_stay = warp_sum_ll(w_stay);
     const bool v_seen = __any_sync(FULL, vseen);
     ncand += nc;
     warp_argmax<S>(best, bc);
-    if (lane == 0) J->D[v] = decide<S>(J, v, Lv, kv, best, bc, w_stay, v_seen);
+    if (lane == 0) J.D[v] = decide<S>(J, v, o.Lv, o.kv, o.KLv, best, bc, w_stay, v_seen, o.Kv);
     __syncwarp();
   }
   ncand = warp_sum_ll(ncand);
@@ -311,78 +506,98 @@ __global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs
     atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
 }
 
-// ------------------------------ deg <= T_BLKx: block + shared table --------
+// --------------- deg <= 65536: one block or a cluster of CS blocks ---------
 
-template <typename S, int CAP, int THREADS, int BK>
-__global__ void __launch_bounds__(THREADS) k_bm_block(const JobDev *__restrict__ jobs, Buckets b,
-                                                      int64_t *ctr) {
+// One vertex per cluster at a time; block r reads entries [r * per,
+// (r + 1) * per) of the row (E per thread per batch).  The table has cap =
+// next_pow2(2 deg) slots:
+//   GM = false: spread evenly over the CS blocks' shared memory (cap / CS <=
+//               TP per block), inserted with distributed-shared-memory atomics;
+//   GM = true:  in a global-memory region private to the cluster, small
+//               enough that the tables of all clusters in flight stay in L2;
+//               cluster size then sets the parallelism per vertex only.
+// Each block scans its share of the slots and block 0 combines.
+template <typename S, int CS, int THREADS, int TP, int E, int BK, bool GM>
+__global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
+                                                      GTab gt, int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;
-  unsigned long long *tval = (unsigned long long *)smem;
-  int32_t *tkey = (int32_t *)(smem + (size_t)CAP * 8);
-  __shared__ unsigned long long acc[NW][32];
+  unsigned long long *tkey = (unsigned long long *)smem;
+  unsigned long long *tval = tkey + TP;
   __shared__ S red_s[NW];
   __shared__ int32_t red_c[NW];
   __shared__ long long red_w[NW];
   __shared__ int red_v[NW];
+  __shared__ S cl_s[CS];
+  __shared__ int32_t cl_c[CS];
+  __shared__ long long cl_w[CS];
+  __shared__ int cl_v[CS];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int64_t count = seg_count(b, BK);
   const uint64_t *items = b.items + b.seg_start[BK];
+  const int64_t ncl = gridDim.x / CS;
+  const int64_t cid = blockIdx.x / CS;
+  if (GM) {
+    tkey = gt.keys + cid * gt.stride;
+    tval = gt.vals + cid * gt.stride;
+  }
   long long ncand = 0;
   bool fail = false;
-  for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+  for (int64_t it = cid; it < count; it += ncl) {
     const uint64_t item = items[it];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
-    const int64_t beg = J->off[v];
-    const int deg = (int)(J->off[v + 1] - beg);
-    const int32_t Lv = J->L[v];
-    const int64_t kv = J->k[v];
-    int cap = (int)next_pow2(2 * (int64_t)deg);
-    if (cap > CAP) cap = CAP;
-    const int lg = log2i(cap);
-    for (int s = tid; s < cap; s += THREADS) {
-      tkey[s] = -1;
-      tval[s] = 0;
+    const int64_t beg = J.off[v];
+    const int64_t deg = J.off[v + 1] - beg;
+    const int64_t per = (deg + CS - 1) / CS;
+    const int64_t lo = (int64_t)rank * per;
+    const int64_t hi = lo + per < deg ? lo + per : deg;
+    Chunk<E> x;
+    load_chunk(J, beg, lo, hi, THREADS, tid, x);
+    const Own o = own_of(J, v);
+    int64_t capl = next_pow2(2 * deg);
+    if (capl < 2 * CS) capl = 2 * CS;
+    const uint32_t cap = (uint32_t)capl;
+    const int lg = log2i(capl);
+    const uint32_t part = cap / CS;  // slots per block (a power of two)
+    const int plg = log2i(part);
+    // block r clears (and later scans) slots [r * part, (r + 1) * part)
+    unsigned long long *mk = GM ? tkey + (size_t)rank * part : tkey;
+    unsigned long long *mv = GM ? tval + (size_t)rank * part : tval;
+    for (uint32_t s = tid; s < part; s += THREADS) {
+      mk[s] = SLOT_EMPTY;
+      mv[s] = 0;
     }
-    __syncthreads();
-    for (int e0 = 0; e0 < deg; e0 += THREADS) {
-      const int e = e0 + tid;
-      const bool has = e < deg;
-      int32_t c = -1;
-      long long wt = 0;
-      if (has) {
-        c = J->L[__ldg(J->nbr + beg + e)];
-        wt = load_w(J->w, J->wtype, beg + e);
+    if (CS > 1) cluster.sync(); else __syncthreads();
+    auto at = [&](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
+      if (GM || CS == 1) {
+        kp = tkey + s;
+        vp = tval + s;
+      } else {
+        const unsigned r = s >> plg, l = s & (part - 1);
+        kp = cluster.map_shared_rank(tkey, r) + l;
+        vp = cluster.map_shared_rank(tval, r) + l;
       }
-      const unsigned peers = __match_any_sync(FULL, c);
-      const int leader = __ffs(peers) - 1;
-      acc[wib][lane] = 0;
-      __syncwarp();
-      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
-      __syncwarp();
-      if (has && lane == leader)
-        fail |= !table_insert(tkey, tval, cap, lg, c, (long long)acc[wib][lane]);
-      __syncwarp();
+    };
+    fail |= !insert_chunk(x, at, cap, lg);
+    for (int64_t more = lo + (int64_t)THREADS * E; more < hi; more += (int64_t)THREADS * E) {
+      load_chunk(J, beg, more, hi, THREADS, tid, x);
+      fail |= !insert_chunk(x, at, cap, lg);
     }
-    __syncthreads();
+    if (CS > 1) cluster.sync(); else __syncthreads();
+    const int32_t Lv = o.Lv;
+    const int64_t kv = o.kv;
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
-    long long w_stay = 0;
-    int vseen = 0, nc = 0;
-    for (int s = tid; s < cap; s += THREADS) {
-      const int32_t c = tkey[s];
-      if (c < 0) continue;
-      const long long val = (long long)tval[s];
-      if (c == Lv) { w_stay = val; continue; }
-      vseen |= (c == v);
-      ++nc;
-      const S sc = (S)J->q * (S)val - (S)J->p * (S)kv * (S)J->K[c];
-      if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
-    }
+    long long w_stay = 0, nc = 0;
+    int vseen = 0;
+    scan_slots<S>(J, mk, mv, tid, (int64_t)part, THREADS, v, Lv, kv, best, bc, w_stay, vseen,
+                  nc);
+    ncand += nc;
     w_stay = warp_sum_ll(w_stay);
     const int vs = __any_sync(FULL, vseen);
-    ncand += nc;
     warp_argmax<S>(best, bc);
     if (lane == 0) {
       red_s[wib] = best;
@@ -398,10 +613,35 @@ __global__ void __launch_bounds__(THREADS) k_bm_block(const JobDev *__restrict__
       int vv = lane < NW ? red_v[lane] : 0;
       warp_argmax<S>(bs, bcc);
       ws = warp_sum_ll(ws);
-      const bool vseen_all = __any_sync(FULL, vv);
-      if (lane == 0) J->D[v] = decide<S>(J, v, Lv, kv, bs, bcc, ws, vseen_all);
+      const int vall = __any_sync(FULL, vv);
+      if (lane == 0) {
+        if (CS == 1) {
+          J.D[v] = decide<S>(J, v, Lv, kv, o.KLv, bs, bcc, ws, vall != 0, o.Kv);
+        } else {
+          *cluster.map_shared_rank(&cl_s[rank], 0) = bs;
+          *cluster.map_shared_rank(&cl_c[rank], 0) = bcc;
+          *cluster.map_shared_rank(&cl_w[rank], 0) = ws;
+          *cluster.map_shared_rank(&cl_v[rank], 0) = vall;
+        }
+      }
     }
-    __syncthreads();
+    if (CS > 1) {
+      cluster.sync();
+      if (rank == 0 && tid == 0) {
+        S bs = cl_s[0];
+        int32_t bcc = cl_c[0];
+        long long ws = cl_w[0];
+        int vall = cl_v[0];
+        for (int r = 1; r < CS; ++r) {
+          if (better<S>(cl_s[r], cl_c[r], bs, bcc)) { bs = cl_s[r]; bcc = cl_c[r]; }
+          ws += cl_w[r];
+          vall |= cl_v[r];
+        }
+        J.D[v] = decide<S>(J, v, Lv, kv, o.KLv, bs, bcc, ws, vall != 0, o.Kv);
+      }
+    } else {
+      __syncthreads();
+    }
   }
   ncand = warp_sum_ll(ncand);
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
@@ -501,15 +741,14 @@ __global__ void k_hub_clear(HubBufs h, const int64_t *ctr, int64_t lo) {
   const int64_t s0 = h.tbl_off[h0] - lo, s1 = h.tbl_off[h1] - lo;
   for (int64_t i = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s1;
        i += (int64_t)gridDim.x * blockDim.x) {
-    h.keys[i] = -1;
+    h.keys[i] = SLOT_EMPTY;
     h.vals[i] = 0;
   }
 }
 
 __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ jobs, Buckets b,
                                                     HubBufs h, int64_t *ctr, int64_t lo) {
-  __shared__ unsigned long long acc[8][32];
-  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int64_t H = ctr[C_HUBS];
   if (H == 0) return;
   const int64_t h0 = hub_lower(h.tbl_off, H, lo);
@@ -521,49 +760,24 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
   for (int64_t u = U0 + blockIdx.x; u < U1; u += gridDim.x) {
     const int hh = find_seg(h.unit_off, H, u);
     const uint64_t item = items[hh];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
-    const int64_t beg = J->off[v];
-    const int64_t deg = J->off[v + 1] - beg;
+    const int64_t beg = J.off[v];
+    const int64_t deg = J.off[v + 1] - beg;
     const int64_t cap = hub_cap(deg);
     const int lg = log2i(cap);
-    int32_t *tkey = h.keys + (h.tbl_off[hh] - lo);
+    unsigned long long *tkey = h.keys + (h.tbl_off[hh] - lo);
     unsigned long long *tval = (unsigned long long *)(h.vals + (h.tbl_off[hh] - lo));
+    auto at = [tkey, tval](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
+      kp = tkey + s;
+      vp = tval + s;
+    };
     const int64_t e_lo = (u - h.unit_off[hh]) * HUB_CHUNK;
     int64_t e_hi = e_lo + HUB_CHUNK;
     if (e_hi > deg) e_hi = deg;
-    for (int64_t e0 = e_lo; e0 < e_hi; e0 += 256) {
-      const int64_t e = e0 + tid;
-      const bool has = e < e_hi;
-      int32_t c = -1;
-      long long wt = 0;
-      if (has) {
-        c = J->L[__ldg(J->nbr + beg + e)];
-        wt = load_w(J->w, J->wtype, beg + e);
-      }
-      const unsigned peers = __match_any_sync(FULL, c);
-      const int leader = __ffs(peers) - 1;
-      acc[wib][lane] = 0;
-      __syncwarp();
-      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
-      __syncwarp();
-      if (has && lane == leader) {
-        const long long sum = (long long)acc[wib][lane];
-        uint64_t s = slot_of(c, lg);
-        bool done = false;
-        for (int64_t t = 0; t < cap; ++t) {
-          const int32_t prev = atomicCAS(tkey + s, -1, c);
-          if (prev == -1 || prev == c) {
-            atomicAdd(tval + s, (unsigned long long)sum);
-            done = true;
-            break;
-          }
-          s = (s + 1) & (uint64_t)(cap - 1);
-        }
-        fail |= !done;
-      }
-      __syncwarp();
-    }
+    Chunk<HUB_CHUNK / 256> x;
+    load_chunk(J, beg, e_lo, e_hi, 256, tid, x);
+    fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
   }
   if (__any_sync(FULL, fail) && lane == 0)
     atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
@@ -586,29 +800,25 @@ __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jo
   for (int64_t su = SU0 + blockIdx.x; su < SU1; su += gridDim.x) {
     const int hh = find_seg(h.sunit_off, H, su);
     const uint64_t item = items[hh];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
-    const int64_t deg = J->off[v + 1] - J->off[v];
+    const int64_t deg = J.off[v + 1] - J.off[v];
     const int64_t cap = hub_cap(deg);
-    const int32_t Lv = J->L[v];
-    const int64_t kv = J->k[v];
-    const int32_t *tkey = h.keys + (h.tbl_off[hh] - lo);
-    const int64_t *tval = h.vals + (h.tbl_off[hh] - lo);
+    const int32_t Lv = J.L[v];
+    const int64_t kv = J.k[v];
+    const unsigned long long *tkey = h.keys + (h.tbl_off[hh] - lo);
+    const unsigned long long *tval = (const unsigned long long *)(h.vals + (h.tbl_off[hh] - lo));
     const int64_t s_lo = (su - h.sunit_off[hh]) * HUB_SCHUNK;
     int64_t s_hi = s_lo + HUB_SCHUNK;
     if (s_hi > cap) s_hi = cap;
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
-    for (int64_t s = s_lo + tid; s < s_hi; s += 256) {
-      const int32_t c = tkey[s];
-      if (c < 0) continue;
-      const long long val = tval[s];
-      if (c == Lv) { h.stay[hh] = val; continue; }
-      if (c == v) h.iso_seen[hh] = 1;
-      ++ncand;
-      const S sc = (S)J->q * (S)val - (S)J->p * (S)kv * (S)J->K[c];
-      if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
-    }
+    long long w_stay = 0;
+    int vseen = 0;
+    scan_slots<S>(J, tkey, tval, s_lo + tid, s_hi, 256, v, Lv, kv, best, bc, w_stay, vseen,
+                  ncand);
+    if (w_stay) atomicAdd((unsigned long long *)&h.stay[hh], (unsigned long long)w_stay);
+    if (vseen) h.iso_seen[hh] = 1;
     warp_argmax<S>(best, bc);
     if (lane == 0) { red_s[wib] = best; red_c[wib] = bc; }
     __syncthreads();
@@ -637,7 +847,7 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
   for (int64_t hh = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); hh < H;
        hh += warps_total) {
     const uint64_t item = items[hh];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
@@ -647,9 +857,11 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
       if (better<S>(s, c, best, bc)) { best = s; bc = c; }
     }
     warp_argmax<S>(best, bc);
-    if (lane == 0)
-      J->D[v] = decide<S>(J, v, J->L[v], J->k[v], best, bc, (long long)h.stay[hh],
-                          h.iso_seen[hh] != 0);
+    if (lane == 0) {
+      const int32_t Lv = J.L[v];
+      J.D[v] = decide<S>(J, v, Lv, J.k[v], own_weight(J, v, Lv), best, bc,
+                          (long long)h.stay[hh], h.iso_seen[hh] != 0);
+    }
   }
 }
 
@@ -663,30 +875,73 @@ int occ_blocks(K kernel, int threads, size_t smem) {
   return nb > 0 ? nb : 1;
 }
 
+struct TableLaunch {
+  int clusters = 0;  // clusters resident at once
+  bool init = false;
+};
+
+template <typename S, int CS, int THREADS, int TP, int E, int BK, bool GM>
+void launch_table(const JobDev *jobs, const Buckets &b, const GTab &gt, int64_t *ctr,
+                  cudaStream_t st, TableLaunch &tl, int *launches, int64_t maxdeg) {
+  auto kern = k_bm_table<S, CS, THREADS, TP, E, BK, GM>;
+  const size_t smem = GM ? 0 : (size_t)TP * 16;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (!tl.init) {
+    if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cfg.gridDim = dim3(CS);
+    int ncl = 0;
+    cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+    tl.clusters = ncl > 0 ? ncl : 1;
+    tl.init = true;
+  }
+  int64_t ncl = tl.clusters;
+  GTab g2 = gt;
+  if (GM) {  // one table region per cluster; all of them within the L2 budget
+    g2.stride = next_pow2(2 * maxdeg);
+    const int64_t by_l2 = gt.stride / g2.stride;
+    if (by_l2 < ncl) ncl = by_l2 > 0 ? by_l2 : 1;
+  }
+  if (b.seg_cap[BK] < ncl) ncl = b.seg_cap[BK];
+  cfg.gridDim = dim3((unsigned)(ncl * CS));
+  cudaLaunchKernelEx(&cfg, kern, jobs, b, g2, ctr);
+  ++*launches;
+}
+
 template <typename S>
-void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes,
-                   int64_t *ctr, cudaStream_t st, const Dev &d, int *launches) {
-  static int occ[16] = {0};
+void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, const GTab &gt,
+                   int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d, int *launches,
+                   cudaEvent_t *ev) {
+  auto mark = [&](int bk) {
+    if (ev) cudaEventRecord(ev[bk], st);
+  };
+  static int occ[10] = {0};
   static bool init = false;
-  const size_t smem1 = (size_t)BLK1_CAP * 12, smem2 = (size_t)BLK2_CAP * 12;
+  static TableLaunch tl[6];
   if (!init) {
-    cudaFuncSetAttribute(k_bm_block<S, BLK1_CAP, 256, B_BLK1>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-    cudaFuncSetAttribute(k_bm_block<S, BLK2_CAP, 512, B_BLK2>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     occ[0] = occ_blocks(k_bm_group<4, S>, 256, 0);
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
     occ[2] = occ_blocks(k_bm_group<16, S>, 256, 0);
     occ[3] = occ_blocks(k_bm_group<32, S>, 256, 0);
-    occ[4] = occ_blocks(k_bm_warp<S>, 128, 0);
-    occ[5] = occ_blocks(k_bm_block<S, BLK1_CAP, 256, B_BLK1>, 256, smem1);
-    occ[6] = occ_blocks(k_bm_block<S, BLK2_CAP, 512, B_BLK2>, 512, smem2);
-    occ[7] = occ_blocks(k_hub_insert, 256, 0);
-    occ[8] = occ_blocks(k_hub_score<S>, 256, 0);
+    occ[4] = occ_blocks(k_bm_warp<S, 8, B_WARP>, 128, 0);
+    occ[7] = occ_blocks(k_bm_warp<S, 2, B_W64>, 128, 0);
+    occ[8] = occ_blocks(k_bm_warp<S, 4, B_W128>, 128, 0);
+    occ[5] = occ_blocks(k_hub_insert, 256, 0);
+    occ[6] = occ_blocks(k_hub_score<S>, 256, 0);
     init = true;
   }
   auto grid = [&](int bk, int o, int per_block) {
-    int64_t need = (b.seg_cap[bk] + per_block - 1) / per_block;
+    const int64_t need = (b.seg_cap[bk] + per_block - 1) / per_block;
     int64_t g = (int64_t)d.sms * o;
     if (need < g) g = need;
     return (int)(g > 0 ? g : 1);
@@ -695,37 +950,67 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     k_bm_group<4, S><<<grid(B_G4, occ[0], 64), 256, 0, st>>>(jobs, b, B_G4, ctr);
     ++*launches;
   }
+  mark(B_G4);
   if (b.seg_cap[B_G8] > 0) {
     k_bm_group<8, S><<<grid(B_G8, occ[1], 32), 256, 0, st>>>(jobs, b, B_G8, ctr);
     ++*launches;
   }
+  mark(B_G8);
   if (b.seg_cap[B_G16] > 0) {
     k_bm_group<16, S><<<grid(B_G16, occ[2], 16), 256, 0, st>>>(jobs, b, B_G16, ctr);
     ++*launches;
   }
+  mark(B_G16);
   if (b.seg_cap[B_G32] > 0) {
     k_bm_group<32, S><<<grid(B_G32, occ[3], 8), 256, 0, st>>>(jobs, b, B_G32, ctr);
     ++*launches;
   }
+  mark(B_G32);
+  if (b.seg_cap[B_W64] > 0) {
+    k_bm_warp<S, 2, B_W64><<<grid(B_W64, occ[7], 4), 128, 0, st>>>(jobs, b, ctr);
+    ++*launches;
+  }
+  mark(B_W64);
+  if (b.seg_cap[B_W128] > 0) {
+    k_bm_warp<S, 4, B_W128><<<grid(B_W128, occ[8], 4), 128, 0, st>>>(jobs, b, ctr);
+    ++*launches;
+  }
+  mark(B_W128);
   if (b.seg_cap[B_WARP] > 0) {
-    k_bm_warp<S><<<grid(B_WARP, occ[4], 4), 128, 0, st>>>(jobs, b, ctr);
+    k_bm_warp<S, 8, B_WARP><<<grid(B_WARP, occ[4], 4), 128, 0, st>>>(jobs, b, ctr);
     ++*launches;
   }
-  if (b.seg_cap[B_BLK1] > 0) {
-    k_bm_block<S, BLK1_CAP, 256, B_BLK1><<<grid(B_BLK1, occ[5], 1), 256, smem1, st>>>(jobs, b, ctr);
-    ++*launches;
-  }
-  if (b.seg_cap[B_BLK2] > 0) {
-    k_bm_block<S, BLK2_CAP, 512, B_BLK2><<<grid(B_BLK2, occ[6], 1), 512, smem2, st>>>(jobs, b, ctr);
-    ++*launches;
-  }
+  mark(B_WARP);
+  if (b.seg_cap[B_BLK] > 0)
+    launch_table<S, 1, 256, BLK_CAP, T_BLK / 256, B_BLK, false>(jobs, b, gt, ctr, st, tl[0],
+                                                                 launches, T_BLK);
+  mark(B_BLK);
+  if (b.seg_cap[B_C1] > 0)
+    launch_table<S, 1, 1024, PART, 4, B_C1, false>(jobs, b, gt, ctr, st, tl[1], launches, T_C1);
+  mark(B_C1);
+  if (b.seg_cap[B_C2] > 0)
+    launch_table<S, 2, 1024, PART, 4, B_C2, false>(jobs, b, gt, ctr, st, tl[2], launches,
+                                                   2 * T_C1);
+  mark(B_C2);
+  if (b.seg_cap[B_C4] > 0)
+    launch_table<S, 4, 1024, PART, 4, B_C4, false>(jobs, b, gt, ctr, st, tl[3], launches,
+                                                   4 * T_C1);
+  mark(B_C4);
+  if (b.seg_cap[B_C8] > 0)
+    launch_table<S, 8, 1024, PART, 4, B_C8, false>(jobs, b, gt, ctr, st, tl[4], launches,
+                                                   8 * T_C1);
+  mark(B_C8);
+  if (b.seg_cap[B_C16] > 0)
+    launch_table<S, 16, 1024, PART, 4, B_C16, false>(jobs, b, gt, ctr, st, tl[5], launches,
+                                                     16 * T_C1);
+  mark(B_C16);
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
     for (int64_t p = 0; p < hub_passes; ++p) {
       const int64_t lo = p * h.window;
       k_hub_clear<<<d.sms * 8, 256, 0, st>>>(h, ctr, lo);
-      k_hub_insert<<<d.sms * occ[7], 256, 0, st>>>(jobs, b, h, ctr, lo);
-      k_hub_score<S><<<d.sms * occ[8], 256, 0, st>>>(jobs, b, h, ctr, lo);
+      k_hub_insert<<<d.sms * occ[5], 256, 0, st>>>(jobs, b, h, ctr, lo);
+      k_hub_score<S><<<d.sms * occ[6], 256, 0, st>>>(jobs, b, h, ctr, lo);
       *launches += 3;
     }
     int64_t fg = (b.seg_cap[B_HUB] + 7) / 8;
@@ -733,16 +1018,17 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     k_hub_final<S><<<(int)(fg > 0 ? fg : 1), 256, 0, st>>>(jobs, b, h, ctr);
     *launches += 2;
   }
+  mark(B_HUB);
 }
 }  // namespace
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches) {
+                     const GTab &gt, int64_t hub_passes, int64_t *ctr, cudaStream_t st,
+                     const Dev &d, int *launches, cudaEvent_t *ev) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches);
+    bestmove_impl<i128>(jobs, b, h, gt, hub_passes, ctr, st, d, launches, ev);
   else
-    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches);
+    bestmove_impl<int64_t>(jobs, b, h, gt, hub_passes, ctr, st, d, launches, ev);
 }
 
 // --------------------------------------------------------------- apply ----

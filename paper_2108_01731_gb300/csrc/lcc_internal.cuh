@@ -30,25 +30,32 @@ enum : int32_t {
   JF_EVAL_ONLY = 8  // compute D only (no apply)
 };
 
-// Degree buckets of the best-move kernels.
+// Degree buckets of the best-move kernels.  Every hash table holds at least
+// two slots per entry of the row, so a row of d entries needs 2d slots.
 enum Bucket : int {
-  B_G4 = 0,   // deg <= 4: 4 lanes per vertex
-  B_G8 = 1,   // deg <= 8
-  B_G16 = 2,  // deg <= 16
-  B_G32 = 3,  // deg <= 32: one warp, register aggregation
-  B_WARP = 4, // deg <= T_WARP: one warp, shared-memory hash table
-  B_BLK1 = 5, // deg <= T_BLK1: one block, shared-memory hash table
-  B_BLK2 = 6, // deg <= T_BLK2: one block, larger shared-memory table
-  B_HUB = 7,  // larger: global-memory hash table, many blocks per vertex
-  NB = 8
+  B_G4 = 0,    // deg <= 4: 4 lanes per vertex, register aggregation
+  B_G8 = 1,    // deg <= 8
+  B_G16 = 2,   // deg <= 16
+  B_G32 = 3,   // deg <= 32: one warp
+  B_W64 = 4,   // deg <= 64: one warp, shared-memory table, 2 entries per lane
+  B_W128 = 5,  // deg <= 128: 4 entries per lane
+  B_WARP = 6,  // deg <= 256: 8 entries per lane
+  B_BLK = 7,   // deg <= 1024: one 256-thread block, shared-memory table
+  B_C1 = 8,    // deg <= 4096: one 1024-thread block, 8192-slot table
+  B_C2 = 9,    // deg <= 8192: cluster of 2 blocks, table in distributed shared memory
+  B_C4 = 10,   // deg <= 16384: cluster of 4
+  B_C8 = 11,   // deg <= 32768: cluster of 8
+  B_C16 = 12,  // deg <= 65536: cluster of 16
+  B_HUB = 13,  // larger: global-memory table, many blocks per vertex
+  NB = 14
 };
 constexpr int T_WARP = 256;
-constexpr int T_BLK1 = 1024;
-constexpr int T_BLK2 = 4096;
-constexpr int WARP_CAP = 512;    // slots per warp table (>= 2 * T_WARP)
-constexpr int BLK1_CAP = 2048;   // >= 2 * T_BLK1
-constexpr int BLK2_CAP = 8192;   // >= 2 * T_BLK2
-constexpr int HUB_CHUNK = 4096;  // edges per insertion unit
+constexpr int T_BLK = 1024;
+constexpr int PART = 8192;       // table slots per block of the cluster kernels
+constexpr int T_C1 = PART / 2;   // rows up to PART/2 * cluster size
+constexpr int WARP_CAP = 512;    // >= 2 * T_WARP
+constexpr int BLK_CAP = 2048;    // >= 2 * T_BLK
+constexpr int HUB_CHUNK = 2048;  // edges per insertion unit
 constexpr int HUB_SCHUNK = 4096; // table slots per scoring unit
 
 __host__ __device__ inline int bucket_of(int64_t deg) {
@@ -56,11 +63,23 @@ __host__ __device__ inline int bucket_of(int64_t deg) {
   if (deg <= 8) return B_G8;
   if (deg <= 16) return B_G16;
   if (deg <= 32) return B_G32;
+  if (deg <= 64) return B_W64;
+  if (deg <= 128) return B_W128;
   if (deg <= T_WARP) return B_WARP;
-  if (deg <= T_BLK1) return B_BLK1;
-  if (deg <= T_BLK2) return B_BLK2;
+  if (deg <= T_BLK) return B_BLK;
+  if (deg <= T_C1) return B_C1;
+  if (deg <= 2 * T_C1) return B_C2;
+  if (deg <= 4 * T_C1) return B_C4;
+  if (deg <= 8 * T_C1) return B_C8;
+  if (deg <= 16 * T_C1) return B_C16;
   return B_HUB;
 }
+
+// A hash-table slot is a 64-bit word (cluster id in the low half, the
+// cluster's weight K in the high half, or KNONE when the level's weights do
+// not fit 32 bits) plus a 64-bit sum of edge weights.
+constexpr uint32_t KNONE = 0xFFFFFFFFu;
+constexpr unsigned long long SLOT_EMPTY = ~0ull;
 
 __host__ __device__ inline int64_t next_pow2(int64_t x) {
   int64_t p = 1;
@@ -82,6 +101,8 @@ struct JobDev {
   int32_t *D;
   uint8_t *fr;
   uint8_t *cl;
+  // per round: lk[u] = K[L[u]] << 32 | L[u]; null when K can reach 2^32 - 1
+  unsigned long long *lk;
   int64_t n;
   int64_t p, q;
   int32_t wtype;
@@ -98,7 +119,9 @@ enum Ctr : int {
   C_MOVED_N = 5,  // entries in the moved list
   C_HUBS = 6,     // hubs handled this round
   C_WB = 7,       // sum of deg * (bytes per stored weight) over evaluated vertices
-  NCTR = 8
+  C_BE = 8,       // [NB] entries per degree bucket
+  C_BV = 8 + NB,  // [NB] vertices per degree bucket
+  NCTR = 8 + 2 * NB
 };
 enum Err : int64_t {
   E_BUCKET_OVERFLOW = 1,
@@ -112,11 +135,21 @@ struct Buckets {
   uint64_t *items;
   int64_t seg_start[NB];
   int64_t seg_cap[NB];
-  int64_t *cnt;  // [NB] device counters
+  int64_t *cnt;       // [NB] device counters
 };
 
+// Global-memory tables of the cluster kernels: cluster i of a launch owns
+// slots [i * stride, (i + 1) * stride) of keys and of vals.
+struct GTab {
+  unsigned long long *keys;
+  unsigned long long *vals;
+  int64_t stride;
+};
+// Table bytes the cluster kernels keep live at once (sized to stay in L2).
+constexpr int64_t GTAB_BYTES = (int64_t)64 << 20;
+
 struct HubBufs {
-  int32_t *keys;      // one window of tables: [window + largest table] slots
+  unsigned long long *keys;  // one window of tables: [window + largest table] slots
   int64_t *vals;
   int64_t window;     // hubs whose table starts in [lo, lo + window) share a pass
   int64_t *tbl_off;   // [max_hubs + 1]
@@ -255,9 +288,10 @@ struct Dev {
 // Round kernels (k_round.cu).
 void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
+// ev (nullable, NB events): ev[b] is recorded after degree bucket b's kernels.
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches);
+                     const GTab &gt, int64_t hub_passes, int64_t *ctr, cudaStream_t st,
+                     const Dev &d, int *launches, cudaEvent_t *ev);
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
 void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, bool any_cl,
@@ -303,6 +337,7 @@ void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, in
 // tmp must hold scan_tmp_elems(n) int64.
 int64_t scan_tmp_elems(int64_t n);
 void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, const Dev &d);
+
 // LSD radix sort of (key, val) pairs on the given 8-bit digit positions.
 int64_t radix_tmp_elems(int64_t n, int npasses);
 void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,

@@ -320,14 +320,17 @@ def random_signed_graph(n, p_edge, w_lo, w_hi, seed, device="cpu"):
 
 def hub_graph(n, mean_deg, hubs, hub_deg, seed, device="cpu", w_lo=None, w_hi=None):
     """Sparse random graph plus `hubs` vertices joined to hub_deg random others
-    each, so that every degree bucket (including rows above a few thousand
-    entries) is populated.  Optional integer weights uniform in [w_lo, w_hi]."""
+    each (hub_deg may be a list, one draw count per hub), so that every degree
+    bucket (including rows of tens of thousands of entries) is populated.
+    Optional integer weights uniform in [w_lo, w_hi]."""
     gen = _gen(seed, device)
     m = int(n * mean_deg // 2)
     u = torch.randint(0, n, (m,), generator=gen, device=device)
     v = torch.randint(0, n, (m,), generator=gen, device=device)
-    hu = torch.arange(hubs, device=device).repeat_interleave(hub_deg)
-    hv = torch.randint(0, n, (hubs * hub_deg,), generator=gen, device=device)
+    degs = list(hub_deg) if isinstance(hub_deg, (list, tuple)) else [hub_deg] * hubs
+    hu = torch.repeat_interleave(torch.arange(len(degs), device=device),
+                                 torch.tensor(degs, device=device))
+    hv = torch.randint(0, n, (int(sum(degs)),), generator=gen, device=device)
     a, b = canonical_unique(torch.cat([u, hu]), torch.cat([v, hv]), n)
     a, b, _ = permute_ids(a, b, n, gen)
     a2, b2 = torch.minimum(a, b), torch.maximum(a, b)

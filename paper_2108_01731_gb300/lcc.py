@@ -45,7 +45,9 @@ class lcc_stats(C.Structure):
                 ("ms_bestmove", C.c_double), ("ms_round_other", C.c_double),
                 ("ms_contract", C.c_double), ("ms_other", C.c_double),
                 ("ms_total", C.c_double), ("bytes_bestmove", C.c_int64),
-                ("pairs_sorted", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("pairs_sorted", C.c_int64), ("kernel_launches", C.c_int64),
+                ("ms_bucket", C.c_double * 16), ("bucket_entries", C.c_int64 * 16),
+                ("bucket_vertices", C.c_int64 * 16)]
 
 
 class lcc_server_cfg(C.Structure):
@@ -198,6 +200,9 @@ def lcc_free_graph(g):
 
 def _stats_dict(s):
     d = {f: getattr(s, f) for f, _ in lcc_stats._fields_}
+    d["ms_bucket"] = list(d["ms_bucket"])
+    d["bucket_entries"] = list(d["bucket_entries"])
+    d["bucket_vertices"] = list(d["bucket_vertices"])
     num = (d["obj_num_hi"] << 64) | d["obj_num_lo"]
     if num >= 1 << 127:
         num -= 1 << 128

@@ -39,5 +39,5 @@ def test_binding_covers_header():
 def test_struct_layouts_match_header_sizes():
     from paper_2108_01731_gb300 import lcc
     assert ctypes.sizeof(lcc.lcc_schedule) == 24
-    assert ctypes.sizeof(lcc.lcc_stats) == 4 * 2 + 8 * 7 + 8 * 6 + 8 * 3
+    assert ctypes.sizeof(lcc.lcc_stats) == 4 * 2 + 8 * 7 + 8 * 6 + 8 * 3 + 8 * 16 * 3
     assert ctypes.sizeof(lcc.lcc_job) == 8 * 7 + 8

@@ -31,6 +31,8 @@ def graphs():
         "cl": I.to_numpy(I.chung_lu(30000, 2.1, 12, seed=4)),
         "rmat": I.to_numpy(I.rmat(14, 120000, seed=5)),
         "signed": I.to_numpy(I.random_signed_graph(300, 0.1, -4, 6, seed=6)),
+        "giant": I.to_numpy(I.hub_graph(150000, 5, 0, [5000, 12000, 25000, 50000, 100000],
+                                        seed=7, w_lo=1, w_hi=3)),
     }
 
 
@@ -85,7 +87,7 @@ def test_desired_matches_oracle(L, name, mode):
 
 
 @pytest.mark.parametrize("vset", [O.VSET_ALL, O.VSET_NBR_VERTICES, O.VSET_NBR_CLUSTERS])
-@pytest.mark.parametrize("name", ["sbm", "hubs", "rmat"])
+@pytest.mark.parametrize("name", ["sbm", "hubs", "rmat", "giant"])
 def test_best_moves_rounds_match_oracle(L, name, vset):
     g = GRAPHS[name]
     n = g["n"]
@@ -148,6 +150,8 @@ CLUSTER_CASES = [
     ("rmat", O.NODEW_DEGREE, 1, 1, {}),
     ("rmat", O.NODEW_DEGREE, 1 << 40, 3, {}),
     ("signed", O.NODEW_UNIT, 1, 10, {"num_iter": 20}),
+    ("giant", O.NODEW_DEGREE, 1, 1, {}),
+    ("giant", O.NODEW_UNIT, 1, 4, {"vset": O.VSET_ALL}),
 ]
 
 

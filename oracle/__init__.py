@@ -42,6 +42,7 @@ def lib():
         _lib.orc_sequential_sweep.argtypes = [I64, P, P, P, P, I64, I64, P, I64]
         _lib.orc_sequential_sweep.restype = I64
         _lib.orc_weighted_degrees_i32.argtypes = [I64, P, P, P]
+        _lib.orc_desired_list.argtypes = [I64, I64, P, P, P, P, P, I64, I64, P, P, P]
         _lib.orc_weighted_degrees_i32.restype = I64
     return _lib
 
@@ -117,6 +118,23 @@ def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K):
                                  p, q, _p(L), _p(K), _p(D))
     if rc:
         raise ValueError("oracle desired failed: %d" % rc)
+    return D
+
+
+def desired_list(n, verts, off_l, nbr_l, w_l, k, p, q, L, K):
+    """Desired cluster of each listed vertex; its rows given as a compact CSR."""
+    verts = _c(verts, np.int64)
+    off_l = _c(off_l, np.int64)
+    nbr_l = _c(nbr_l, np.int32)
+    w_l = np.ones(len(nbr_l), np.int64) if w_l is None else _c(w_l, np.int64)
+    k = _c(k, np.int64)
+    L = _c(L, np.int32)
+    K = _c(K, np.int64)
+    D = np.empty(len(verts), np.int32)
+    rc = lib().orc_desired_list(n, len(verts), _p(verts), _p(off_l), _p(nbr_l), _p(w_l), _p(k),
+                                p, q, _p(L), _p(K), _p(D))
+    if rc:
+        raise ValueError("oracle desired_list failed: %d" % rc)
     return D
 
 

@@ -563,3 +563,23 @@ int64_t orc_weighted_degrees_i32(int64_t n, const int64_t *off,
   }
   return total;
 }
+
+/* Desired cluster of each vertex in a list (verts[0..nv)), whose rows are
+ * given as a compact CSR: row i is nbr_l[off_l[i] .. off_l[i+1]).  Same rule
+ * as orc_desired_range; used to check samples of very large graphs. */
+int orc_desired_list(int64_t n, int64_t nv, const int64_t *verts,
+                     const int64_t *off_l, const int32_t *nbr_l,
+                     const int64_t *w_l, const int64_t *k, int64_t p,
+                     int64_t q, const int32_t *L, const int64_t *K,
+                     int32_t *D) {
+  if (nv < 0 || q <= 0 || p < 0) return ORC_ERR_INVALID;
+  scratch_t s;
+  if (scratch_init(&s, n) != ORC_OK) { scratch_free(&s); return ORC_ERR_OOM; }
+  for (int64_t i = 0; i < nv; ++i) {
+    if (verts[i] < 0 || verts[i] >= n) { scratch_free(&s); return ORC_ERR_INVALID; }
+    D[i] = desired_cluster(verts[i], off_l[i], off_l[i + 1], nbr_l, w_l, k, p,
+                           q, L, K, &s);
+  }
+  scratch_free(&s);
+  return ORC_OK;
+}

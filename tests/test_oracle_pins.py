@@ -454,3 +454,21 @@ def test_weighted_degrees_match_numpy():
         assert np.array_equal(k, want) and tot == int(want.sum())
         k1, t1 = O.weighted_degrees(g["off"], None)
         assert np.array_equal(k1, np.diff(g["off"])) and t1 == g["nnz"]
+
+
+def test_desired_list_equals_range():
+    g = I.to_numpy(I.random_signed_graph(60, 0.2, -2, 5, 701))
+    n = g["n"]
+    rng = np.random.default_rng(3)
+    k = rng.integers(0, 4, n)
+    L = rng.integers(0, n, n).astype(np.int32)
+    K = np.zeros(n, np.int64)
+    np.add.at(K, L, k)
+    full = O.desired(g["off"], g["nbr"], g["w"], k, 1, 7, L, K)
+    verts = rng.permutation(n)[:25]
+    rows = [np.arange(g["off"][v], g["off"][v + 1]) for v in verts]
+    off_l = np.zeros(len(verts) + 1, np.int64)
+    off_l[1:] = np.cumsum([len(r) for r in rows])
+    idx = np.concatenate(rows)
+    D = O.desired_list(n, verts, off_l, g["nbr"][idx], g["w"][idx], k, 1, 7, L, K)
+    assert np.array_equal(D, full[verts])

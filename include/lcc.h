@@ -83,6 +83,13 @@ typedef enum lcc_memspace { LCC_MEM_HOST = 0, LCC_MEM_DEVICE = 1 } lcc_memspace;
 
 /* Schedule flags. */
 #define LCC_SCHED_TIMING 1 /* record per-phase device time in lcc_stats */
+/* With LCC_VSET_NBR_VERTICES, V' of the next round is by default found in one
+   of two ways with the same result on a symmetric graph: by marking the
+   neighbours of every moved vertex, or, after a round whose movers' rows hold
+   at least a quarter of the level's entries, by evaluating every vertex with
+   an edge and keeping the label of each one none of whose neighbours moved.
+   This flag always takes the first way. */
+#define LCC_SCHED_MARK_ONLY 2
 
 typedef struct lcc_schedule {
   int32_t num_iter;   /* max rounds per Best-Moves call (Algorithm 1); >= 0 */
@@ -118,8 +125,10 @@ typedef struct lcc_stats {
      entries, and longer; the last two elements are unused), filled when
      LCC_SCHED_TIMING is set */
   double ms_bucket[16];
-  int64_t bucket_entries[16];  /* entries scanned per degree bucket */
-  int64_t bucket_vertices[16]; /* vertices evaluated per degree bucket */
+  int64_t bucket_entries[16];  /* entries processed per degree bucket (after a
+                                  round that marks no V', every row with an
+                                  edge is processed) */
+  int64_t bucket_vertices[16]; /* vertices processed per degree bucket */
 } lcc_stats;
 
 typedef struct lcc_graph lcc_graph;

@@ -134,13 +134,13 @@ static lcc_graph *load_graph(const int64_t *offsets, const int32_t *nbrs, const 
   CK(cudaMemcpyAsync(h + 9, g->off + n, 8, cudaMemcpyDeviceToHost, st));
   launch_validate(g->off, g->nbr, (const int32_t *)g->w, n, nnz, v, st, d);
   CK(cudaMemcpyAsync(h, v, 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  sync_checked(st);
   if ((int64_t)h[8] != 0 || (int64_t)h[9] != nnz)
     fail(LCC_ERR_INVALID, "offsets[0] must be 0 and offsets[n] must equal nnz");
   if (h[0] & 1) fail(LCC_ERR_INVALID, "offsets are not monotone");
   launch_validate_rows(g->off, g->nbr, (const int32_t *)g->w, n, v, st, d);
   CK(cudaMemcpyAsync(h, v, 64, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  sync_checked(st);
   note_launches(2);
   if (h[0] & 2) fail(LCC_ERR_INVALID, "neighbour id out of range [0, n)");
   if (h[0] & 4) fail(LCC_ERR_SELF_LOOP, "self loop in the input");
@@ -312,7 +312,7 @@ lcc_status lcc_desired(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, i
     E->add_job(&J, labels, frontier);
     while (!E->idle()) E->tick();
     CK(cudaMemcpyAsync(desired_out, J.lv[0].D, g->n * 4, cudaMemcpyDeviceToHost, g->st));
-    CK(cudaStreamSynchronize(g->st));
+    sync_checked(g->st);
   } catch (...) {
     E->drop_job(&J);
     throw;
@@ -348,7 +348,7 @@ lcc_status lcc_best_moves(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q
     E->add_job(&J, labels_inout, nullptr);
     while (!E->idle()) E->tick();
     CK(cudaMemcpyAsync(labels_inout, J.lv[0].L, g->n * 4, cudaMemcpyDeviceToHost, g->st));
-    CK(cudaStreamSynchronize(g->st));
+    sync_checked(g->st);
   } catch (...) {
     E->drop_job(&J);
     throw;
@@ -408,7 +408,7 @@ lcc_status lcc_graph_export(const lcc_graph *g, int64_t *off, int32_t *nbr, int6
     }
   }
   if (k && g->kc && g->n) CK(cudaMemcpyAsync(k, g->kc, g->n * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  sync_checked(st);
   if (w && g->nnz) {
     if (g->wtype == W_I32)
       for (int64_t e = 0; e < g->nnz; ++e) w[e] = w32[e];

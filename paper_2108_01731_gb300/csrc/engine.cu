@@ -127,10 +127,10 @@ size_t Engine::scratch_bytes() const {
 
 void *Engine::stage(size_t bytes) {
   // the previous upload from this buffer may still be in flight
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   if (bytes > h_stage_bytes_) {
     if (h_stage_) {
-      CK(cudaStreamSynchronize(st_));
+      sync_checked(st_);
       cudaFreeHost(h_stage_);
     }
     size_t nb = bytes + bytes / 2 + 4096;
@@ -143,7 +143,7 @@ void *Engine::stage(size_t bytes) {
 void *Engine::stage2(size_t bytes) {
   if (bytes > h_stage2_bytes_) {
     if (h_stage2_) {
-      CK(cudaStreamSynchronize(st_));
+      sync_checked(st_);
       cudaFreeHost(h_stage2_);
     }
     size_t nb = bytes + bytes / 2 + 4096;
@@ -214,7 +214,7 @@ void Engine::level_stats(std::vector<Job *> &js, std::vector<Level *> &lvs) {
   note_launches(1);
   LevelInfo *h = (LevelInfo *)stage2(nj * sizeof(LevelInfo));
   CK(cudaMemcpyAsync(h, di, nj * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   for (int i = 0; i < nj; ++i) {
     lvs[i]->info = h[i];
     lvs[i]->wide = needs_wide(*lvs[i], js[i]->p, js[i]->q, js[i]->ktot);
@@ -239,7 +239,7 @@ void Engine::init_levels(std::vector<Level *> &lvs) {
   launch_init_level(dt, dv, nj, vt, st_, d_);
   note_launches(1);
   // the staging buffer is reused by the next upload: wait for the copies
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
 }
 
 // ------------------------------------------------------------ add job ----
@@ -322,7 +322,7 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
     upload_table(tab, vs, dt, dv, stage(sizeof(LJob) + 16), st_);
     launch_recompute_K(dt, dv, 1, n, st_, d_);
     note_launches(2);
-    CK(cudaStreamSynchronize(st_));
+    sync_checked(st_);
   } else {
     std::vector<Level *> lvs = {&L};
     init_levels(lvs);
@@ -385,12 +385,22 @@ void Engine::round(std::vector<Job *> &js) {
     x.p = J->p;
     x.q = J->q;
     x.wtype = L.wtype;
+    x.pull_min = INT64_MAX;
     int32_t f = 0;
     if (J->eval_only) {
       f |= JF_EVAL_ONLY;
     } else {
       if (J->round == 0 || J->sc.vset == LCC_VSET_ALL) f |= JF_ALL;
-      if (J->sc.vset == LCC_VSET_NBR_VERTICES) f |= JF_MARK_NBR;
+      if (J->sc.vset == LCC_VSET_NBR_VERTICES) {
+        f |= JF_MARK_NBR;
+        // When the movers' rows cover a quarter of the level's entries, their
+        // neighbourhoods are most of the graph: the next round evaluates every
+        // vertex with an edge and keeps the labels of those with no moved
+        // neighbour, instead of marking V' entry by entry.
+        if (L.lk && !(J->sc.flags & LCC_SCHED_MARK_ONLY))
+          x.pull_min = std::max<int64_t>(1, L.info.nnz / 4);
+        if (J->round > 0 && J->pull) f |= JF_PULL;
+      }
       if (J->sc.vset == LCC_VSET_NBR_CLUSTERS) f |= JF_MARK_CL;
       any_apply = true;
     }
@@ -419,7 +429,7 @@ void Engine::round(std::vector<Job *> &js) {
   b.cnt = s_cnt_.get<int64_t>(NB, st_);
 
   int64_t *ctr = s_ctr_.get<int64_t>(NCTR, st_);
-  int64_t *jm = s_jmoves_.get<int64_t>(nj, st_);
+  int64_t *jm = s_jmoves_.get<int64_t>(2 * nj, st_);
   uint64_t *moved = s_moved_.get<uint64_t>(vt, st_);
   HubBufs h;
   memset(&h, 0, sizeof(h));
@@ -448,7 +458,7 @@ void Engine::round(std::vector<Job *> &js) {
   upload_table(tab, vs, dt, dv, stage(nj * (sizeof(JobDev) + 8) + 8), st_);
   CK(cudaMemsetAsync(b.cnt, 0, NB * sizeof(int64_t), st_));
   CK(cudaMemsetAsync(ctr, 0, NCTR * sizeof(int64_t), st_));
-  CK(cudaMemsetAsync(jm, 0, nj * sizeof(int64_t), st_));
+  CK(cudaMemsetAsync(jm, 0, 2 * nj * sizeof(int64_t), st_));
 
   int launches = 0;
   if (timing) CK(cudaEventRecord(ev_[0], st_));
@@ -470,15 +480,15 @@ void Engine::round(std::vector<Job *> &js) {
   if (any_apply) {
     launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);
     ++launches;
-    if (any_mark) launch_mark(dt, moved, ctr, any_cl, dv, nj, vt, st_, d_, &launches);
+    if (any_mark) launch_mark(dt, moved, ctr, jm, any_cl, dv, nj, vt, st_, d_, &launches);
   }
   if (timing) CK(cudaEventRecord(ev_[3], st_));
   note_launches(launches);
 
-  int64_t *hbuf = (int64_t *)stage2((NCTR + nj) * sizeof(int64_t));
+  int64_t *hbuf = (int64_t *)stage2((NCTR + 2 * nj) * sizeof(int64_t));
   CK(cudaMemcpyAsync(hbuf, ctr, NCTR * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
-  CK(cudaMemcpyAsync(hbuf + NCTR, jm, nj * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  CK(cudaMemcpyAsync(hbuf + NCTR, jm, 2 * nj * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
+  sync_checked(st_);
   if (hbuf[C_ERR])
     throw Error(LCC_ERR_CUDA, "best-move round overflowed a work buffer (code " +
                                   std::to_string(hbuf[C_ERR]) + ")");
@@ -499,7 +509,9 @@ void Engine::round(std::vector<Job *> &js) {
   }
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
-    const int64_t mv = hbuf[NCTR + i];
+    const int64_t mv = hbuf[NCTR + 2 * i];
+    // the mark kernel skipped this job under the same test
+    J->pull = hbuf[NCTR + 2 * i + 1] >= tab[i].pull_min;
     J->round += 1;
     J->rounds_total += 1;
     if (J->eval_only) {
@@ -578,7 +590,7 @@ void Engine::contract(std::vector<Job *> &js) {
   CK(cudaMemcpyAsync(hb + 1, pcnt + vt, 8, cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(hb + 2, err, 4, cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(hb + 3, jc, 2 * nj * 8, cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   if ((int32_t)hb[2]) throw Error(LCC_ERR_INVALID, "label out of range in Compress");
   const int64_t ntot = hb[0];
   const int64_t P = hb[1];
@@ -620,7 +632,7 @@ void Engine::contract(std::vector<Job *> &js) {
   scan_exclusive_i64(flags, P, stmp = tmp.alloc<int64_t>(scan_tmp_elems(P + 1)), st_, d_);
   note_launches(4);
   CK(cudaMemcpyAsync(hb, flags + P, 8, cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   const int64_t U = hb[0];
   int64_t *uvals = store->alloc<int64_t>(U);
   int32_t *unbr = store->alloc<int32_t>(U);
@@ -738,7 +750,7 @@ void Engine::up(std::vector<Job *> &js) {
         next.push_back(J);
       }
     }
-    CK(cudaStreamSynchronize(st_));  // staging reuse
+    sync_checked(st_);  // staging reuse
     if (!rtab.empty()) {
       const int nr = (int)rtab.size();
       LJob *rt = s_ljobs_.get<LJob>(nr, st_);
@@ -746,7 +758,7 @@ void Engine::up(std::vector<Job *> &js) {
       upload_table(rtab, rvs, rt, rv, stage(nr * (sizeof(LJob) + 8) + 8), st_);
       launch_recompute_K(rt, rv, nr, rvs.back(), st_, d_);
       note_launches(2);
-      CK(cudaStreamSynchronize(st_));
+      sync_checked(st_);
     }
     cur.swap(next);
   }
@@ -790,7 +802,7 @@ void Engine::finalize(std::vector<Job *> &js) {
       CK(cudaMemcpyAsync(J->labels_out, J->lv[0].L, J->lv[0].n * sizeof(int32_t), kind, st_));
     }
   }
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
     const i128 s_in = (i128)(int64_t)h[i].s_in;
@@ -821,7 +833,7 @@ void Engine::objective_of(Job *J) {
   note_launches(4);
   ObjAcc *h = (ObjAcc *)stage2(sizeof(ObjAcc));
   CK(cudaMemcpyAsync(h, acc, sizeof(ObjAcc), cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   const i128 s_in = (i128)(int64_t)h->s_in;
   const u128 ksq = ((u128)h->ksq_hi << 64) | h->ksq_lo;
   const u128 kself = ((u128)h->kself_hi << 64) | h->kself_lo;
@@ -840,7 +852,7 @@ void Engine::compress_to_graph(Job *J, int32_t *map_host, lcc_graph **out) {
   int64_t first = 0, last = 0;
   CK(cudaMemcpyAsync(&first, Lc.off, 8, cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(&last, Lc.off + n2, 8, cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   const int64_t nnz2 = last - first;
   lcc_graph *g = new lcc_graph();
   g->dev = dev_;
@@ -861,7 +873,7 @@ void Engine::compress_to_graph(Job *J, int32_t *map_host, lcc_graph **out) {
   }
   CK(cudaMemcpyAsync(g->kc, Lc.k, n2 * 8, cudaMemcpyDeviceToDevice, st_));
   if (map_host) CK(cudaMemcpyAsync(map_host, Lf.map, Lf.n * 4, cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
+  sync_checked(st_);
   if (first != 0) {
     // offsets of a single-job level start at 0; keep the invariant explicit
     throw Error(LCC_ERR_CUDA, "internal: coarse offsets do not start at 0");

@@ -23,6 +23,12 @@ struct Error : std::runtime_error {
 
 void check_cuda(cudaError_t e, const char *what, int line);
 #define CK(x) ::lcc::check_cuda((x), #x, __LINE__)
+// Waits for the stream, then reports any launch that the runtime refused
+// (a bad launch configuration does not surface through the stream).
+inline void sync_checked(cudaStream_t st) {
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+}
 
 extern std::atomic<long long> g_launches;
 inline void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -119,6 +125,7 @@ struct Job {
   Phase phase = P_BM;
   BMKind kind = BM_COARSEN;
   int round = 0;
+  bool pull = false;  // the next round tests V' in the best-move kernels (JF_PULL)
   bool moved_level = false;
   bool moved_any = false;
   bool eval_only = false;

@@ -285,69 +285,112 @@ void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, co
 // ----------------------------------------------------------- radix sort --
 
 constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
+constexpr int RS_WRUN = RS_TILE / RS_W;  // contiguous elements ranked by one warp
 
+// Per-tile digit counts, lanes of equal digit aggregated before the shared
+// atomic (skewed digits do not serialise on one counter).
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *keys, int64_t n, int shift,
                                                   int64_t ntiles, int64_t *ghist) {
   __shared__ unsigned int h[256];
+  const int lane = threadIdx.x & 31;
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int i = threadIdx.x; i < RS_TILE; i += RS_T) {
     const int64_t idx = base + i;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    const int dg = idx < n ? (int)((keys[idx] >> shift) & 255u) : -1;
+    const unsigned peers = __match_any_sync(FULL, dg);
+    if (dg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[dg], (unsigned)__popc(peers));
   }
   __syncthreads();
   ghist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter: elements are ranked in index order within the tile (16
-// rounds of 256 consecutive elements; within a round, warp order then lane
-// order) and placed after everything of smaller digit or earlier tile.
-__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ keys,
+// Stable scatter of one tile.  Warp w ranks elements [w * RS_WRUN, (w + 1) *
+// RS_WRUN) of the tile in index order with warp-private digit counters; a
+// per-digit prefix over the warps and an exclusive scan over the digits give
+// every element its place in the tile sorted by digit (ties in index order).
+// The tile is rearranged in shared memory and written out so that consecutive
+// threads store consecutive places of one digit's run (coalesced), after
+// everything of smaller digit or earlier tile (tile-major offsets goff).
+__global__ void __launch_bounds__(RS_T, 3) k_rs_scatter(const uint64_t *__restrict__ keys,
                                                      const int64_t *__restrict__ vals, int64_t n,
                                                      int shift, int64_t ntiles,
                                                      const int64_t *__restrict__ goff,
                                                      uint64_t *keys_out, int64_t *vals_out) {
-  __shared__ int64_t base_off[256];
-  __shared__ int run[256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t *s_key = (uint64_t *)rs_smem;
+  int64_t *s_val = (int64_t *)(s_key + RS_TILE);
   __shared__ int wcnt[RS_W][256];
+  __shared__ int dstart[256];
+  __shared__ int wsum[RS_W];
+  __shared__ int64_t gbase[256];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  base_off[tid] = goff[(int64_t)tid * ntiles + blockIdx.x];
-  run[tid] = 0;
+#pragma unroll
   for (int k = 0; k < RS_W; ++k) wcnt[k][tid] = 0;
+  gbase[tid] = goff[(int64_t)tid * ntiles + blockIdx.x];
   __syncthreads();
   const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t wbase = tile0 + (int64_t)w * RS_WRUN;
+  uint64_t key[RS_I];
+  int lr[RS_I];
+#pragma unroll
   for (int r = 0; r < RS_I; ++r) {
-    const int64_t idx = tile0 + (int64_t)r * RS_T + tid;
+    const int64_t idx = wbase + r * 32 + lane;
     const bool has = idx < n;
-    uint64_t key = 0;
-    int64_t val = 0;
-    int dg = 256 + lane;  // unique dummy digit for lanes past the end
-    if (has) {
-      key = keys[idx];
-      val = vals[idx];
-      dg = (int)((key >> shift) & 255u);
-    }
+    key[r] = has ? keys[idx] : 0ull;
+    const int dg = has ? (int)((key[r] >> shift) & 255u) : 256 + lane;
     const unsigned peers = __match_any_sync(FULL, dg);
-    const bool leader = lane == __ffs(peers) - 1;
-    const int rk = __popc(peers & lanemask_lt());
-    if (has && leader) wcnt[w][dg] = __popc(peers);
-    __syncthreads();
-    if (has) {
-      int pre = 0;
-      for (int k = 0; k < w; ++k) pre += wcnt[k][dg];
-      const int64_t pos = base_off[dg] + run[dg] + pre + rk;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+    lr[r] = has ? wcnt[w][dg] + __popc(peers & lanemask_lt()) : 0;
+    __syncwarp();
+    if (has && lane == __ffs(peers) - 1) wcnt[w][dg] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // digit tid: exclusive prefix over the warps, then the tile's digit starts
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < RS_W; ++k) {
+    const int c = wcnt[k][tid];
+    wcnt[k][tid] = tot;
+    tot += c;
+  }
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < w; ++k) before += wsum[k];
+  dstart[tid] = before + incl - tot;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_I; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    if (idx < n) {
+      const int dg = (int)((key[r] >> shift) & 255u);
+      const int pos = dstart[dg] + wcnt[w][dg] + lr[r];
+      s_key[pos] = key[r];
+      s_val[pos] = vals[idx];
     }
-    __syncthreads();
-    if (has && leader) {
-      atomicAdd(&run[dg], __popc(peers));
-      wcnt[w][dg] = 0;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int64_t rem = n - tile0;
+  const int cnt = rem < RS_TILE ? (int)rem : RS_TILE;
+#pragma unroll 4
+  for (int p = tid; p < cnt; p += RS_T) {
+    const uint64_t k = s_key[p];
+    const int dg = (int)((k >> shift) & 255u);
+    const int64_t g = gbase[dg] + (p - dstart[dg]);
+    keys_out[g] = k;
+    vals_out[g] = s_val[p];
   }
 }
+
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 16;
 
 int64_t radix_tmp_elems(int64_t n, int npasses) {
   const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
@@ -366,11 +409,15 @@ void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t
   int64_t *stmp = tmp + m + 1;
   uint64_t *ki = keys, *ko = keys_alt;
   int64_t *vi = vals, *vo = vals_alt;
+  // (a refusal shows up as the launch error of the first scatter)
+  (void)cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RS_SMEM);
   for (int p = 0; p < npasses; ++p) {
     k_rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, n, shifts[p], ntiles, ghist);
     cudaMemsetAsync(ghist + m, 0, sizeof(int64_t), st);
     scan_exclusive_i64(ghist, m, stmp, st, d);
-    k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, vi, n, shifts[p], ntiles, ghist, ko, vo);
+    k_rs_scatter<<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ki, vi, n, shifts[p], ntiles, ghist, ko,
+                                                          vo);
     *launches += 3;
     uint64_t *tk = ki; ki = ko; ko = tk;
     int64_t *tv = vi; vi = vo; vo = tv;

@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   int cur = -1;
   int64_t bc[NB];
-  int64_t hcap = 0, hun = 0, hsu = 0, rmax = 0, kmax = 0, ksum = 0, wabs = 0, kneg = 0, hmax = 0;
+  int64_t hcap = 0, hun = 0, hsu = 0, rmax = 0, kmax = 0, ksum = 0, wabs = 0, kneg = 0, hmax = 0,
+          ents = 0;
   for (int i = 0; i < NB; ++i) bc[i] = 0;
   auto flush = [&]() {
     if (cur < 0) return;
@@ -51,8 +52,9 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
     if (wabs) atomicAdd((unsigned long long *)&I->wabs, (unsigned long long)wabs);
     if (kneg) atomicAdd((unsigned long long *)&I->pad, (unsigned long long)kneg);
     if (hmax) atomicMax((unsigned long long *)&I->hub_maxcap, (unsigned long long)hmax);
+    if (ents) atomicAdd((unsigned long long *)&I->nnz, (unsigned long long)ents);
     for (int i = 0; i < NB; ++i) bc[i] = 0;
-    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = hmax = 0;
+    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = hmax = ents = 0;
   };
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
        i += warps_total) {
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
       const int64_t deg = end - beg;
       const int b = bucket_of(deg);
       bc[b] += 1;
+      ents += deg;
       if (b == B_HUB) {
         const int64_t cap = hub_cap(deg);
         hcap += cap;

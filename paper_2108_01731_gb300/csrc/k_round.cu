@@ -86,6 +86,7 @@ struct JobView {
   const unsigned long long *lk;
   int64_t p, q;
   int32_t wtype;
+  int32_t flags;
 };
 
 __device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
@@ -101,14 +102,18 @@ __device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
   x.p = J->p;
   x.q = J->q;
   x.wtype = J->wtype;
+  x.flags = J->flags;
   return x;
 }
 
-// Cluster of neighbour u and, when packed, its weight.
-__device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c, uint32_t &k32) {
+// Cluster of neighbour u and, when packed, its weight; `moved` collects the
+// LK_MOVED bit.
+__device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c, uint32_t &k32,
+                                         uint32_t &moved) {
   if (J.lk) {
     const unsigned long long x = __ldg(J.lk + u);
-    c = (int32_t)(uint32_t)x;
+    moved |= (uint32_t)x & LK_MOVED;
+    c = (int32_t)((uint32_t)x & ~LK_MOVED);
     k32 = (uint32_t)(x >> 32);
   } else {
     c = J.L[u];
@@ -161,7 +166,7 @@ __device__ __forceinline__ Own own_of(const JobView &J, int32_t v) {
   Own o;
   if (J.lk) {
     const unsigned long long x = __ldg(J.lk + v);
-    o.Lv = (int32_t)(uint32_t)x;
+    o.Lv = (int32_t)((uint32_t)x & ~LK_MOVED);
     o.KLv = (int64_t)(x >> 32);
   } else {
     o.Lv = J.L[v];
@@ -170,6 +175,51 @@ __device__ __forceinline__ Own own_of(const JobView &J, int32_t v) {
   o.kv = J.k[v];
   o.Kv = J.K[v];
   return o;
+}
+
+// V' work of JF_PULL jobs, counted where it is decided (the frontier kernel
+// counts the vertices of the other jobs): entries, vertices and weight bytes,
+// summed per block in shared memory so that no thread holds accumulators.
+__shared__ unsigned long long s_pull[3];
+
+struct PullCount {
+  // every thread of the block, before the first add
+  static __device__ __forceinline__ void init() {
+    if (threadIdx.x < 3) s_pull[threadIdx.x] = 0;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void add(const JobView &J, int64_t deg) const {
+    atomicAdd(&s_pull[0], (unsigned long long)deg);
+    atomicAdd(&s_pull[1], 1ull);
+    const int wb = J.wtype == W_I32 ? 4 : (J.wtype == W_I64 ? 8 : 0);
+    if (wb) atomicAdd(&s_pull[2], (unsigned long long)(deg * wb));
+  }
+  // every thread of the block, after the last add
+  static __device__ __forceinline__ void flush(int64_t *ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0 && s_pull[1]) {
+      atomicAdd((unsigned long long *)&ctr[C_EDGES], s_pull[0]);
+      atomicAdd((unsigned long long *)&ctr[C_VERTS], s_pull[1]);
+      if (s_pull[2]) atomicAdd((unsigned long long *)&ctr[C_WB], s_pull[2]);
+    }
+  }
+};
+
+// D[v] of an evaluated vertex.  A vertex of a JF_PULL job is in V' only when
+// some neighbour moved in the previous round; otherwise it keeps its label.
+template <typename S>
+__device__ __forceinline__ void write_desired(const JobView &J, int32_t v, int64_t deg,
+                                              int32_t Lv, int64_t kv, int64_t KLv, S best,
+                                              int32_t bc, long long w_stay, bool v_seen,
+                                              bool row_moved, int64_t Kv = -1) {
+  if (J.flags & JF_PULL) {
+    if (!row_moved) {
+      J.D[v] = Lv;
+      return;
+    }
+    PullCount().add(J, deg);
+  }
+  J.D[v] = decide<S>(J, v, Lv, kv, KLv, best, bc, w_stay, v_seen, Kv);
 }
 
 // Linear-probing insert of (c, k32) += sum.  The table has at least twice as
@@ -196,62 +246,106 @@ __device__ __forceinline__ bool probe_insert(At at, uint32_t cap, int lg, int32_
 
 // ---------------------------------------------------------------- V' -----
 
-__global__ void __launch_bounds__(256) k_frontier(const JobDev *__restrict__ jobs,
-                                                  const int64_t *__restrict__ vstart, int njobs,
-                                                  int64_t vtot, Buckets b, int64_t *ctr) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+// Sum of a non-negative value over the lanes of `peers` (each term below
+// 2^43, so the high parts stay below 2^32), exact through two 32-bit
+// reductions.
+__device__ __forceinline__ unsigned long long peers_sum(unsigned peers, long long x) {
+  const unsigned lo = __reduce_add_sync(peers, (unsigned)(x & 0xFFFF));
+  const unsigned hi = __reduce_add_sync(peers, (unsigned)(x >> 16));
+  return ((unsigned long long)hi << 16) + lo;
+}
+
+// Tiles of FR_T * FR_V vertices: the lanes of a warp that share a bucket take
+// consecutive places of the tile's run of that bucket, and one global atomic
+// per bucket and tile places the runs.
+constexpr int FR_T = 256, FR_V = 4;
+
+__global__ void __launch_bounds__(FR_T) k_frontier(const JobDev *__restrict__ jobs,
+                                                   const int64_t *__restrict__ vstart, int njobs,
+                                                   int64_t vtot, Buckets b, int64_t *ctr) {
+  __shared__ unsigned t_cnt[NB];
+  __shared__ unsigned long long t_base[NB];
+  __shared__ unsigned long long s_be[NB], s_bv[NB];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < NB) {
+    t_cnt[tid] = 0;
+    s_be[tid] = 0;
+    s_bv[tid] = 0;
+  }
+  __syncthreads();
   long long my_deg = 0, my_cnt = 0, my_wb = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < vtot;
-       base += stride) {
-    const int64_t i = base + lane;
-    int bk = -1;
-    uint64_t item = 0;
-    int64_t my_last_deg = 0;
-    if (i < vtot) {
-      const int j = find_job(vstart, njobs, i);
-      const JobDev *J = jobs + j;
-      const int64_t v = i - vstart[j];
-      const int32_t Lv = J->L[v];
-      if (J->lk) J->lk[v] = slot_word(Lv, (uint32_t)J->K[Lv]);
-      bool f = (J->flags & JF_ALL) != 0;
-      if (J->fr[v]) {
-        J->fr[v] = 0;
-        f = true;
+  const int64_t tile = (int64_t)FR_T * FR_V;
+  for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < vtot; t0 += (int64_t)gridDim.x * tile) {
+    int bk[FR_V];
+    uint64_t item[FR_V];
+    unsigned place[FR_V];
+#pragma unroll
+    for (int r = 0; r < FR_V; ++r) {
+      const int64_t i = t0 + (int64_t)r * FR_T + tid;
+      bk[r] = -1;
+      item[r] = 0;
+      place[r] = 0;
+      int64_t deg = 0;
+      if (i < vtot) {
+        const int j = find_job(vstart, njobs, i);
+        const JobDev *J = jobs + j;
+        const int64_t v = i - vstart[j];
+        const int32_t Lv = J->L[v];
+        // fr bit 0: v is in V' (marked); bit 1: v moved in the previous round
+        const uint8_t m = J->fr[v];
+        if (m) J->fr[v] = 0;
+        const bool pull = (J->flags & JF_PULL) != 0;
+        if (J->lk)
+          J->lk[v] = slot_word(Lv, (uint32_t)J->K[Lv]) | (pull && (m & 2) ? LK_MOVED : 0u);
+        deg = J->off[v + 1] - J->off[v];
+        bool f;
+        if (J->flags & JF_ALL)
+          f = !(deg == 0 && Lv == (int32_t)v);  // alone with no neighbour: no candidate
+        else if (pull)
+          f = deg > 0;  // every vertex that can have a moved neighbour; the kernels test it
+        else
+          f = (m & 1) != 0;
+        if (f) {
+          bk[r] = bucket_of(deg);
+          item[r] = ((uint64_t)(uint32_t)j << 32) | (uint32_t)v;
+          if (!pull) {
+            my_deg += deg;
+            my_cnt += 1;
+            my_wb += deg * (J->wtype == W_I32 ? 4 : (J->wtype == W_I64 ? 8 : 0));
+          }
+        } else {
+          deg = 0;
+        }
       }
-      if (f) {
-        const int64_t deg = J->off[v + 1] - J->off[v];
-        // A vertex with no neighbour in its own singleton has no candidate.
-        if (!(deg == 0 && Lv == (int32_t)v)) {
-          bk = bucket_of(deg);
-          my_last_deg = deg;
-          item = ((uint64_t)(uint32_t)j << 32) | (uint32_t)v;
-          my_deg += deg;
-          my_cnt += 1;
-          my_wb += deg * (J->wtype == W_I32 ? 4 : (J->wtype == W_I64 ? 8 : 0));
+      const unsigned peers = __match_any_sync(FULL, bk[r]);
+      if (bk[r] >= 0) {
+        const int leader = __ffs(peers) - 1;
+        unsigned p0 = 0;
+        if (lane == leader) p0 = atomicAdd(&t_cnt[bk[r]], (unsigned)__popc(peers));
+        p0 = __shfl_sync(peers, p0, leader);
+        place[r] = p0 + __popc(peers & lanemask_lt());
+        const unsigned long long ents = peers_sum(peers, deg);
+        if (lane == leader) {
+          atomicAdd(&s_be[bk[r]], ents);
+          atomicAdd(&s_bv[bk[r]], (unsigned long long)__popc(peers));
         }
       }
     }
-    const unsigned active = __ballot_sync(FULL, bk >= 0);
-    if (active) {
-      const unsigned peers = __match_any_sync(FULL, bk);
-      if (bk >= 0) {
-        const int leader = __ffs(peers) - 1;
-        unsigned long long basepos = 0;
-        if (lane == leader)
-          basepos = atomicAdd((unsigned long long *)&b.cnt[bk], (unsigned long long)__popc(peers));
-        basepos = __shfl_sync(peers, basepos, leader);
-        const int64_t pos = (int64_t)basepos + __popc(peers & lanemask_lt());
-        if (pos < b.seg_cap[bk])
-          b.items[b.seg_start[bk] + pos] = item;
-        else
-          atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_BUCKET_OVERFLOW);
-        const unsigned ents = __reduce_add_sync(peers, (unsigned)my_last_deg);
-        if (lane == leader) {
-          atomicAdd((unsigned long long *)&ctr[C_BE + bk], (unsigned long long)ents);
-          atomicAdd((unsigned long long *)&ctr[C_BV + bk], (unsigned long long)__popc(peers));
-        }
-      }
+    __syncthreads();
+    if (tid < NB) {
+      const unsigned c = t_cnt[tid];
+      t_base[tid] = c ? atomicAdd((unsigned long long *)&b.cnt[tid], (unsigned long long)c) : 0ull;
+      t_cnt[tid] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < FR_V; ++r) {
+      if (bk[r] < 0) continue;
+      const int64_t pos = (int64_t)(t_base[bk[r]] + place[r]);
+      if (pos < b.seg_cap[bk[r]])
+        b.items[b.seg_start[bk[r]] + pos] = item[r];
+      else
+        atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_BUCKET_OVERFLOW);
     }
   }
   my_deg = warp_sum_ll(my_deg);
@@ -262,15 +356,21 @@ __global__ void __launch_bounds__(256) k_frontier(const JobDev *__restrict__ job
     atomicAdd((unsigned long long *)&ctr[C_VERTS], (unsigned long long)my_cnt);
     if (my_wb) atomicAdd((unsigned long long *)&ctr[C_WB], (unsigned long long)my_wb);
   }
+  __syncthreads();
+  if (tid < NB && s_bv[tid]) {
+    atomicAdd((unsigned long long *)&ctr[C_BE + tid], s_be[tid]);
+    atomicAdd((unsigned long long *)&ctr[C_BV + tid], s_bv[tid]);
+  }
 }
 
 void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d) {
   if (vtot <= 0) return;
-  int64_t blocks = (vtot + 255) / 256;
+  const int64_t tile = (int64_t)FR_T * FR_V;
+  int64_t blocks = (vtot + tile - 1) / tile;
   const int64_t maxb = (int64_t)d.sms * 8;
   if (blocks > maxb) blocks = maxb;
-  k_frontier<<<(int)blocks, 256, 0, st>>>(jobs, vstart, njobs, vtot, b, ctr);
+  k_frontier<<<(int)blocks, FR_T, 0, st>>>(jobs, vstart, njobs, vtot, b, ctr);
 }
 
 // ------------------------------------------------ deg <= G: G lanes/vertex --
@@ -293,6 +393,7 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   long long ncand = 0;
+  PullCount::init();
   for (int64_t wbase = gw * GPW; wbase < count; wbase += warps_total * GPW) {
     const int64_t it = wbase + gsub;
     const bool valid = it < count;
@@ -311,13 +412,14 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
     }
     const bool has = valid && gl < deg;
     int32_t c = -1;
-    uint32_t k32 = KNONE;
+    uint32_t k32 = KNONE, mbit = 0;
     long long wt = 0;
     if (has) {
       const int32_t u = __ldg(J.nbr + beg + gl);
       wt = weight_at(J, beg + gl);
-      label_of(J, u, c, k32);
+      label_of(J, u, c, k32, mbit);
     }
+    const bool row_moved = (__ballot_sync(FULL, mbit != 0) & gmask) != 0;
     const unsigned long long key = ((unsigned long long)gsub << 32) | (uint32_t)c;
     const unsigned peers = __match_any_sync(FULL, key);
     const int leader = __ffs(peers) - 1;
@@ -350,10 +452,12 @@ __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ job
       if (better<S>(os, oc, score, cid)) { score = os; cid = oc; }
     }
     if (valid && gl == 0)
-      J.D[v] = decide<S>(J, v, Lv, kv, own_weight(J, v, Lv), score, cid, w_stay, v_seen);
+      write_desired<S>(J, v, deg, Lv, kv, own_weight(J, v, Lv), score, cid, w_stay, v_seen,
+                       row_moved);
     ncand += __popc(__ballot_sync(FULL, cand));
   }
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
+  PullCount::flush(ctr);
 }
 
 // ------------------------------------------------ preloaded row chunks -----
@@ -366,6 +470,7 @@ struct Chunk {
   int32_t c[E];
   uint32_t k[E];
   long long w[E];
+  uint32_t mv;  // LK_MOVED if some neighbour of the chunk moved
 };
 
 template <int E>
@@ -382,11 +487,12 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
       x.w[i] = weight_at(J, beg + e);
     }
   }
+  x.mv = 0;
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     x.c[i] = -1;
     x.k[i] = KNONE;
-    if (u[i] >= 0) label_of(J, u[i], x.c[i], x.k[i]);
+    if (u[i] >= 0) label_of(J, u[i], x.c[i], x.k[i], x.mv);
   }
 }
 
@@ -452,9 +558,11 @@ __device__ __forceinline__ void scan_slots(const JobView &J, const unsigned long
 
 // ----------------------------------- deg <= T_WARP: warp + shared table --
 
+// Blocks per SM held to what the shared tables allow, so that the register
+// allocation does not lower the occupancy.
 template <typename S, int E, int BK>
-__global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs, Buckets b,
-                                                 int64_t *ctr) {
+__global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
+    k_bm_warp(const JobDev *__restrict__ jobs, Buckets b, int64_t *ctr) {
   constexpr int WPB = 4;
   constexpr int CAP = 64 * E;  // >= 2 * 32 * E
   __shared__ unsigned long long tkey[WPB][CAP];
@@ -465,6 +573,7 @@ __global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs
   const int64_t warps_total = (int64_t)gridDim.x * WPB;
   long long ncand = 0;
   bool fail = false;
+  PullCount::init();
   unsigned long long *K0 = tkey[wib], *V0 = tval[wib];
   auto at = [K0, V0](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
     kp = K0 + s;
@@ -487,7 +596,7 @@ __global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs
     }
     __syncwarp();
     fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
-    __syncwarp();
+    const bool row_moved = __any_sync(FULL, x.mv != 0);  // after the gathers have landed
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
     long long w_stay = 0, nc = 0;
@@ -497,13 +606,16 @@ __global__ void __launch_bounds__(128) k_bm_warp(const JobDev *__restrict__ jobs
     const bool v_seen = __any_sync(FULL, vseen);
     ncand += nc;
     warp_argmax<S>(best, bc);
-    if (lane == 0) J.D[v] = decide<S>(J, v, o.Lv, o.kv, o.KLv, best, bc, w_stay, v_seen, o.Kv);
+    if (lane == 0)
+      write_desired<S>(J, v, deg, o.Lv, o.kv, o.KLv, best, bc, w_stay, v_seen, row_moved,
+                       o.Kv);
     __syncwarp();
   }
   ncand = warp_sum_ll(ncand);
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
   if (__any_sync(FULL, fail) && lane == 0)
     atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
+  PullCount::flush(ctr);
 }
 
 // --------------- deg <= 65536: one block or a cluster of CS blocks ---------
@@ -532,6 +644,7 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
   __shared__ int32_t cl_c[CS];
   __shared__ long long cl_w[CS];
   __shared__ int cl_v[CS];
+  __shared__ int s_rowmv;  // a neighbour of the current vertex moved (this block's entries)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
@@ -545,6 +658,8 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
   }
   long long ncand = 0;
   bool fail = false;
+  if (threadIdx.x == 0) s_rowmv = 0;
+  PullCount::init();
   for (int64_t it = cid; it < count; it += ncl) {
     const uint64_t item = items[it];
     const JobView J = view_of(jobs + (int)(item >> 32));
@@ -582,9 +697,11 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
       }
     };
     fail |= !insert_chunk(x, at, cap, lg);
+    if (x.mv) s_rowmv = 1;
     for (int64_t more = lo + (int64_t)THREADS * E; more < hi; more += (int64_t)THREADS * E) {
       load_chunk(J, beg, more, hi, THREADS, tid, x);
       fail |= !insert_chunk(x, at, cap, lg);
+      if (x.mv) s_rowmv = 1;
     }
     if (CS > 1) cluster.sync(); else __syncthreads();
     const int32_t Lv = o.Lv;
@@ -613,10 +730,15 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
       int vv = lane < NW ? red_v[lane] : 0;
       warp_argmax<S>(bs, bcc);
       ws = warp_sum_ll(ws);
-      const int vall = __any_sync(FULL, vv);
+      // bit 0: cluster id v occurs; bit 1: a neighbour moved (read, then
+      // cleared for the next vertex: its writes come after the next sync)
+      int vall = __any_sync(FULL, vv);
       if (lane == 0) {
+        if (s_rowmv) vall |= 2;
+        s_rowmv = 0;
         if (CS == 1) {
-          J.D[v] = decide<S>(J, v, Lv, kv, o.KLv, bs, bcc, ws, vall != 0, o.Kv);
+          write_desired<S>(J, v, deg, Lv, kv, o.KLv, bs, bcc, ws, (vall & 1) != 0,
+                           (vall & 2) != 0, o.Kv);
         } else {
           *cluster.map_shared_rank(&cl_s[rank], 0) = bs;
           *cluster.map_shared_rank(&cl_c[rank], 0) = bcc;
@@ -637,7 +759,8 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
           ws += cl_w[r];
           vall |= cl_v[r];
         }
-        J.D[v] = decide<S>(J, v, Lv, kv, o.KLv, bs, bcc, ws, vall != 0, o.Kv);
+        write_desired<S>(J, v, deg, Lv, kv, o.KLv, bs, bcc, ws, (vall & 1) != 0,
+                         (vall & 2) != 0, o.Kv);
       }
     } else {
       __syncthreads();
@@ -647,6 +770,7 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
   if (__any_sync(FULL, fail) && lane == 0)
     atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
+  PullCount::flush(ctr);
 }
 
 // ------------------------------------- hubs: global-memory hash tables ----
@@ -777,6 +901,7 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
     if (e_hi > deg) e_hi = deg;
     Chunk<HUB_CHUNK / 256> x;
     load_chunk(J, beg, e_lo, e_hi, 256, tid, x);
+    if (__any_sync(FULL, x.mv != 0) && lane == 0) atomicOr(&h.iso_seen[hh], 2);
     fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
   }
   if (__any_sync(FULL, fail) && lane == 0)
@@ -818,7 +943,7 @@ __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jo
     scan_slots<S>(J, tkey, tval, s_lo + tid, s_hi, 256, v, Lv, kv, best, bc, w_stay, vseen,
                   ncand);
     if (w_stay) atomicAdd((unsigned long long *)&h.stay[hh], (unsigned long long)w_stay);
-    if (vseen) h.iso_seen[hh] = 1;
+    if (vseen) atomicOr(&h.iso_seen[hh], 1);
     warp_argmax<S>(best, bc);
     if (lane == 0) { red_s[wib] = best; red_c[wib] = bc; }
     __syncthreads();
@@ -839,11 +964,12 @@ __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jo
 
 template <typename S>
 __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jobs, Buckets b,
-                                                   HubBufs h, const int64_t *ctr) {
+                                                   HubBufs h, int64_t *ctr) {
   const int lane = threadIdx.x & 31;
   const int64_t H = ctr[C_HUBS];
   const uint64_t *items = b.items + b.seg_start[B_HUB];
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  PullCount::init();
   for (int64_t hh = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); hh < H;
        hh += warps_total) {
     const uint64_t item = items[hh];
@@ -859,10 +985,12 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
     warp_argmax<S>(best, bc);
     if (lane == 0) {
       const int32_t Lv = J.L[v];
-      J.D[v] = decide<S>(J, v, Lv, J.k[v], own_weight(J, v, Lv), best, bc,
-                          (long long)h.stay[hh], h.iso_seen[hh] != 0);
+      const int fl = h.iso_seen[hh];
+      write_desired<S>(J, v, J.off[v + 1] - J.off[v], Lv, J.k[v], own_weight(J, v, Lv), best,
+                       bc, (long long)h.stay[hh], (fl & 1) != 0, (fl & 2) != 0);
     }
   }
+  PullCount::flush(ctr);
 }
 
 // ------------------------------------------------------------ dispatch ----
@@ -1033,62 +1161,117 @@ void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubB
 
 // --------------------------------------------------------------- apply ----
 
-__global__ void __launch_bounds__(256) k_apply(const JobDev *__restrict__ jobs, Buckets b,
-                                               int64_t *jmoves, uint64_t *moved, int64_t moved_cap,
-                                               int64_t *ctr) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+// Sum of any 64-bit value over the lanes of `peers` (every lane of peers).
+__device__ __forceinline__ unsigned long long peers_sum64(unsigned peers, unsigned long long x) {
+  unsigned long long t = 0;
+  for (unsigned m = peers; m; m &= m - 1) t += __shfl_sync(peers, x, __ffs(m) - 1);
+  return t;
+}
+
+// Moves every evaluated vertex to D[v] and keeps K in step (Algorithm 1).
+// Per job: moves and the movers' entries in jmoves[2j], jmoves[2j + 1],
+// summed per lane while the lane stays on one job.  Movers of JF_MARK_NBR
+// jobs get fr = 2 and a place in the moved list (one global atomic per tile).
+constexpr int AP_T = 256, AP_V = 4;
+
+__global__ void __launch_bounds__(AP_T) k_apply(const JobDev *__restrict__ jobs, Buckets b,
+                                                int64_t *jmoves, uint64_t *moved,
+                                                int64_t moved_cap, int64_t *ctr) {
+  __shared__ unsigned t_cnt;
+  __shared__ unsigned long long t_base;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) t_cnt = 0;
+  __syncthreads();
   long long nmv = 0;
+  int cur = -1;
+  unsigned long long c_mv = 0, c_ents = 0;
+  auto flush_lane = [&]() {
+    if (cur >= 0 && c_mv) {
+      atomicAdd((unsigned long long *)(jmoves + 2 * cur), c_mv);
+      if (c_ents) atomicAdd((unsigned long long *)(jmoves + 2 * cur + 1), c_ents);
+    }
+    c_mv = c_ents = 0;
+  };
+  const int64_t tile = (int64_t)AP_T * AP_V;
   for (int bk = 0; bk < NB; ++bk) {
     const int64_t count = seg_count(b, bk);
     const uint64_t *items = b.items + b.seg_start[bk];
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < count;
-         base += stride) {
-      const int64_t i = base + lane;
-      int j = -1;
-      bool mv = false, mark = false;
-      uint64_t item = 0;
-      if (i < count) {
-        item = items[i];
-        j = (int)(item >> 32);
-        const JobDev *J = jobs + j;
-        const int32_t v = (int32_t)(uint32_t)item;
-        if (!(J->flags & JF_EVAL_ONLY)) {
-          const int32_t dv = J->D[v];
-          const int32_t lv = J->L[v];
-          if (dv != lv) {
-            mv = true;
-            const int64_t kv = J->k[v];
-            J->L[v] = dv;
-            if (kv) {
-              atomic_add_i64(J->K + lv, -kv);
-              atomic_add_i64(J->K + dv, kv);
+    for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < count; t0 += (int64_t)gridDim.x * tile) {
+      unsigned place[AP_V];
+      uint64_t mitem[AP_V];
+#pragma unroll
+      for (int r = 0; r < AP_V; ++r) {
+        const int64_t i = t0 + (int64_t)r * AP_T + tid;
+        bool mark = false;
+        mitem[r] = 0;
+        place[r] = ~0u;
+        if (i < count) {
+          const uint64_t item = items[i];
+          const int j = (int)(item >> 32);
+          const JobDev *J = jobs + j;
+          const int32_t v = (int32_t)(uint32_t)item;
+          if (!(J->flags & JF_EVAL_ONLY)) {
+            const int32_t dv = J->D[v];
+            const int32_t lv = J->L[v];
+            if (dv != lv) {
+              const int64_t kv = J->k[v];
+              J->L[v] = dv;
+              if (kv) {
+                atomic_add_i64(J->K + lv, -kv);
+                atomic_add_i64(J->K + dv, kv);
+              }
+              if (J->flags & JF_MARK_CL) J->cl[lv] = 1;
+              int64_t deg = 0;
+              if (J->flags & JF_MARK_NBR) {
+                mark = true;
+                mitem[r] = item;
+                J->fr[v] = 2;  // moved: read by the frontier kernel when the next round pulls
+                deg = J->off[v + 1] - J->off[v];
+              }
+              if (j != cur) {
+                flush_lane();
+                cur = j;
+              }
+              c_mv += 1;
+              c_ents += (unsigned long long)deg;
+              nmv += 1;
             }
-            if (J->flags & JF_MARK_CL) J->cl[lv] = 1;
-            mark = (J->flags & JF_MARK_NBR) != 0;
           }
         }
-      }
-      // per-job move counts, aggregated over the lanes of one job
-      const unsigned peers = __match_any_sync(FULL, mv ? j : -1);
-      if (mv && lane == __ffs(peers) - 1)
-        atomicAdd((unsigned long long *)(jmoves + j), (unsigned long long)__popc(peers));
-      nmv += mv;
-      const unsigned mb = __ballot_sync(FULL, mark);
-      if (mb) {
-        unsigned long long basepos = 0;
-        if (lane == __ffs(mb) - 1)
-          basepos = atomicAdd((unsigned long long *)&ctr[C_MOVED_N], (unsigned long long)__popc(mb));
-        basepos = __shfl_sync(FULL, basepos, __ffs(mb) - 1);
-        if (mark) {
-          const int64_t pos = (int64_t)basepos + __popc(mb & lanemask_lt());
-          if (pos < moved_cap)
-            moved[pos] = item;
-          else
-            atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_MOVED_OVERFLOW);
+        const unsigned mb = __ballot_sync(FULL, mark);
+        if (mb) {
+          unsigned p0 = 0;
+          if (lane == __ffs(mb) - 1) p0 = atomicAdd(&t_cnt, (unsigned)__popc(mb));
+          p0 = __shfl_sync(FULL, p0, __ffs(mb) - 1);
+          if (mark) place[r] = p0 + __popc(mb & lanemask_lt());
         }
       }
+      __syncthreads();
+      if (tid == 0) {
+        t_base = t_cnt ? atomicAdd((unsigned long long *)&ctr[C_MOVED_N],
+                                   (unsigned long long)t_cnt)
+                       : 0ull;
+        t_cnt = 0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < AP_V; ++r) {
+        if (place[r] == ~0u) continue;
+        const int64_t pos = (int64_t)(t_base + place[r]);
+        if (pos < moved_cap)
+          moved[pos] = mitem[r];
+        else
+          atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_MOVED_OVERFLOW);
+      }
     }
+  }
+  // per-job sums: one atomic per warp and job where the lanes agree
+  const unsigned peers = __match_any_sync(FULL, c_mv ? cur : -1);
+  const unsigned long long s_mv = peers_sum64(peers, c_mv);
+  const unsigned long long s_ents = peers_sum64(peers, c_ents);
+  if (c_mv && lane == __ffs(peers) - 1) {
+    atomicAdd((unsigned long long *)(jmoves + 2 * cur), s_mv);
+    if (s_ents) atomicAdd((unsigned long long *)(jmoves + 2 * cur + 1), s_ents);
   }
   nmv = warp_sum_ll(nmv);
   if (lane == 0 && nmv) atomicAdd((unsigned long long *)&ctr[C_MOVES], (unsigned long long)nmv);
@@ -1099,17 +1282,21 @@ void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_
   int64_t tot = 0;
   for (int i = 0; i < NB; ++i) tot += b.seg_cap[i];
   if (tot == 0) return;
-  int64_t g = (tot + 255) / 256;
+  const int64_t tile = (int64_t)AP_T * AP_V;
+  int64_t g = (tot + tile - 1) / tile;
   if (g > d.sms * 8) g = d.sms * 8;
-  k_apply<<<(int)g, 256, 0, st>>>(jobs, b, jmoves, moved, moved_cap, ctr);
+  k_apply<<<(int)g, AP_T, 0, st>>>(jobs, b, jmoves, moved, moved_cap, ctr);
 }
 
 // ---------------------------------------------------------------- mark ----
 
-// V' <- neighbours of the moved vertices (Algorithm 1 / Sec. 3.2.2).
+// V' <- neighbours of the moved vertices (Algorithm 1 / Sec. 3.2.2).  Jobs
+// whose movers hold at least pull_min entries skip the marking: their next
+// round runs with JF_PULL (the host takes the same decision from jmoves).
 __global__ void __launch_bounds__(256) k_mark_nbr(const JobDev *__restrict__ jobs,
                                                   const uint64_t *__restrict__ moved,
-                                                  const int64_t *ctr, int64_t moved_cap) {
+                                                  const int64_t *ctr, const int64_t *jmoves,
+                                                  int64_t moved_cap) {
   const int lane = threadIdx.x & 31;
   int64_t M = ctr[C_MOVED_N];
   if (M > moved_cap) M = moved_cap;
@@ -1117,7 +1304,9 @@ __global__ void __launch_bounds__(256) k_mark_nbr(const JobDev *__restrict__ job
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M;
        i += warps_total) {
     const uint64_t item = moved[i];
-    const JobDev *J = jobs + (int)(item >> 32);
+    const int j = (int)(item >> 32);
+    const JobDev *J = jobs + j;
+    if (jmoves[2 * j + 1] >= J->pull_min) continue;
     const int32_t v = (int32_t)(uint32_t)item;
     const int64_t beg = J->off[v], end = J->off[v + 1];
     for (int64_t e = beg + lane; e < end; e += 32) J->fr[__ldg(J->nbr + e)] = 1;
@@ -1149,10 +1338,10 @@ __global__ void k_clear_cl(const JobDev *__restrict__ jobs, const int64_t *__res
   }
 }
 
-void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, bool any_cl,
-                 const int64_t *vstart, int njobs, int64_t vtot, cudaStream_t st, const Dev &d,
-                 int *launches) {
-  k_mark_nbr<<<d.sms * 8, 256, 0, st>>>(jobs, moved, ctr, vtot);
+void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, const int64_t *jmoves,
+                 bool any_cl, const int64_t *vstart, int njobs, int64_t vtot, cudaStream_t st,
+                 const Dev &d, int *launches) {
+  k_mark_nbr<<<d.sms * 8, 256, 0, st>>>(jobs, moved, ctr, jmoves, vtot);
   ++*launches;
   if (any_cl && vtot > 0) {
     int64_t g = (vtot + 255) / 256;

@@ -27,8 +27,16 @@ enum : int32_t {
   JF_ALL = 1,       // evaluate every vertex this round (V' = V)
   JF_MARK_NBR = 2,  // next V' = neighbours of moved vertices
   JF_MARK_CL = 4,   // next V' = neighbours of clusters that lost a vertex
-  JF_EVAL_ONLY = 8  // compute D only (no apply)
+  JF_EVAL_ONLY = 8, // compute D only (no apply)
+  // V' = neighbours of the previous round's moved vertices, tested by the
+  // best-move kernels themselves: a vertex is evaluated in full and keeps its
+  // label unless some entry of its row has LK_MOVED set.  On a symmetric
+  // graph this is the same set as marking the neighbours of every mover.
+  JF_PULL = 16
 };
+// Bit 31 of the label half of lk[u] (labels are non-negative int32): u moved
+// in the previous round.  Set only for JF_PULL jobs.
+constexpr uint32_t LK_MOVED = 0x80000000u;
 
 // Degree buckets of the best-move kernels.  Every hash table holds at least
 // two slots per entry of the row, so a row of d entries needs 2d slots.
@@ -105,6 +113,9 @@ struct JobDev {
   unsigned long long *lk;
   int64_t n;
   int64_t p, q;
+  // the next round tests V' in the kernels (JF_PULL) instead of marking it
+  // when the movers' rows hold at least this many entries (INT64_MAX: never)
+  int64_t pull_min;
   int32_t wtype;
   int32_t flags;
 };
@@ -158,7 +169,7 @@ struct HubBufs {
   i128 *part_score;   // [max_sunits]
   int32_t *part_cid;  // [max_sunits]
   int64_t *stay;      // [max_hubs]
-  int32_t *iso_seen;  // [max_hubs]
+  int32_t *iso_seen;  // [max_hubs] bit 0: cluster id v occurs; bit 1: a neighbour moved
   int64_t max_hubs;
   int64_t max_sunits;
 };
@@ -204,6 +215,7 @@ struct LevelInfo {
   int64_t wabs;         // sum of |w| over entries
   int64_t pad;          // vertices with a negative node weight
   int64_t hub_maxcap;   // largest hub table
+  int64_t nnz;          // entries (sum of deg)
 };
 
 // Per-job accumulators of the objective kernels.
@@ -292,11 +304,12 @@ void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      const GTab &gt, int64_t hub_passes, int64_t *ctr, cudaStream_t st,
                      const Dev &d, int *launches, cudaEvent_t *ev);
+// jmoves[2j] = moves of job j, jmoves[2j + 1] = entries of its movers' rows.
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
-void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, bool any_cl,
-                 const int64_t *vstart, int njobs, int64_t vtot, cudaStream_t st, const Dev &d,
-                 int *launches);
+void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, const int64_t *jmoves,
+                 bool any_cl, const int64_t *vstart, int njobs, int64_t vtot, cudaStream_t st,
+                 const Dev &d, int *launches);
 
 // Level kernels (k_level.cu).
 void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,

@@ -28,6 +28,7 @@ LCC_NODEW_UNIT, LCC_NODEW_DEGREE, LCC_NODEW_CUSTOM = 0, 1, 2
 LCC_VSET_ALL, LCC_VSET_NBR_VERTICES, LCC_VSET_NBR_CLUSTERS = 0, 1, 2
 LCC_MEM_HOST, LCC_MEM_DEVICE = 0, 1
 LCC_SCHED_TIMING = 1
+LCC_SCHED_MARK_ONLY = 2
 
 
 class lcc_schedule(C.Structure):
@@ -145,9 +146,9 @@ def _ptr(a, dtype):
 
 
 def schedule(num_iter=10, max_levels=64, refine=True, vset=LCC_VSET_NBR_VERTICES,
-             timing=False):
-    return lcc_schedule(int(num_iter), int(max_levels), int(bool(refine)), int(vset), 1,
-                        LCC_SCHED_TIMING if timing else 0)
+             timing=False, mark_only=False):
+    flags = (LCC_SCHED_TIMING if timing else 0) | (LCC_SCHED_MARK_ONLY if mark_only else 0)
+    return lcc_schedule(int(num_iter), int(max_levels), int(bool(refine)), int(vset), 1, flags)
 
 
 class Graph:

@@ -178,6 +178,40 @@ def test_cluster_matches_oracle(L, case):
     G.free()
 
 
+def test_pull_and_mark_frontiers_agree(L):
+    """V' = neighbours of the movers (Sec. 3.2.2), found by marking them or by
+    evaluating every vertex with an edge and keeping the labels of those with
+    no moved neighbour: same labels, rounds and scanned entries as the oracle
+    either way, and the second way does run (it processes more entries)."""
+    extra = 0
+    for name, mode, p, q, kw in CLUSTER_CASES:
+        if kw.get("vset", 1) != O.VSET_NBR_VERTICES:
+            continue
+        g = GRAPHS[name]
+        k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None
+        G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+        wl, num, den, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k,
+                                      num_iter=kw.get("num_iter", 10),
+                                      max_levels=kw.get("max_levels", 64),
+                                      refine=kw.get("refine", True))
+        for mark_only in (True, False):
+            sched = L.schedule(num_iter=kw.get("num_iter", 10),
+                               max_levels=kw.get("max_levels", 64),
+                               refine=kw.get("refine", True), mark_only=mark_only)
+            labels, _, st = L.lcc_cluster(G, p, q, mode, sched)
+            assert np.array_equal(labels, wl), (name, mark_only)
+            assert st["obj_num"] == num and st["rounds_total"] == wst[1]
+            assert st["edges_scanned"] == wst[2], (name, mark_only)
+            processed = sum(st["bucket_entries"])
+            if mark_only:
+                assert processed == st["edges_scanned"]
+            else:
+                assert processed >= st["edges_scanned"]
+                extra += processed - st["edges_scanned"]
+        G.free()
+    assert extra > 0
+
+
 def test_config1_planted_partition_full_size(L):
     """SBM, 10,000 vertices in 100 blocks, p_in 0.05, p_out 0.0005, lambda
     1/100, 20 rounds per Best-Moves, contraction and refinement."""

@@ -107,8 +107,7 @@ Engine::~Engine() {
   for (auto &e : bev_) cudaEventDestroy(e);
   Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                     &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
-                    &s_gtab_};
+                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
   for (Scratch *s : all) s->release(st_);
   cudaStreamSynchronize(st_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -118,8 +117,7 @@ Engine::~Engine() {
 size_t Engine::scratch_bytes() const {
   const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                           &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
-                    &s_gtab_};
+                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
   size_t t = 0;
   for (const Scratch *s : all) t += s->bytes;
   return t;
@@ -465,17 +463,7 @@ void Engine::round(std::vector<Job *> &js) {
   launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
   ++launches;
   if (timing) CK(cudaEventRecord(ev_[1], st_));
-  // global tables of the cluster kernels: GTAB_BYTES in all (keys and sums),
-  // split between the clusters in flight of each launch
-  GTab gt;
-  {
-    const int64_t slots = 1;  // the cluster kernels keep their tables in shared memory
-    unsigned long long *g = s_gtab_.get<unsigned long long>(2 * slots, st_);
-    gt.keys = g;
-    gt.vals = g + slots;
-    gt.stride = slots;  // total slots; each launch divides them
-  }
-  launch_bestmove(wide, dt, b, h, gt, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr);
+  launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_apply) {
     launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);

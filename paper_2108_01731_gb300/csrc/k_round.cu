@@ -224,18 +224,22 @@ __device__ __forceinline__ void write_desired(const JobView &J, int32_t v, int64
 
 // Linear-probing insert of (c, k32) += sum.  The table has at least twice as
 // many slots as keys, so a free or matching slot is found within cap probes.
-// `at(s, kp, vp)` gives the key and value pointers of slot s.
+// `at(s, kp, vp)` gives the key and value pointers of slot s.  `taken` is the
+// slot when this call stored the key there first, else NOSLOT.
+constexpr uint32_t NOSLOT = 0xFFFFFFFFu;
 template <class At>
 __device__ __forceinline__ bool probe_insert(At at, uint32_t cap, int lg, int32_t c, uint32_t k32,
-                                             long long sum) {
+                                             long long sum, uint32_t &taken) {
   const unsigned long long word = slot_word(c, k32);
   uint32_t s = slot_of(c, lg);
+  taken = NOSLOT;
   for (uint32_t t = 0; t < cap; ++t) {
     unsigned long long *kp, *vp;
     at(s, kp, vp);
     const unsigned long long prev = atomicCAS(kp, SLOT_EMPTY, word);
     if (prev == SLOT_EMPTY || (int32_t)(uint32_t)prev == c) {
       atomicAdd(vp, (unsigned long long)sum);
+      if (prev == SLOT_EMPTY) taken = s;
       return true;
     }
     s = (s + 1) & (cap - 1);
@@ -501,8 +505,11 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
 // entries whose home slot holds another cluster continue probing one by one.
 // Equal clusters need no pre-aggregation: every inserter of a cluster finds
 // its slot and adds to it (integer sums, so the order does not matter).
+// won[i] is the slot where entry i's cluster was stored first (by this
+// thread), else NOSLOT: each distinct cluster is won by exactly one thread.
 template <int E, class At>
-__device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, uint32_t cap, int lg) {
+__device__ __forceinline__ bool insert_chunk_won(const Chunk<E> &x, At at, uint32_t cap, int lg,
+                                                 uint32_t (&won)[E]) {
   unsigned long long prev[E];
   uint32_t home[E];
 #pragma unroll
@@ -519,16 +526,62 @@ __device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, uint32_t 
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < E; ++i) {
+    won[i] = NOSLOT;
     if (x.c[i] < 0) continue;
     if (prev[i] == SLOT_EMPTY || (int32_t)(uint32_t)prev[i] == x.c[i]) {
       unsigned long long *kp, *vp;
       at(home[i], kp, vp);
       atomicAdd(vp, (unsigned long long)x.w[i]);
+      if (prev[i] == SLOT_EMPTY) won[i] = home[i];
     } else {
-      ok &= probe_insert(at, cap, lg, x.c[i], x.k[i], x.w[i]);
+      ok &= probe_insert(at, cap, lg, x.c[i], x.k[i], x.w[i], won[i]);
     }
   }
   return ok;
+}
+
+template <int E, class At>
+__device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, uint32_t cap, int lg) {
+  uint32_t won[E];
+  return insert_chunk_won(x, at, cap, lg, won);
+}
+
+// Scores the clusters a thread won (once the sums are complete) and empties
+// their slots: best candidate, stay weight, and whether cluster id v occurs.
+template <typename S, int E, class At>
+__device__ __forceinline__ void scan_won(const JobView &J, const uint32_t (&won)[E], At at,
+                                         int32_t v, int32_t Lv, int64_t kv, S &best, int32_t &bc,
+                                         long long &w_stay, int &vseen, long long &ncand) {
+  const S q = (S)J.q, pk = (S)J.p * (S)kv;
+  unsigned long long word[E], val[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {  // all reads first (they may be remote)
+    word[i] = SLOT_EMPTY;
+    val[i] = 0;
+    if (won[i] != NOSLOT) {
+      unsigned long long *kp, *vp;
+      at(won[i], kp, vp);
+      word[i] = *kp;
+      val[i] = *vp;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (won[i] == NOSLOT) continue;
+    unsigned long long *kp, *vp;
+    at(won[i], kp, vp);
+    *kp = SLOT_EMPTY;
+    *vp = 0;
+    const int32_t c = (int32_t)(uint32_t)word[i];
+    if (c == Lv) {
+      w_stay += (long long)val[i];
+      continue;
+    }
+    vseen |= (c == v);
+    ++ncand;
+    const S sc = q * (S)(long long)val[i] - pk * (S)weight_of(J, c, (uint32_t)(word[i] >> 32));
+    if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
+  }
 }
 
 // Scans table slots s0, s0 + step, ... < s1 of a vertex: best candidate, stay
@@ -556,10 +609,40 @@ __device__ __forceinline__ void scan_slots(const JobView &J, const unsigned long
   }
 }
 
+// The same over a block's own share of a table, emptying each slot as it is
+// read (the next vertex finds the share empty after the closing sync).
+template <typename S>
+__device__ __forceinline__ void scan_slots_reset(const JobView &J, unsigned long long *keys,
+                                                 unsigned long long *vals, int s0, int s1,
+                                                 int step, int32_t v, int32_t Lv, int64_t kv,
+                                                 S &best, int32_t &bc, long long &w_stay,
+                                                 int &vseen, long long &ncand) {
+  const S q = (S)J.q, pk = (S)J.p * (S)kv;
+  for (int s = s0; s < s1; s += step) {
+    const unsigned long long word = keys[s];
+    if (word == SLOT_EMPTY) continue;
+    const long long val = (long long)vals[s];
+    keys[s] = SLOT_EMPTY;
+    vals[s] = 0;
+    const int32_t c = (int32_t)(uint32_t)word;
+    if (c == Lv) {
+      w_stay += val;
+      continue;
+    }
+    vseen |= (c == v);
+    ++ncand;
+    const S sc = q * (S)val - pk * (S)weight_of(J, c, (uint32_t)(word >> 32));
+    if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
+  }
+}
+
 // ----------------------------------- deg <= T_WARP: warp + shared table --
 
-// Blocks per SM held to what the shared tables allow, so that the register
-// allocation does not lower the occupancy.
+// One warp per vertex, lane t reads entries t, t + 32, ...  The warp's table
+// is emptied once at the start; afterwards every lane empties the slots it
+// won while scoring them, so each vertex costs one step per distinct cluster.
+// Blocks per SM are held to what the shared tables allow, so that the
+// register allocation does not lower the occupancy.
 template <typename S, int E, int BK>
 __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     k_bm_warp(const JobDev *__restrict__ jobs, Buckets b, int64_t *ctr) {
@@ -579,6 +662,11 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     kp = K0 + s;
     vp = V0 + s;
   };
+  for (int s = lane; s < CAP; s += 32) {
+    K0[s] = SLOT_EMPTY;
+    V0[s] = 0;
+  }
+  __syncwarp();
   for (int64_t it = (int64_t)blockIdx.x * WPB + wib; it < count; it += warps_total) {
     const uint64_t item = items[it];
     const JobView J = view_of(jobs + (int)(item >> 32));
@@ -590,18 +678,15 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     const Own o = own_of(J, v);
     const int cap = (int)next_pow2(2 * (int64_t)deg);
     const int lg = log2i(cap);
-    for (int s = lane; s < cap; s += 32) {
-      K0[s] = SLOT_EMPTY;
-      V0[s] = 0;
-    }
-    __syncwarp();
-    fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
+    uint32_t won[E];
+    fail |= !insert_chunk_won(x, at, (uint32_t)cap, lg, won);
     const bool row_moved = __any_sync(FULL, x.mv != 0);  // after the gathers have landed
+    __syncwarp();  // every lane's sums are in place
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
     long long w_stay = 0, nc = 0;
     int vseen = 0;
-    scan_slots<S>(J, K0, V0, lane, cap, 32, v, o.Lv, o.kv, best, bc, w_stay, vseen, nc);
+    scan_won<S, E>(J, won, at, v, o.Lv, o.kv, best, bc, w_stay, vseen, nc);
     w_stay = warp_sum_ll(w_stay);
     const bool v_seen = __any_sync(FULL, vseen);
     ncand += nc;
@@ -609,7 +694,7 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     if (lane == 0)
       write_desired<S>(J, v, deg, o.Lv, o.kv, o.KLv, best, bc, w_stay, v_seen, row_moved,
                        o.Kv);
-    __syncwarp();
+    __syncwarp();  // the emptied slots are seen by the next vertex's inserts
   }
   ncand = warp_sum_ll(ncand);
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
@@ -621,19 +706,22 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
 // --------------- deg <= 65536: one block or a cluster of CS blocks ---------
 
 // One vertex per cluster at a time; block r reads entries [r * per,
-// (r + 1) * per) of the row (E per thread per batch).  The table has cap =
-// next_pow2(2 deg) slots:
-//   GM = false: spread evenly over the CS blocks' shared memory (cap / CS <=
-//               TP per block), inserted with distributed-shared-memory atomics;
-//   GM = true:  in a global-memory region private to the cluster, small
-//               enough that the tables of all clusters in flight stay in L2;
-//               cluster size then sets the parallelism per vertex only.
-// Each block scans its share of the slots and block 0 combines.
-template <typename S, int CS, int THREADS, int TP, int E, int BK, bool GM>
+// (r + 1) * per) of the row, at most E per thread (the degree buckets keep
+// per <= THREADS * E).  The table has cap = next_pow2(2 deg) slots spread
+// evenly over the CS blocks' shared memory (cap / CS <= TP per block), reached
+// with distributed-shared-memory atomics when CS > 1.  The tables are emptied
+// once at the start; after the inserts, the thread that first stored a
+// cluster scores it and empties its slot (CS <= 2: a vertex costs one step
+// per distinct cluster), or each block scans and empties its own share
+// (CS >= 4), so no clearing pass is needed.  Block 0 combines the results.
+template <typename S, int CS, int THREADS, int TP, int E, int BK>
 __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
-                                                      GTab gt, int64_t *ctr) {
+                                                      int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;
+  // with 4 or more blocks most won slots are remote: each block then scans
+  // (and empties) its own share of the table instead
+  constexpr bool LOCAL_SCAN = CS >= 4;
   unsigned long long *tkey = (unsigned long long *)smem;
   unsigned long long *tval = tkey + TP;
   __shared__ S red_s[NW];
@@ -652,14 +740,15 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
   const uint64_t *items = b.items + b.seg_start[BK];
   const int64_t ncl = gridDim.x / CS;
   const int64_t cid = blockIdx.x / CS;
-  if (GM) {
-    tkey = gt.keys + cid * gt.stride;
-    tval = gt.vals + cid * gt.stride;
-  }
   long long ncand = 0;
   bool fail = false;
-  if (threadIdx.x == 0) s_rowmv = 0;
+  if (tid == 0) s_rowmv = 0;
+  for (int s = tid; s < TP; s += THREADS) {
+    tkey[s] = SLOT_EMPTY;
+    tval[s] = 0;
+  }
   PullCount::init();
+  if (CS > 1) cluster.sync();  // every block's table is empty before any remote insert
   for (int64_t it = cid; it < count; it += ncl) {
     const uint64_t item = items[it];
     const JobView J = view_of(jobs + (int)(item >> 32));
@@ -669,6 +758,7 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
     const int64_t per = (deg + CS - 1) / CS;
     const int64_t lo = (int64_t)rank * per;
     const int64_t hi = lo + per < deg ? lo + per : deg;
+    if (hi - lo > (int64_t)THREADS * E) fail = true;  // excluded by the degree buckets
     Chunk<E> x;
     load_chunk(J, beg, lo, hi, THREADS, tid, x);
     const Own o = own_of(J, v);
@@ -678,16 +768,8 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
     const int lg = log2i(capl);
     const uint32_t part = cap / CS;  // slots per block (a power of two)
     const int plg = log2i(part);
-    // block r clears (and later scans) slots [r * part, (r + 1) * part)
-    unsigned long long *mk = GM ? tkey + (size_t)rank * part : tkey;
-    unsigned long long *mv = GM ? tval + (size_t)rank * part : tval;
-    for (uint32_t s = tid; s < part; s += THREADS) {
-      mk[s] = SLOT_EMPTY;
-      mv[s] = 0;
-    }
-    if (CS > 1) cluster.sync(); else __syncthreads();
     auto at = [&](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
-      if (GM || CS == 1) {
+      if (CS == 1) {
         kp = tkey + s;
         vp = tval + s;
       } else {
@@ -696,22 +778,21 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
         vp = cluster.map_shared_rank(tval, r) + l;
       }
     };
-    fail |= !insert_chunk(x, at, cap, lg);
+    uint32_t won[E];
+    fail |= !insert_chunk_won(x, at, cap, lg, won);
     if (x.mv) s_rowmv = 1;
-    for (int64_t more = lo + (int64_t)THREADS * E; more < hi; more += (int64_t)THREADS * E) {
-      load_chunk(J, beg, more, hi, THREADS, tid, x);
-      fail |= !insert_chunk(x, at, cap, lg);
-      if (x.mv) s_rowmv = 1;
-    }
-    if (CS > 1) cluster.sync(); else __syncthreads();
+    if (CS > 1) cluster.sync(); else __syncthreads();  // sums complete
     const int32_t Lv = o.Lv;
     const int64_t kv = o.kv;
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
     long long w_stay = 0, nc = 0;
     int vseen = 0;
-    scan_slots<S>(J, mk, mv, tid, (int64_t)part, THREADS, v, Lv, kv, best, bc, w_stay, vseen,
-                  nc);
+    if (LOCAL_SCAN)
+      scan_slots_reset<S>(J, tkey, tval, tid, (int)part, THREADS, v, Lv, kv, best, bc, w_stay,
+                          vseen, nc);
+    else
+      scan_won<S, E>(J, won, at, v, Lv, kv, best, bc, w_stay, vseen, nc);
     ncand += nc;
     w_stay = warp_sum_ll(w_stay);
     const int vs = __any_sync(FULL, vseen);
@@ -747,6 +828,7 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
         }
       }
     }
+    // this sync also orders the emptied slots before the next vertex's inserts
     if (CS > 1) {
       cluster.sync();
       if (rank == 0 && tid == 0) {
@@ -1008,11 +1090,11 @@ struct TableLaunch {
   bool init = false;
 };
 
-template <typename S, int CS, int THREADS, int TP, int E, int BK, bool GM>
-void launch_table(const JobDev *jobs, const Buckets &b, const GTab &gt, int64_t *ctr,
-                  cudaStream_t st, TableLaunch &tl, int *launches, int64_t maxdeg) {
-  auto kern = k_bm_table<S, CS, THREADS, TP, E, BK, GM>;
-  const size_t smem = GM ? 0 : (size_t)TP * 16;
+template <typename S, int CS, int THREADS, int TP, int E, int BK>
+void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream_t st,
+                  TableLaunch &tl, int *launches) {
+  auto kern = k_bm_table<S, CS, THREADS, TP, E, BK>;
+  const size_t smem = (size_t)TP * 16;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1025,7 +1107,7 @@ void launch_table(const JobDev *jobs, const Buckets &b, const GTab &gt, int64_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (!tl.init) {
-    if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cfg.gridDim = dim3(CS);
     int ncl = 0;
@@ -1034,21 +1116,14 @@ void launch_table(const JobDev *jobs, const Buckets &b, const GTab &gt, int64_t 
     tl.init = true;
   }
   int64_t ncl = tl.clusters;
-  GTab g2 = gt;
-  if (GM) {  // one table region per cluster; all of them within the L2 budget
-    g2.stride = next_pow2(2 * maxdeg);
-    const int64_t by_l2 = gt.stride / g2.stride;
-    if (by_l2 < ncl) ncl = by_l2 > 0 ? by_l2 : 1;
-  }
   if (b.seg_cap[BK] < ncl) ncl = b.seg_cap[BK];
   cfg.gridDim = dim3((unsigned)(ncl * CS));
-  cudaLaunchKernelEx(&cfg, kern, jobs, b, g2, ctr);
+  cudaLaunchKernelEx(&cfg, kern, jobs, b, ctr);
   ++*launches;
 }
 
 template <typename S>
-void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, const GTab &gt,
-                   int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d, int *launches,
+void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d, int *launches,
                    cudaEvent_t *ev) {
   auto mark = [&](int bk) {
     if (ev) cudaEventRecord(ev[bk], st);
@@ -1110,27 +1185,22 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, const
   }
   mark(B_WARP);
   if (b.seg_cap[B_BLK] > 0)
-    launch_table<S, 1, 256, BLK_CAP, T_BLK / 256, B_BLK, false>(jobs, b, gt, ctr, st, tl[0],
-                                                                 launches, T_BLK);
+    launch_table<S, 1, 256, BLK_CAP, T_BLK / 256, B_BLK>(jobs, b, ctr, st, tl[0], launches);
   mark(B_BLK);
   if (b.seg_cap[B_C1] > 0)
-    launch_table<S, 1, 1024, PART, 4, B_C1, false>(jobs, b, gt, ctr, st, tl[1], launches, T_C1);
+    launch_table<S, 1, 1024, PART, 4, B_C1>(jobs, b, ctr, st, tl[1], launches);
   mark(B_C1);
   if (b.seg_cap[B_C2] > 0)
-    launch_table<S, 2, 1024, PART, 4, B_C2, false>(jobs, b, gt, ctr, st, tl[2], launches,
-                                                   2 * T_C1);
+    launch_table<S, 2, 1024, PART, 4, B_C2>(jobs, b, ctr, st, tl[2], launches);
   mark(B_C2);
   if (b.seg_cap[B_C4] > 0)
-    launch_table<S, 4, 1024, PART, 4, B_C4, false>(jobs, b, gt, ctr, st, tl[3], launches,
-                                                   4 * T_C1);
+    launch_table<S, 4, 1024, PART, 4, B_C4>(jobs, b, ctr, st, tl[3], launches);
   mark(B_C4);
   if (b.seg_cap[B_C8] > 0)
-    launch_table<S, 8, 1024, PART, 4, B_C8, false>(jobs, b, gt, ctr, st, tl[4], launches,
-                                                   8 * T_C1);
+    launch_table<S, 8, 1024, PART, 4, B_C8>(jobs, b, ctr, st, tl[4], launches);
   mark(B_C8);
   if (b.seg_cap[B_C16] > 0)
-    launch_table<S, 16, 1024, PART, 4, B_C16, false>(jobs, b, gt, ctr, st, tl[5], launches,
-                                                     16 * T_C1);
+    launch_table<S, 16, 1024, PART, 4, B_C16>(jobs, b, ctr, st, tl[5], launches);
   mark(B_C16);
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
@@ -1151,12 +1221,12 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, const
 }  // namespace
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     const GTab &gt, int64_t hub_passes, int64_t *ctr, cudaStream_t st,
-                     const Dev &d, int *launches, cudaEvent_t *ev) {
+                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
+                     int *launches, cudaEvent_t *ev) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, gt, hub_passes, ctr, st, d, launches, ev);
+    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev);
   else
-    bestmove_impl<int64_t>(jobs, b, h, gt, hub_passes, ctr, st, d, launches, ev);
+    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev);
 }
 
 // --------------------------------------------------------------- apply ----

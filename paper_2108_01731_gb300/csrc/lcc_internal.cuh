@@ -149,16 +149,6 @@ struct Buckets {
   int64_t *cnt;       // [NB] device counters
 };
 
-// Global-memory tables of the cluster kernels: cluster i of a launch owns
-// slots [i * stride, (i + 1) * stride) of keys and of vals.
-struct GTab {
-  unsigned long long *keys;
-  unsigned long long *vals;
-  int64_t stride;
-};
-// Table bytes the cluster kernels keep live at once (sized to stay in L2).
-constexpr int64_t GTAB_BYTES = (int64_t)64 << 20;
-
 struct HubBufs {
   unsigned long long *keys;  // one window of tables: [window + largest table] slots
   int64_t *vals;
@@ -302,8 +292,8 @@ void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
 // ev (nullable, NB events): ev[b] is recorded after degree bucket b's kernels.
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
-                     const GTab &gt, int64_t hub_passes, int64_t *ctr, cudaStream_t st,
-                     const Dev &d, int *launches, cudaEvent_t *ev);
+                     int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
+                     int *launches, cudaEvent_t *ev);
 // jmoves[2j] = moves of job j, jmoves[2j + 1] = entries of its movers' rows.
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);

@@ -540,9 +540,11 @@ struct lcc_server {
 };
 
 static int64_t job_estimate(int64_t n, int64_t nnz, bool weighted) {
-  // CSR + level-0 state + the first level's contraction workspace
+  // CSR + level-0 state + the first level's contraction workspace, and the
+  // gather layout (positions and remapped neighbours) of large levels
   const int64_t csr = (n + 1) * 8 + nnz * (weighted ? 8 : 4);
-  return 2 * csr + n * 64 + nnz * 56 + (1 << 20);
+  const int64_t layout = n * 8 > layout_min_bytes() ? 2 * (n * 4 + nnz * 4) : 0;
+  return 2 * csr + n * 64 + nnz * 56 + layout + (1 << 20);
 }
 
 static void finish_job(lcc_server *s, SJob *j, lcc_status st, const std::string &err) {

@@ -38,6 +38,18 @@ static int64_t hub_window() {
   return (int64_t)1 << 27;
 }
 
+// Packed-word bytes above which a level gets a gather layout; the
+// LCC_LAYOUT_MIN_BYTES environment variable overrides it (tests use 0 so that
+// small graphs run through the layout too).
+int64_t layout_min_bytes() {
+  const char *e = getenv("LCC_LAYOUT_MIN_BYTES");
+  if (e && *e) {
+    const long long v = atoll(e);
+    if (v >= 0) return (int64_t)v;
+  }
+  return LAYOUT_MIN_BYTES;
+}
+
 void check_cuda(cudaError_t e, const char *what, int line) {
   if (e == cudaSuccess) return;
   if (e == cudaErrorMemoryAllocation) {
@@ -107,7 +119,7 @@ Engine::~Engine() {
   for (auto &e : bev_) cudaEventDestroy(e);
   Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                     &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,    &s_layout_};
   for (Scratch *s : all) s->release(st_);
   cudaStreamSynchronize(st_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -117,7 +129,8 @@ Engine::~Engine() {
 size_t Engine::scratch_bytes() const {
   const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                           &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_};
+                          &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
+                          &s_layout_};
   size_t t = 0;
   for (const Scratch *s : all) t += s->bytes;
   return t;
@@ -167,6 +180,8 @@ static LJob ljob_of(const Level &L) {
   x.L = L.L;
   x.K = L.K;
   x.D = L.D;
+  x.pos = L.pos;
+  x.gnbr = L.gnbr;
   x.n = L.n;
   x.wtype = L.wtype;
   return x;
@@ -217,6 +232,32 @@ void Engine::level_stats(std::vector<Job *> &js, std::vector<Level *> &lvs) {
     lvs[i]->info = h[i];
     lvs[i]->wide = needs_wide(*lvs[i], js[i]->p, js[i]->q, js[i]->ktot);
   }
+}
+
+void Engine::build_layout(std::vector<Level *> &lvs, std::vector<Store *> &stores) {
+  std::vector<LJob> tab;
+  std::vector<int64_t> vs(1, 0), es(1, 0);
+  for (size_t i = 0; i < lvs.size(); ++i) {
+    Level &L = *lvs[i];
+    if (!L.lk || L.n * (int64_t)sizeof(unsigned long long) <= layout_min_bytes()) continue;
+    L.pos = stores[i]->alloc<int32_t>(L.n);
+    L.gnbr = stores[i]->alloc<int32_t>(L.info.nnz);
+    tab.push_back(ljob_of(L));
+    vs.push_back(vs.back() + L.n);
+    es.push_back(es.back() + L.info.nnz);
+  }
+  const int nj = (int)tab.size();
+  if (nj == 0) return;
+  std::vector<int64_t> ves(vs);
+  ves.insert(ves.end(), es.begin(), es.end());
+  LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(2 * (nj + 1), st_);
+  int64_t *cnt = s_layout_.get<int64_t>(nj * LAYOUT_CLASSES, st_);
+  upload_table(tab, ves, dt, dv, stage(nj * sizeof(LJob) + ves.size() * 8), st_);
+  CK(cudaMemsetAsync(cnt, 0, nj * LAYOUT_CLASSES * sizeof(int64_t), st_));
+  launch_layout(dt, dv, dv + (nj + 1), nj, vs.back(), es.back(), cnt, st_, d_);
+  note_launches(4);
+  sync_checked(st_);  // staging reuse
 }
 
 void Engine::init_levels(std::vector<Level *> &lvs) {
@@ -308,6 +349,8 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
     j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
     // cluster weights fit the 32-bit half of the packed label word
     if (j->ktot >= (int64_t)KNONE) j->lv[0].lk = nullptr;
+    std::vector<Store *> stores = {j->base.get()};
+    build_layout(lvs, stores);
   }
   Level &L = j->lv[0];
   if (init_labels_host) {
@@ -379,6 +422,8 @@ void Engine::round(std::vector<Job *> &js) {
     x.fr = L.fr;
     x.cl = L.cl;
     x.lk = L.lk;
+    x.pos = L.pos;
+    x.gnbr = L.gnbr ? L.gnbr : L.nbr;
     x.n = L.n;
     x.p = J->p;
     x.q = J->q;
@@ -674,6 +719,10 @@ void Engine::contract(std::vector<Job *> &js) {
   }
   for (Job *J : grow) newlv.push_back(&J->lv[J->depth]);
   level_stats(grow, newlv);
+  {
+    std::vector<Store *> stores(newlv.size(), store.get());
+    build_layout(newlv, stores);
+  }
   init_levels(newlv);
   if (timing) {
     CK(cudaEventRecord(ev_[5], st_));

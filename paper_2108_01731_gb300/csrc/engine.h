@@ -31,6 +31,7 @@ inline void sync_checked(cudaStream_t st) {
 }
 
 extern std::atomic<long long> g_launches;
+int64_t layout_min_bytes();
 inline void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Stream-ordered device allocation from a per-device pool that keeps freed
@@ -104,6 +105,8 @@ struct Level {
   uint8_t *fr = nullptr;
   uint8_t *cl = nullptr;
   unsigned long long *lk = nullptr;  // packed (K[L[u]], L[u]); null if K can exceed 32 bits
+  int32_t *pos = nullptr;            // gather layout (null: identity), see JobDev
+  int32_t *gnbr = nullptr;
   int32_t *map = nullptr;  // vertex -> coarse vertex of the next level
   std::shared_ptr<Store> store;
   std::shared_ptr<Store> map_store;
@@ -184,6 +187,9 @@ class Engine {
   void up(std::vector<Job *> &js);
   void finalize(std::vector<Job *> &js);
   void level_stats(std::vector<Job *> &js, std::vector<Level *> &lvs);
+  // Gather layout for the levels (with packed words) that are large enough;
+  // its arrays come from stores[i].
+  void build_layout(std::vector<Level *> &lvs, std::vector<Store *> &stores);
   void init_levels(std::vector<Level *> &lvs);
   void end_bm(Job *j);
   float elapsed(cudaEvent_t a, cudaEvent_t b);
@@ -195,7 +201,7 @@ class Engine {
   // scratch
   Scratch s_jobs_, s_vstart_, s_items_, s_cnt_, s_ctr_, s_jmoves_, s_moved_;
   Scratch s_hkeys_, s_hvals_, s_hmeta_, s_hpart_s_, s_hpart_c_, s_hstay_, s_hiso_;
-  Scratch s_ljobs_, s_info_, s_obj_;
+  Scratch s_ljobs_, s_info_, s_obj_, s_layout_;
   // pinned host staging
   void *h_stage_ = nullptr;
   size_t h_stage_bytes_ = 0;

@@ -105,6 +105,103 @@ void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int6
   k_level_stats<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, info);
 }
 
+// ---------------------------------------------------------- gather layout --
+
+// Where each vertex's packed label word is kept for the best-move gathers:
+// vertices in decreasing degree class, so that the words most rows refer to
+// share a few L2-sized regions (on power-law graphs a small fraction of the
+// vertices receives most entries).  Only storage positions change: labels,
+// clusters and every result stay in terms of the vertex ids.
+
+__device__ __forceinline__ int degree_class(int64_t deg) {
+  return deg <= 0 ? 0 : 64 - __clzll((long long)deg);  // 1 + floor(log2 deg)
+}
+
+__device__ __forceinline__ unsigned lanemask_lt_l() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void k_layout_count(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                               int njobs, int64_t vtot, int64_t *cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < vtot;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    int key = -1;
+    if (i < vtot) {
+      const int j = find_job(vstart, njobs, i);
+      const int64_t v = i - vstart[j];
+      key = j * LAYOUT_CLASSES + degree_class(jobs[j].off[v + 1] - jobs[j].off[v]);
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    if (key >= 0 && lane == __ffs(peers) - 1)
+      atomicAdd((unsigned long long *)&cnt[key], (unsigned long long)__popc(peers));
+  }
+}
+
+// One thread per job: class counts -> first position of each class, highest
+// class first (in place).
+__global__ void k_layout_base(int njobs, int64_t *cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= njobs) return;
+  int64_t run = 0;
+  for (int c = LAYOUT_CLASSES - 1; c >= 0; --c) {
+    const int64_t x = cnt[j * LAYOUT_CLASSES + c];
+    cnt[j * LAYOUT_CLASSES + c] = run;
+    run += x;
+  }
+}
+
+// pos[v] = next free position of v's class (positions within a class are
+// taken in no particular order; any order is a valid layout).
+__global__ void k_layout_place(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                               int njobs, int64_t vtot, int64_t *cur) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < vtot;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    int key = -1, j = 0;
+    int64_t v = 0;
+    if (i < vtot) {
+      j = find_job(vstart, njobs, i);
+      v = i - vstart[j];
+      key = j * LAYOUT_CLASSES + degree_class(jobs[j].off[v + 1] - jobs[j].off[v]);
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    if (key >= 0) {
+      const int leader = __ffs(peers) - 1;
+      unsigned long long p0 = 0;
+      if (lane == leader)
+        p0 = atomicAdd((unsigned long long *)&cur[key], (unsigned long long)__popc(peers));
+      p0 = __shfl_sync(peers, p0, leader);
+      jobs[j].pos[v] = (int32_t)(p0 + __popc(peers & lanemask_lt_l()));
+    }
+  }
+}
+
+// gnbr[e] = pos[nbr[e]] over the flat entry space of all jobs.
+__global__ void k_layout_nbr(const LJob *__restrict__ jobs, const int64_t *__restrict__ estart,
+                             int njobs, int64_t etot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < etot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(estart, njobs, i);
+    const LJob &J = jobs[j];
+    const int64_t e = i - estart[j];
+    J.gnbr[e] = __ldg(J.pos + __ldg(J.nbr + e));
+  }
+}
+
+void launch_layout(const LJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
+                   int64_t vtot, int64_t etot, int64_t *cnt, cudaStream_t st, const Dev &d) {
+  if (vtot <= 0) return;
+  k_layout_count<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, cnt);
+  k_layout_base<<<(njobs + 127) / 128, 128, 0, st>>>(njobs, cnt);
+  k_layout_place<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, cnt);
+  if (etot > 0) k_layout_nbr<<<grid_for(etot, 256, d), 256, 0, st>>>(jobs, estart, njobs, etot);
+}
+
 // ------------------------------------------------------- per-vertex maps --
 
 __global__ void k_init_level(const LJob *__restrict__ jobs, const int64_t *__restrict__ vstart,

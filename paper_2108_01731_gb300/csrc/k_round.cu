@@ -92,7 +92,7 @@ struct JobView {
 __device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
   JobView x;
   x.off = J->off;
-  x.nbr = J->nbr;
+  x.nbr = J->gnbr;  // neighbour positions in the gather layout
   x.w = J->w;
   x.k = J->k;
   x.L = J->L;
@@ -151,9 +151,9 @@ __device__ __forceinline__ int32_t decide(const JobView &J, int32_t v, int32_t L
   return (bc != INT32_MAX && best > stay) ? bc : Lv;
 }
 
-// Weight of v's own cluster from the snapshot.
+// Weight of v's own cluster (K does not change during the best-move kernels).
 __device__ __forceinline__ int64_t own_weight(const JobView &J, int32_t v, int32_t Lv) {
-  return J.lk ? (int64_t)(__ldg(J.lk + v) >> 32) : J.K[Lv];
+  return J.K[Lv];
 }
 
 // The scalars of v that the final decision needs.
@@ -164,14 +164,8 @@ struct Own {
 // Issued early so the loads overlap the row's gathers.
 __device__ __forceinline__ Own own_of(const JobView &J, int32_t v) {
   Own o;
-  if (J.lk) {
-    const unsigned long long x = __ldg(J.lk + v);
-    o.Lv = (int32_t)((uint32_t)x & ~LK_MOVED);
-    o.KLv = (int64_t)(x >> 32);
-  } else {
-    o.Lv = J.L[v];
-    o.KLv = J.K[o.Lv];
-  }
+  o.Lv = J.L[v];
+  o.KLv = J.K[o.Lv];
   o.kv = J.k[v];
   o.Kv = J.K[v];
   return o;
@@ -300,7 +294,8 @@ __global__ void __launch_bounds__(FR_T) k_frontier(const JobDev *__restrict__ jo
         if (m) J->fr[v] = 0;
         const bool pull = (J->flags & JF_PULL) != 0;
         if (J->lk)
-          J->lk[v] = slot_word(Lv, (uint32_t)J->K[Lv]) | (pull && (m & 2) ? LK_MOVED : 0u);
+          J->lk[J->pos ? J->pos[v] : v] =
+              slot_word(Lv, (uint32_t)J->K[Lv]) | (pull && (m & 2) ? LK_MOVED : 0u);
         deg = J->off[v + 1] - J->off[v];
         bool f;
         if (J->flags & JF_ALL)

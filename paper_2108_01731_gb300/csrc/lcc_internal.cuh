@@ -109,8 +109,12 @@ struct JobDev {
   int32_t *D;
   uint8_t *fr;
   uint8_t *cl;
-  // per round: lk[u] = K[L[u]] << 32 | L[u]; null when K can reach 2^32 - 1
+  // per round: lk[pos[u]] = K[L[u]] << 32 | L[u]; null when K can reach 2^32 - 1
   unsigned long long *lk;
+  // gather layout (null: identity): pos[u] is where u's packed word is kept,
+  // and gnbr[e] = pos[nbr[e]] is what the best-move kernels gather through
+  const int32_t *pos;
+  const int32_t *gnbr;  // = nbr without a layout
   int64_t n;
   int64_t p, q;
   // the next round tests V' in the kernels (JF_PULL) instead of marking it
@@ -188,10 +192,18 @@ struct LJob {
   int32_t *D;
   const int32_t *map;     // flatten: coarse vertex of each vertex
   const int32_t *Lcoarse; // flatten: labels of the coarse level
+  int32_t *pos;           // gather layout (see JobDev)
+  int32_t *gnbr;
   int64_t n;
   int32_t wtype;
   int32_t pad;
 };
+
+// Degree classes of the gather layout: 0 for an isolated vertex, else
+// 1 + floor(log2 deg); positions are handed out from the highest class down.
+constexpr int LAYOUT_CLASSES = 34;
+// Levels whose packed words take more than this many bytes get a layout.
+constexpr int64_t LAYOUT_MIN_BYTES = (int64_t)64 << 20;
 
 // Per-job results of the level statistics kernel.
 struct LevelInfo {
@@ -304,6 +316,11 @@ void launch_mark(const JobDev *jobs, const uint64_t *moved, int64_t *ctr, const 
 // Level kernels (k_level.cu).
 void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                         LevelInfo *info, cudaStream_t st, const Dev &d);
+// Gather layout of a level per job (k_level.cu): cnt is [njobs *
+// LAYOUT_CLASSES] zeroed int64 scratch; estart[j] = first flat entry of job j
+// (estart[njobs] = all entries).
+void launch_layout(const LJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
+                   int64_t vtot, int64_t etot, int64_t *cnt, cudaStream_t st, const Dev &d);
 void launch_init_level(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                        cudaStream_t st, const Dev &d);
 void launch_degree_k(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,

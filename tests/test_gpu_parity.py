@@ -158,6 +158,27 @@ CLUSTER_CASES = [
 @pytest.mark.parametrize("case", CLUSTER_CASES, ids=lambda c: "%s-%d-%d/%d-%s" % (
     c[0], c[1], c[2], c[3], "-".join("%s%s" % kv for kv in sorted(c[4].items()))))
 def test_cluster_matches_oracle(L, case):
+    check_cluster_case(L, case)
+
+
+def test_gather_layout_matches_oracle(L, monkeypatch):
+    """The degree-ordered storage of the packed label words (forced here on
+    graphs far below the size that gets it by default) moves words only:
+    labels, objective and every counter stay the oracle's."""
+    monkeypatch.setenv("LCC_LAYOUT_MIN_BYTES", "0")
+    for case in CLUSTER_CASES:
+        check_cluster_case(L, case)
+    g = GRAPHS["rmat"]
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    k, two_m = O.weighted_degrees(g["off"], g["w"])
+    L0 = np.arange(g["n"], dtype=np.int32)
+    got, _, rounds = L.lcc_best_moves(G, 1, 1, L.LCC_NODEW_DEGREE, 4, 1, L0)
+    want, _, wrounds = O.best_moves(g["off"], g["nbr"], g["w"], k, 1, two_m, L0, 4)
+    assert rounds == wrounds and np.array_equal(got, want)
+    G.free()
+
+
+def check_cluster_case(L, case):
     name, mode, p, q, kw = case
     g = GRAPHS[name]
     k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None

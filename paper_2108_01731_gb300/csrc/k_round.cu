@@ -24,6 +24,7 @@
 // spread over the distributed shared memory of a 2..16-block cluster; above
 // that in global-memory tables processed in bounded windows.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "lcc_internal.cuh"
 
@@ -40,12 +41,37 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-__device__ __forceinline__ uint32_t slot_of(int32_t c, int lg) {
-  const uint64_t h = (uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull;
-  return (uint32_t)(h >> (64 - lg));
+// Home slot of cluster c in a table of cap slots: the high half of a
+// multiplicative (Fibonacci) hash scaled to [0, cap); for cap = 2^lg these
+// are the hash's top lg bits.  Probing continues at the next slot, wrapping.
+__device__ __forceinline__ uint32_t slot_in(int32_t c, uint32_t cap) {
+  const uint32_t h = (uint32_t)(((uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull) >> 32);
+  return (uint32_t)(((uint64_t)h * cap) >> 32);
+}
+__device__ __forceinline__ uint32_t next_slot(uint32_t s, uint32_t cap) {
+  return s + 1 < cap ? s + 1 : 0;
 }
 
+
 __device__ __forceinline__ int log2i(int64_t pow2) { return 63 - __clzll((long long)pow2); }
+
+// Table geometry for the insert helpers: a power-of-two capacity (home slot
+// = top bits of the hash, probing by masking) or any capacity.
+struct Pow2Cap {
+  uint32_t cap;
+  int lg;
+  __device__ __forceinline__ explicit Pow2Cap(uint32_t c) : cap(c), lg(log2i((int64_t)c)) {}
+  __device__ __forceinline__ uint32_t home(int32_t c) const {
+    return (uint32_t)(((uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull) >> (64 - lg));
+  }
+  __device__ __forceinline__ uint32_t next(uint32_t s) const { return (s + 1) & (cap - 1); }
+};
+struct AnyCap {
+  uint32_t cap;
+  __device__ __forceinline__ explicit AnyCap(uint32_t c) : cap(c) {}
+  __device__ __forceinline__ uint32_t home(int32_t c) const { return slot_in(c, cap); }
+  __device__ __forceinline__ uint32_t next(uint32_t s) const { return next_slot(s, cap); }
+};
 
 __device__ __forceinline__ int64_t seg_count(const Buckets &b, int bk) {
   const int64_t c = b.cnt[bk];
@@ -221,13 +247,13 @@ __device__ __forceinline__ void write_desired(const JobView &J, int32_t v, int64
 // `at(s, kp, vp)` gives the key and value pointers of slot s.  `taken` is the
 // slot when this call stored the key there first, else NOSLOT.
 constexpr uint32_t NOSLOT = 0xFFFFFFFFu;
-template <class At>
-__device__ __forceinline__ bool probe_insert(At at, uint32_t cap, int lg, int32_t c, uint32_t k32,
+template <class At, class Cap>
+__device__ __forceinline__ bool probe_insert(At at, Cap g, int32_t c, uint32_t k32,
                                              long long sum, uint32_t &taken) {
   const unsigned long long word = slot_word(c, k32);
-  uint32_t s = slot_of(c, lg);
+  uint32_t s = g.home(c);
   taken = NOSLOT;
-  for (uint32_t t = 0; t < cap; ++t) {
+  for (uint32_t t = 0; t < g.cap; ++t) {
     unsigned long long *kp, *vp;
     at(s, kp, vp);
     const unsigned long long prev = atomicCAS(kp, SLOT_EMPTY, word);
@@ -236,7 +262,7 @@ __device__ __forceinline__ bool probe_insert(At at, uint32_t cap, int lg, int32_
       if (prev == SLOT_EMPTY) taken = s;
       return true;
     }
-    s = (s + 1) & (cap - 1);
+    s = g.next(s);
   }
   return false;
 }
@@ -502,8 +528,8 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
 // its slot and adds to it (integer sums, so the order does not matter).
 // won[i] is the slot where entry i's cluster was stored first (by this
 // thread), else NOSLOT: each distinct cluster is won by exactly one thread.
-template <int E, class At>
-__device__ __forceinline__ bool insert_chunk_won(const Chunk<E> &x, At at, uint32_t cap, int lg,
+template <int E, class At, class Cap>
+__device__ __forceinline__ bool insert_chunk_won(const Chunk<E> &x, At at, Cap g,
                                                  uint32_t (&won)[E]) {
   unsigned long long prev[E];
   uint32_t home[E];
@@ -512,7 +538,7 @@ __device__ __forceinline__ bool insert_chunk_won(const Chunk<E> &x, At at, uint3
     prev[i] = 0;
     home[i] = 0;
     if (x.c[i] >= 0) {
-      home[i] = slot_of(x.c[i], lg);
+      home[i] = g.home(x.c[i]);
       unsigned long long *kp, *vp;
       at(home[i], kp, vp);
       prev[i] = atomicCAS(kp, SLOT_EMPTY, slot_word(x.c[i], x.k[i]));
@@ -529,16 +555,16 @@ __device__ __forceinline__ bool insert_chunk_won(const Chunk<E> &x, At at, uint3
       atomicAdd(vp, (unsigned long long)x.w[i]);
       if (prev[i] == SLOT_EMPTY) won[i] = home[i];
     } else {
-      ok &= probe_insert(at, cap, lg, x.c[i], x.k[i], x.w[i], won[i]);
+      ok &= probe_insert(at, g, x.c[i], x.k[i], x.w[i], won[i]);
     }
   }
   return ok;
 }
 
-template <int E, class At>
-__device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, uint32_t cap, int lg) {
+template <int E, class At, class Cap>
+__device__ __forceinline__ bool insert_chunk(const Chunk<E> &x, At at, Cap g) {
   uint32_t won[E];
-  return insert_chunk_won(x, at, cap, lg, won);
+  return insert_chunk_won(x, at, g, won);
 }
 
 // Scores the clusters a thread won (once the sums are complete) and empties
@@ -672,9 +698,8 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     load_chunk(J, beg, 0, deg, 32, lane, x);
     const Own o = own_of(J, v);
     const int cap = (int)next_pow2(2 * (int64_t)deg);
-    const int lg = log2i(cap);
     uint32_t won[E];
-    fail |= !insert_chunk_won(x, at, (uint32_t)cap, lg, won);
+    fail |= !insert_chunk_won(x, at, Pow2Cap((uint32_t)cap), won);
     const bool row_moved = __any_sync(FULL, x.mv != 0);  // after the gathers have landed
     __syncwarp();  // every lane's sums are in place
     S best = ScoreOps<S>::lowest();
@@ -701,22 +726,24 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
 // --------------- deg <= 65536: one block or a cluster of CS blocks ---------
 
 // One vertex per cluster at a time; block r reads entries [r * per,
-// (r + 1) * per) of the row, at most E per thread (the degree buckets keep
-// per <= THREADS * E).  The table has cap = next_pow2(2 deg) slots spread
-// evenly over the CS blocks' shared memory (cap / CS <= TP per block), reached
-// with distributed-shared-memory atomics when CS > 1.  The tables are emptied
-// once at the start; after the inserts, the thread that first stored a
-// cluster scores it and empties its slot (CS <= 2: a vertex costs one step
-// per distinct cluster), or each block scans and empties its own share
-// (CS >= 4), so no clearing pass is needed.  Block 0 combines the results.
-template <typename S, int CS, int THREADS, int TP, int E, int BK>
+// (r + 1) * per) of the row in CH chunks of E per thread (the degree buckets
+// keep per <= THREADS * E * CH).  The table has 1.6 slots per entry of the
+// row (load <= 0.625, any size: home slots are scaled hashes), P slots in
+// each block's shared memory (P <= TP), slot s in block s % CS, reached with
+// distributed-shared-memory atomics when CS > 1.  The tables are emptied once
+// at the start; after the inserts either the thread that first stored a
+// cluster scores it and empties its slot (one chunk and CS <= 2: a vertex
+// costs one step per distinct cluster), or each block scans and empties its
+// own share, so no clearing pass is needed.  Block 0 combines the results.
+template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK>
 __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
                                                       int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;
-  // with 4 or more blocks most won slots are remote: each block then scans
-  // (and empties) its own share of the table instead
-  constexpr bool LOCAL_SCAN = CS >= 4;
+  // with several chunks, or with 4 or more blocks (most won slots remote),
+  // each block scans (and empties) its own share of the table instead
+  constexpr bool LOCAL_SCAN = CS >= 4 || CH > 1;
+  constexpr int CSLG = CS >= 16 ? 4 : CS >= 8 ? 3 : CS >= 4 ? 2 : CS >= 2 ? 1 : 0;
   unsigned long long *tkey = (unsigned long long *)smem;
   unsigned long long *tval = tkey + TP;
   __shared__ S red_s[NW];
@@ -753,29 +780,49 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
     const int64_t per = (deg + CS - 1) / CS;
     const int64_t lo = (int64_t)rank * per;
     const int64_t hi = lo + per < deg ? lo + per : deg;
-    if (hi - lo > (int64_t)THREADS * E) fail = true;  // excluded by the degree buckets
+    if (hi - lo > (int64_t)THREADS * E * CH) fail = true;  // excluded by the degree buckets
     Chunk<E> x;
     load_chunk(J, beg, lo, hi, THREADS, tid, x);
     const Own o = own_of(J, v);
-    int64_t capl = next_pow2(2 * deg);
-    if (capl < 2 * CS) capl = 2 * CS;
-    const uint32_t cap = (uint32_t)capl;
-    const int lg = log2i(capl);
-    const uint32_t part = cap / CS;  // slots per block (a power of two)
-    const int plg = log2i(part);
+    // P slots per block: POW2, next_pow2(2 deg) / CS (at least 32); else 1.6
+    // per entry of the row, a multiple of 32
+    int64_t P;
+    if (POW2) {
+      P = next_pow2(2 * deg) / CS;
+      if (P < 32) P = 32;
+    } else {
+      P = (deg * 8 + 5 * CS - 1) / (5 * CS);
+      P = (P + 31) & ~(int64_t)31;
+    }
+    if (P > TP) {  // excluded by the degree buckets
+      P = TP;
+      fail = true;
+    }
+    const uint32_t part = (uint32_t)P;
+    const uint32_t cap = part * CS;
+    using Cap = typename std::conditional<POW2, Pow2Cap, AnyCap>::type;
+    const Cap geo(cap);
     auto at = [&](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
       if (CS == 1) {
         kp = tkey + s;
         vp = tval + s;
       } else {
-        const unsigned r = s >> plg, l = s & (part - 1);
+        const unsigned r = s & (CS - 1), l = s >> CSLG;
         kp = cluster.map_shared_rank(tkey, r) + l;
         vp = cluster.map_shared_rank(tval, r) + l;
       }
     };
     uint32_t won[E];
-    fail |= !insert_chunk_won(x, at, cap, lg, won);
-    if (x.mv) s_rowmv = 1;
+    if (CH == 1) {
+      fail |= !insert_chunk_won(x, at, geo, won);
+      if (x.mv) s_rowmv = 1;
+    } else {
+      Chunk<E> y;  // the second chunk's gathers overlap the first chunk's inserts
+      load_chunk(J, beg, lo + (int64_t)THREADS * E, hi, THREADS, tid, y);
+      fail |= !insert_chunk(x, at, geo);
+      fail |= !insert_chunk(y, at, geo);
+      if (x.mv | y.mv) s_rowmv = 1;
+    }
     if (CS > 1) cluster.sync(); else __syncthreads();  // sums complete
     const int32_t Lv = o.Lv;
     const int64_t kv = o.kv;
@@ -966,7 +1013,6 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
     const int64_t beg = J.off[v];
     const int64_t deg = J.off[v + 1] - beg;
     const int64_t cap = hub_cap(deg);
-    const int lg = log2i(cap);
     unsigned long long *tkey = h.keys + (h.tbl_off[hh] - lo);
     unsigned long long *tval = (unsigned long long *)(h.vals + (h.tbl_off[hh] - lo));
     auto at = [tkey, tval](uint32_t s, unsigned long long *&kp, unsigned long long *&vp) {
@@ -979,7 +1025,7 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
     Chunk<HUB_CHUNK / 256> x;
     load_chunk(J, beg, e_lo, e_hi, 256, tid, x);
     if (__any_sync(FULL, x.mv != 0) && lane == 0) atomicOr(&h.iso_seen[hh], 2);
-    fail |= !insert_chunk(x, at, (uint32_t)cap, lg);
+    fail |= !insert_chunk(x, at, AnyCap((uint32_t)cap));
   }
   if (__any_sync(FULL, fail) && lane == 0)
     atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
@@ -1085,10 +1131,10 @@ struct TableLaunch {
   bool init = false;
 };
 
-template <typename S, int CS, int THREADS, int TP, int E, int BK>
+template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK>
 void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream_t st,
                   TableLaunch &tl, int *launches) {
-  auto kern = k_bm_table<S, CS, THREADS, TP, E, BK>;
+  auto kern = k_bm_table<S, CS, THREADS, TP, E, CH, POW2, BK>;
   const size_t smem = (size_t)TP * 16;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -1180,23 +1226,23 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   }
   mark(B_WARP);
   if (b.seg_cap[B_BLK] > 0)
-    launch_table<S, 1, 256, BLK_CAP, T_BLK / 256, B_BLK>(jobs, b, ctr, st, tl[0], launches);
+    launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK>(jobs, b, ctr, st, tl[0], launches);
   mark(B_BLK);
-  if (b.seg_cap[B_C1] > 0)
-    launch_table<S, 1, 1024, PART, 4, B_C1>(jobs, b, ctr, st, tl[1], launches);
-  mark(B_C1);
-  if (b.seg_cap[B_C2] > 0)
-    launch_table<S, 2, 1024, PART, 4, B_C2>(jobs, b, ctr, st, tl[2], launches);
-  mark(B_C2);
-  if (b.seg_cap[B_C4] > 0)
-    launch_table<S, 4, 1024, PART, 4, B_C4>(jobs, b, ctr, st, tl[3], launches);
-  mark(B_C4);
-  if (b.seg_cap[B_C8] > 0)
-    launch_table<S, 8, 1024, PART, 4, B_C8>(jobs, b, ctr, st, tl[4], launches);
-  mark(B_C8);
-  if (b.seg_cap[B_C16] > 0)
-    launch_table<S, 16, 1024, PART, 4, B_C16>(jobs, b, ctr, st, tl[5], launches);
-  mark(B_C16);
+  if (b.seg_cap[B_T4K] > 0)
+    launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K>(jobs, b, ctr, st, tl[1], launches);
+  mark(B_T4K);
+  if (b.seg_cap[B_T8K] > 0)
+    launch_table<S, 1, 1024, TP_8K, 4, 2, false, B_T8K>(jobs, b, ctr, st, tl[2], launches);
+  mark(B_T8K);
+  if (b.seg_cap[B_T16K] > 0)
+    launch_table<S, 2, 1024, TP_8K, 4, 2, false, B_T16K>(jobs, b, ctr, st, tl[3], launches);
+  mark(B_T16K);
+  if (b.seg_cap[B_T32K] > 0)
+    launch_table<S, 4, 1024, TP_8K, 4, 2, false, B_T32K>(jobs, b, ctr, st, tl[4], launches);
+  mark(B_T32K);
+  if (b.seg_cap[B_T64K] > 0)
+    launch_table<S, 8, 1024, TP_8K, 4, 2, false, B_T64K>(jobs, b, ctr, st, tl[5], launches);
+  mark(B_T64K);
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
     for (int64_t p = 0; p < hub_passes; ++p) {

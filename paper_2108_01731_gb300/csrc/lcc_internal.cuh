@@ -38,31 +38,32 @@ enum : int32_t {
 // in the previous round.  Set only for JF_PULL jobs.
 constexpr uint32_t LK_MOVED = 0x80000000u;
 
-// Degree buckets of the best-move kernels.  Every hash table holds at least
-// two slots per entry of the row, so a row of d entries needs 2d slots.
+// Degree buckets of the best-move kernels.  The tables hold at least two
+// slots per entry of the row (power-of-two sizes) up to B_T4K, and 1.6 in
+// the larger-row kernels (any size).
 enum Bucket : int {
-  B_G4 = 0,    // deg <= 4: 4 lanes per vertex, register aggregation
-  B_G8 = 1,    // deg <= 8
-  B_G16 = 2,   // deg <= 16
-  B_G32 = 3,   // deg <= 32: one warp
-  B_W64 = 4,   // deg <= 64: one warp, shared-memory table, 2 entries per lane
-  B_W128 = 5,  // deg <= 128: 4 entries per lane
-  B_WARP = 6,  // deg <= 256: 8 entries per lane
-  B_BLK = 7,   // deg <= 1024: one 256-thread block, shared-memory table
-  B_C1 = 8,    // deg <= 4096: one 1024-thread block, 8192-slot table
-  B_C2 = 9,    // deg <= 8192: cluster of 2 blocks, table in distributed shared memory
-  B_C4 = 10,   // deg <= 16384: cluster of 4
-  B_C8 = 11,   // deg <= 32768: cluster of 8
-  B_C16 = 12,  // deg <= 65536: cluster of 16
-  B_HUB = 13,  // larger: global-memory table, many blocks per vertex
+  B_G4 = 0,     // deg <= 4: 4 lanes per vertex, register aggregation
+  B_G8 = 1,     // deg <= 8
+  B_G16 = 2,    // deg <= 16
+  B_G32 = 3,    // deg <= 32: one warp
+  B_W64 = 4,    // deg <= 64: one warp, shared-memory table, 2 entries per lane
+  B_W128 = 5,   // deg <= 128: 4 entries per lane
+  B_WARP = 6,   // deg <= 256: 8 entries per lane
+  B_BLK = 7,    // deg <= 1024: one 256-thread block, shared-memory table
+  B_T4K = 8,    // deg <= 4096: one 1024-thread block
+  B_T8K = 9,    // deg <= 8192: one 1024-thread block, two chunks per thread
+  B_T16K = 10,  // deg <= 16384: cluster of 2 blocks, table in distributed shared memory
+  B_T32K = 11,  // deg <= 32768: cluster of 4
+  B_T64K = 12,  // deg <= 65536: cluster of 8
+  B_HUB = 13,   // larger: global-memory table, many blocks per vertex
   NB = 14
 };
 constexpr int T_WARP = 256;
 constexpr int T_BLK = 1024;
-constexpr int PART = 8192;       // table slots per block of the cluster kernels
-constexpr int T_C1 = PART / 2;   // rows up to PART/2 * cluster size
+constexpr int TP_BLK = 2048;     // table slots of the B_BLK kernel (power of two, 2 per entry)
+constexpr int TP_4K = 8192;      // of the B_T4K kernel (power of two, 2 per entry)
+constexpr int TP_8K = 13312;     // per block of the larger-row kernels (>= 1.6 * 8192)
 constexpr int WARP_CAP = 512;    // >= 2 * T_WARP
-constexpr int BLK_CAP = 2048;    // >= 2 * T_BLK
 constexpr int HUB_CHUNK = 2048;  // edges per insertion unit
 constexpr int HUB_SCHUNK = 4096; // table slots per scoring unit
 
@@ -75,11 +76,11 @@ __host__ __device__ inline int bucket_of(int64_t deg) {
   if (deg <= 128) return B_W128;
   if (deg <= T_WARP) return B_WARP;
   if (deg <= T_BLK) return B_BLK;
-  if (deg <= T_C1) return B_C1;
-  if (deg <= 2 * T_C1) return B_C2;
-  if (deg <= 4 * T_C1) return B_C4;
-  if (deg <= 8 * T_C1) return B_C8;
-  if (deg <= 16 * T_C1) return B_C16;
+  if (deg <= 4096) return B_T4K;
+  if (deg <= 8192) return B_T8K;
+  if (deg <= 16384) return B_T16K;
+  if (deg <= 32768) return B_T32K;
+  if (deg <= 65536) return B_T64K;
   return B_HUB;
 }
 

@@ -278,6 +278,37 @@ LCC_API lcc_status lcc_cluster_batch(const lcc_graph *const *graphs, int32_t cou
                              int32_t *const *labels_out,
                              double *objectives_out);
 
+/*
+ * Kernel tuning of one device.  The paper routes rows by one fixed degree
+ * threshold between a sequential scan and a parallel hash table (Appendix B);
+ * here rows of 33..warp_max entries run one warp per row and longer rows up
+ * to 1024 entries one 256-thread block per row.  A tuning changes which
+ * kernel evaluates a vertex, never a result.  A level keeps the routing it
+ * was bucketed with when it was built.
+ */
+typedef struct lcc_tuning {
+  int32_t warp_max;    /* 32, 64, 128 or 256 (the default) */
+  int32_t reserved[7]; /* zero */
+} lcc_tuning;
+
+/* lcc_get_tuning / lcc_set_tuning -- the tuning used by later calls on CUDA
+ * device `device`.  LCC_ERR_INVALID for a bad device or tuning. */
+LCC_API lcc_status lcc_get_tuning(int32_t device, lcc_tuning *out);
+LCC_API lcc_status lcc_set_tuning(int32_t device, const lcc_tuning *t);
+
+/*
+ * lcc_autotune -- choose the tuning of g's device.  With cache_path naming a
+ * text file that has a line for this device (its name and SM count), that
+ * line is applied.  Otherwise every warp_max is timed on three best-move
+ * rounds of g from singletons (lambda and mode as in lcc_best_moves, V' of
+ * moved vertices' neighbours), the fastest is applied and, with cache_path,
+ * appended to the file as "<device name>|<SMs> <warp_max>".  The chosen
+ * tuning goes to `out` (nullable).  LCC_ERR_INVALID for bad arguments or a
+ * malformed line for this device; file errors are LCC_ERR_INVALID too.
+ */
+LCC_API lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q,
+                                int32_t mode, const char *cache_path, lcc_tuning *out);
+
 typedef struct lcc_server lcc_server;
 
 typedef struct lcc_server_cfg {

@@ -360,6 +360,138 @@ lcc_status lcc_best_moves(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q
   API_END
 }
 
+// ------------------------------------------------------------ tuning ----
+
+static void check_tuning(const lcc_tuning *t) {
+  if (!t) fail(LCC_ERR_INVALID, "tuning is NULL");
+  const int w = t->warp_max;
+  if (w != 32 && w != 64 && w != 128 && w != 256)
+    fail(LCC_ERR_INVALID, "warp_max must be 32, 64, 128 or 256");
+  for (int i = 0; i < 7; ++i)
+    if (t->reserved[i]) fail(LCC_ERR_INVALID, "reserved tuning fields must be zero");
+}
+
+static void check_device(int32_t device) {
+  int nd = 0;
+  CK(cudaGetDeviceCount(&nd));
+  if (device < 0 || device >= nd) fail(LCC_ERR_INVALID, "no such CUDA device");
+}
+
+lcc_status lcc_get_tuning(int32_t device, lcc_tuning *out) {
+  API_BEGIN
+  check_device(device);
+  if (!out) fail(LCC_ERR_INVALID, "out is NULL");
+  *out = tuning_for(device);
+  API_END
+}
+
+lcc_status lcc_set_tuning(int32_t device, const lcc_tuning *t) {
+  API_BEGIN
+  check_device(device);
+  check_tuning(t);
+  set_tuning(device, *t);
+  API_END
+}
+
+// Key of a device in the tuning file: its name and SM count.
+static std::string tuning_key(int dev) {
+  cudaDeviceProp pr;
+  CK(cudaGetDeviceProperties(&pr, dev));
+  std::string name(pr.name);
+  for (char &c : name)
+    if (c == '|' || c == '\n') c = ' ';
+  return name + "|" + std::to_string(pr.multiProcessorCount);
+}
+
+// Best-move device time of `rounds` rounds of g from singletons.
+static double time_rounds(const lcc_graph *g, int64_t p, int64_t q, int32_t mode, int rounds) {
+  std::unique_lock<std::mutex> lk;
+  Engine *E = engine_for(g->dev, g->st, lk);
+  E->stats = EngineStats();
+  E->timing = true;
+  Job J;
+  J.g = g;
+  J.p = p;
+  J.q = q;
+  J.mode = mode;
+  J.sc = default_schedule();
+  J.sc.num_iter = rounds;
+  J.kind = BM_ONLY;
+  try {
+    E->add_job(&J, nullptr, nullptr);
+    while (!E->idle()) E->tick();
+    sync_checked(g->st);
+  } catch (...) {
+    E->drop_job(&J);
+    E->timing = false;
+    throw;
+  }
+  E->timing = false;
+  const double ms = E->stats.ms_bm;
+  J.lv.clear();
+  J.base.reset();
+  return ms;
+}
+
+lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, int32_t mode,
+                        const char *cache_path, lcc_tuning *out) {
+  API_BEGIN
+  check_graph(g);
+  check_lambda(lambda_p, lambda_q, mode);
+  const std::string key = tuning_key(g->dev);
+  lcc_tuning t;
+  memset(&t, 0, sizeof(t));
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "r")) {
+      char line[512];
+      bool found = false;
+      while (!found && fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        const size_t sp = l.rfind(' ');
+        if (sp == std::string::npos || l.compare(0, sp, key) != 0 || sp != key.size()) continue;
+        t.warp_max = atoi(l.c_str() + sp + 1);
+        found = true;
+      }
+      fclose(f);
+      if (found) {
+        check_tuning(&t);
+        set_tuning(g->dev, t);
+        if (out) *out = t;
+        return LCC_OK;
+      }
+    }
+  }
+  const lcc_tuning before = tuning_for(g->dev);
+  const int cand[4] = {32, 64, 128, 256};
+  double best_ms = 0;
+  int best = T_WARP;
+  try {
+    time_rounds(g, lambda_p, lambda_q, mode, 1);  // first-use costs outside the comparison
+    for (int c : cand) {
+      t.warp_max = c;
+      set_tuning(g->dev, t);
+      const double ms = time_rounds(g, lambda_p, lambda_q, mode, 3);
+      if (c == cand[0] || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  } catch (...) {
+    set_tuning(g->dev, before);
+    throw;
+  }
+  t.warp_max = best;
+  set_tuning(g->dev, t);
+  if (cache_path) {
+    FILE *f = fopen(cache_path, "a");
+    if (!f) fail(LCC_ERR_INVALID, std::string("cannot write the tuning file ") + cache_path);
+    fprintf(f, "%s %d\n", key.c_str(), best);
+    fclose(f);
+  }
+  if (out) *out = t;
+  API_END
+}
+
 lcc_status lcc_compress(const lcc_graph *g, int32_t mode, const int32_t *labels,
                         int32_t *map_out, lcc_graph **coarse_out) {
   API_BEGIN

@@ -50,6 +50,24 @@ int64_t layout_min_bytes() {
   return LAYOUT_MIN_BYTES;
 }
 
+static std::mutex g_tune_mu;
+static std::unordered_map<int, lcc_tuning> g_tune;
+
+lcc_tuning tuning_for(int dev) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(dev);
+  if (it != g_tune.end()) return it->second;
+  lcc_tuning t;
+  memset(&t, 0, sizeof(t));
+  t.warp_max = T_WARP;
+  return t;
+}
+
+void set_tuning(int dev, const lcc_tuning &t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[dev] = t;
+}
+
 void check_cuda(cudaError_t e, const char *what, int line) {
   if (e == cudaSuccess) return;
   if (e == cudaErrorMemoryAllocation) {
@@ -184,6 +202,7 @@ static LJob ljob_of(const Level &L) {
   x.gnbr = L.gnbr;
   x.n = L.n;
   x.wtype = L.wtype;
+  x.warp_max = L.warp_max;
   return x;
 }
 
@@ -289,6 +308,7 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
   j->base = std::make_shared<Store>(st_);
   Level L0;
   L0.n = g->n;
+  L0.warp_max = tuning_for(dev_).warp_max;
   L0.off = g->off;
   L0.nbr = g->nbr;
   L0.w = g->w;
@@ -429,6 +449,7 @@ void Engine::round(std::vector<Job *> &js) {
     x.q = J->q;
     x.wtype = L.wtype;
     x.pull_min = INT64_MAX;
+    x.warp_max = L.warp_max;
     int32_t f = 0;
     if (J->eval_only) {
       f |= JF_EVAL_ONLY;
@@ -658,20 +679,23 @@ void Engine::contract(std::vector<Job *> &js) {
   note_launches(lcount);
   uint64_t *sk = in_alt ? keys2 : keys;
   int64_t *sv = in_alt ? vals2 : vals;
-  int64_t *flags = (int64_t *)(in_alt ? keys : keys2);
   uint64_t *ukeys = (uint64_t *)(in_alt ? vals : vals2);
-  CK(cudaMemsetAsync(flags + P, 0, 8, st_));
-  launch_seg_heads(sk, P, flags, st_, d_);
-  scan_exclusive_i64(flags, P, stmp = tmp.alloc<int64_t>(scan_tmp_elems(P + 1)), st_, d_);
-  note_launches(4);
-  CK(cudaMemcpyAsync(hb, flags + P, 8, cudaMemcpyDeviceToHost, st_));
+  // reduce by key: heads per tile, their scan (first run of each tile; the
+  // total is the number of coarse entries), then keys and sums
+  const int64_t nt = rb_tiles(P);
+  int64_t *toff = tmp.alloc<int64_t>(nt + 1);
+  CK(cudaMemsetAsync(toff + nt, 0, 8, st_));
+  launch_rb_count(sk, P, toff, st_);
+  scan_exclusive_i64(toff, nt, stmp = tmp.alloc<int64_t>(scan_tmp_elems(nt + 1)), st_, d_);
+  note_launches(3);
+  CK(cudaMemcpyAsync(hb, toff + nt, 8, cudaMemcpyDeviceToHost, st_));
   sync_checked(st_);
   const int64_t U = hb[0];
   int64_t *uvals = store->alloc<int64_t>(U);
   int32_t *unbr = store->alloc<int32_t>(U);
   int64_t *offg = store->alloc<int64_t>(ntot + 1);
   CK(cudaMemsetAsync(uvals, 0, (U > 0 ? U : 1) * 8, st_));
-  launch_seg_reduce(sk, sv, flags, P, ukeys, uvals, st_, d_);
+  launch_rb_write(sk, sv, P, toff, ukeys, uvals, st_);
   launch_csr_rows(ukeys, U, ntot, offg, unbr, st_, d_);
   note_launches(2);
   int32_t *Lu = store->alloc<int32_t>(ntot);
@@ -696,6 +720,7 @@ void Engine::contract(std::vector<Job *> &js) {
     Lf.map_store = store;
     Level nl;
     nl.n = nprime[i];
+    nl.warp_max = tuning_for(dev_).warp_max;
     nl.off = offg + cbase[i];
     nl.nbr = unbr;
     nl.w = uvals;

@@ -32,6 +32,9 @@ inline void sync_checked(cudaStream_t st) {
 
 extern std::atomic<long long> g_launches;
 int64_t layout_min_bytes();
+// Kernel tuning per device (degree routing), shared by every engine there.
+lcc_tuning tuning_for(int dev);
+void set_tuning(int dev, const lcc_tuning &t);
 inline void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Stream-ordered device allocation from a per-device pool that keeps freed
@@ -107,6 +110,7 @@ struct Level {
   unsigned long long *lk = nullptr;  // packed (K[L[u]], L[u]); null if K can exceed 32 bits
   int32_t *pos = nullptr;            // gather layout (null: identity), see JobDev
   int32_t *gnbr = nullptr;
+  int32_t warp_max = T_WARP;         // degree routing the level was bucketed with
   int32_t *map = nullptr;  // vertex -> coarse vertex of the next level
   std::shared_ptr<Store> store;
   std::shared_ptr<Store> map_store;

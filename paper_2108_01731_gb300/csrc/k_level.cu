@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
         cur = j;
       }
       const int64_t deg = end - beg;
-      const int b = bucket_of(deg);
+      const int b = bucket_of(deg, J->warp_max);
       bc[b] += 1;
       ents += deg;
       if (b == B_HUB) {

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(FR_T) k_frontier(const JobDev *__restrict__ jo
         else
           f = (m & 1) != 0;
         if (f) {
-          bk[r] = bucket_of(deg);
+          bk[r] = bucket_of(deg, J->warp_max);
           item[r] = ((uint64_t)(uint32_t)j << 32) | (uint32_t)v;
           if (!pull) {
             my_deg += deg;

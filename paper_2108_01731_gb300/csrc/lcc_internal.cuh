@@ -67,14 +67,18 @@ constexpr int WARP_CAP = 512;    // >= 2 * T_WARP
 constexpr int HUB_CHUNK = 2048;  // edges per insertion unit
 constexpr int HUB_SCHUNK = 4096; // table slots per scoring unit
 
-__host__ __device__ inline int bucket_of(int64_t deg) {
+// Rows of more than warp_max entries (a tuning: 32, 64, 128 or 256) and up
+// to T_BLK go to the block kernel instead of the warp kernels.
+__host__ __device__ inline int bucket_of(int64_t deg, int warp_max = T_WARP) {
   if (deg <= 4) return B_G4;
   if (deg <= 8) return B_G8;
   if (deg <= 16) return B_G16;
   if (deg <= 32) return B_G32;
-  if (deg <= 64) return B_W64;
-  if (deg <= 128) return B_W128;
-  if (deg <= T_WARP) return B_WARP;
+  if (deg <= warp_max) {
+    if (deg <= 64) return B_W64;
+    if (deg <= 128) return B_W128;
+    return B_WARP;
+  }
   if (deg <= T_BLK) return B_BLK;
   if (deg <= 4096) return B_T4K;
   if (deg <= 8192) return B_T8K;
@@ -123,6 +127,8 @@ struct JobDev {
   int64_t pull_min;
   int32_t wtype;
   int32_t flags;
+  int32_t warp_max;  // degree routing of the level (see bucket_of)
+  int32_t pad;
 };
 
 // Device counters of a round (int64 each).
@@ -197,7 +203,7 @@ struct LJob {
   int32_t *gnbr;
   int64_t n;
   int32_t wtype;
-  int32_t pad;
+  int32_t warp_max;       // degree routing of the level (see bucket_of)
 };
 
 // Degree classes of the gather layout: 0 for an isolated vertex, else
@@ -364,6 +370,13 @@ int64_t radix_tmp_elems(int64_t n, int npasses);
 void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,
                       int64_t n, const int *shifts, int npasses, int64_t *tmp,
                       cudaStream_t st, const Dev &d, bool *result_in_alt, int *launches);
+// Reduce by key over sorted keys (k_contract.cu): rb_tiles(n) tiles;
+// tile_heads[t] = heads of tile t (scanned in place by the caller into each
+// tile's first run); ukeys/uvals receive one entry per run (uvals zeroed).
+int64_t rb_tiles(int64_t n);
+void launch_rb_count(const uint64_t *keys, int64_t n, int64_t *tile_heads, cudaStream_t st);
+void launch_rb_write(const uint64_t *keys, const int64_t *vals, int64_t n, const int64_t *tile_off,
+                     uint64_t *ukeys, int64_t *uvals, cudaStream_t st);
 void launch_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags, cudaStream_t st,
                       const Dev &d);
 void launch_seg_reduce(const uint64_t *keys, const int64_t *vals, const int64_t *idx, int64_t n,

@@ -37,6 +37,10 @@ class lcc_schedule(C.Structure):
                 ("flags", C.c_int32)]
 
 
+class lcc_tuning(C.Structure):
+    _fields_ = [("warp_max", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
 class lcc_stats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("rounds_total", C.c_int32),
                 ("edges_scanned", C.c_int64), ("vertices_scanned", C.c_int64),
@@ -90,6 +94,9 @@ _SIGS = {
     "lcc_server_wait_idle": [P, I64],
     "lcc_server_counters": [P, P],
     "lcc_server_destroy": [P],
+    "lcc_get_tuning": [I32, P],
+    "lcc_set_tuning": [I32, P],
+    "lcc_autotune": [P, I64, I64, I32, C.c_char_p, P],
     "lcc_status_str": [I32],
     "lcc_last_error": [],
 }
@@ -287,6 +294,29 @@ def lcc_objective(g, lambda_p, lambda_q, mode, labels):
     if num >= 1 << 127:
         num -= 1 << 128
     return num, den.value
+
+
+def lcc_get_tuning(device=0):
+    """The degree routing used on `device`: returns warp_max."""
+    t = lcc_tuning()
+    _check(load().lcc_get_tuning(int(device), C.byref(t)))
+    return t.warp_max
+
+
+def lcc_set_tuning(device, warp_max):
+    t = lcc_tuning()
+    t.warp_max = int(warp_max)
+    _check(load().lcc_set_tuning(int(device), C.byref(t)))
+
+
+def lcc_autotune(g, lambda_p, lambda_q, mode, cache_path=None):
+    """Times each routing on three best-move rounds of g (or reads the cache
+    file's line for this device) and applies the fastest; returns warp_max."""
+    t = lcc_tuning()
+    path = cache_path.encode() if cache_path else None
+    _check(load().lcc_autotune(g.handle, int(lambda_p), int(lambda_q), int(mode), path,
+                               C.byref(t)))
+    return t.warp_max
 
 
 def lcc_desired_noalloc(off, nbr, w, k, lambda_p, lambda_q, labels, K, out, stream=None):

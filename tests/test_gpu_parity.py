@@ -178,6 +178,41 @@ def test_gather_layout_matches_oracle(L, monkeypatch):
     G.free()
 
 
+def test_tuning_routes_without_changing_results(L, tmp_path):
+    """Every degree routing (rows of 33..warp_max entries in the warp kernels,
+    longer rows up to 1024 in the block kernel) gives the oracle's labels and
+    scanned entries; the autotuner picks one of the routings, and its cache
+    file is read back on the next call."""
+    before = L.lcc_get_tuning(0)
+    try:
+        for name, mode, p, q in [("hubs", O.NODEW_DEGREE, 1, 1), ("rmat", O.NODEW_DEGREE, 1, 1),
+                                 ("signed", O.NODEW_UNIT, 1, 10)]:
+            g = GRAPHS[name]
+            G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+            wl, num, _, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode)
+            for wm in (32, 64, 128, 256):
+                L.lcc_set_tuning(0, wm)
+                labels, _, st = L.lcc_cluster(G, p, q, mode, None)
+                assert np.array_equal(labels, wl), (name, wm)
+                assert st["obj_num"] == num and st["edges_scanned"] == wst[2]
+            G.free()
+        g = GRAPHS["rmat"]
+        G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+        path = tmp_path / "tuning.txt"
+        wm = L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path))
+        assert wm in (32, 64, 128, 256) and L.lcc_get_tuning(0) == wm
+        assert path.read_text().strip().endswith(" %d" % wm)
+        L.lcc_set_tuning(0, 32 if wm != 32 else 256)
+        assert L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path)) == wm
+        assert L.lcc_get_tuning(0) == wm
+        G.free()
+        for bad in (0, 48, 512):
+            with pytest.raises(L.LccError):
+                L.lcc_set_tuning(0, bad)
+    finally:
+        L.lcc_set_tuning(0, before)
+
+
 def check_cluster_case(L, case):
     name, mode, p, q, kw = case
     g = GRAPHS[name]

@@ -122,24 +122,21 @@ static lcc_graph *load_graph(const int64_t *offsets, const int32_t *nbrs, const 
     if (n > 0) CK(cudaMemcpyAsync(g->kc, node_w, n * 8, kind, st));
   }
   Store tmp(st);
-  unsigned long long *v = tmp.alloc<unsigned long long>(8);
-  unsigned long long *h = nullptr;
-  CK(cudaMallocHost(&h, 10 * 8));
-  struct HostFree {
-    void *p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{h};
+  unsigned long long *v = tmp.alloc<unsigned long long>(10);
+  // results come back to pageable memory: each such copy returns once done
+  // (a pinned buffer per call would cost more than the copies)
+  unsigned long long h[10];
   CK(cudaMemsetAsync(v, 0, 64, st));
-  CK(cudaMemcpyAsync(h + 8, g->off, 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 9, g->off + n, 8, cudaMemcpyDeviceToHost, st));
   launch_validate(g->off, g->nbr, (const int32_t *)g->w, n, nnz, v, st, d);
-  CK(cudaMemcpyAsync(h, v, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(v + 8, g->off, 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(v + 9, g->off + n, 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h, v, 10 * 8, cudaMemcpyDeviceToHost, st));
   sync_checked(st);
   if ((int64_t)h[8] != 0 || (int64_t)h[9] != nnz)
     fail(LCC_ERR_INVALID, "offsets[0] must be 0 and offsets[n] must equal nnz");
   if (h[0] & 1) fail(LCC_ERR_INVALID, "offsets are not monotone");
   launch_validate_rows(g->off, g->nbr, (const int32_t *)g->w, n, v, st, d);
-  CK(cudaMemcpyAsync(h, v, 64, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h, v, 8 * 8, cudaMemcpyDeviceToHost, st));
   sync_checked(st);
   note_launches(2);
   if (h[0] & 2) fail(LCC_ERR_INVALID, "neighbour id out of range [0, n)");

@@ -467,12 +467,48 @@ __global__ void __launch_bounds__(256) k_validate_rows(const int64_t *off, const
       h4 += mix64(mix64(b + 0x9e3779b97f4a7c15ull) + uw);
     }
   }
-  if (bits) atomicOr(out, bits);
-  atomicAdd(out + 1, h1);
-  atomicAdd(out + 2, h2);
-  atomicAdd(out + 3, h3);
-  atomicAdd(out + 4, h4);
-  atomic_add_u128(out + 5, out + 6, wabs);
+  // warp, then block sums: one set of atomics per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    h1 += __shfl_xor_sync(FULL, h1, o);
+    h2 += __shfl_xor_sync(FULL, h2, o);
+    h3 += __shfl_xor_sync(FULL, h3, o);
+    h4 += __shfl_xor_sync(FULL, h4, o);
+    bits |= __shfl_xor_sync(FULL, bits, o);
+    const unsigned long long lo = __shfl_xor_sync(FULL, (unsigned long long)wabs, o);
+    const unsigned long long hi = __shfl_xor_sync(FULL, (unsigned long long)(wabs >> 64), o);
+    wabs += ((u128)hi << 64) | lo;
+  }
+  __shared__ unsigned long long part[8][7];
+  const int wib = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[wib][0] = bits;
+    part[wib][1] = h1;
+    part[wib][2] = h2;
+    part[wib][3] = h3;
+    part[wib][4] = h4;
+    part[wib][5] = (unsigned long long)wabs;
+    part[wib][6] = (unsigned long long)(wabs >> 64);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tb = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+    u128 tw = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      tb |= part[k][0];
+      t1 += part[k][1];
+      t2 += part[k][2];
+      t3 += part[k][3];
+      t4 += part[k][4];
+      tw += ((u128)part[k][6] << 64) | part[k][5];
+    }
+    if (tb) atomicOr(out, tb);
+    atomicAdd(out + 1, t1);
+    atomicAdd(out + 2, t2);
+    atomicAdd(out + 3, t3);
+    atomicAdd(out + 4, t4);
+    atomic_add_u128(out + 5, out + 6, tw);
+  }
 }
 
 void launch_validate(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,

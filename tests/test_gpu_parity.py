@@ -123,6 +123,46 @@ def test_compress_matches_oracle(L, name):
     G.free()
 
 
+def test_compress_long_runs_of_equal_keys(L):
+    """Compress sums parallel edges (Sec. 3.1): two 200-vertex cliques joined
+    by a complete bipartite graph, labelled as the two cliques, give one run
+    of 40,000 equal keys per direction, which crosses many warp chunks and
+    sort tiles of the reduction; a chain of cliques gives uneven runs."""
+    import torch
+    a = torch.arange(200)
+    pairs = [torch.combinations(a).T, torch.combinations(a + 200).T,
+             torch.stack([a.repeat_interleave(200), (a + 200).repeat(200)])]
+    # a chain of 12 cliques of 5..60 vertices, consecutive ones joined by one edge
+    base = 400
+    sizes = [5 + 5 * i for i in range(12)]
+    starts = []
+    for s_ in sizes:
+        starts.append(base)
+        pairs.append(torch.combinations(torch.arange(base, base + s_)).T)
+        base += s_
+    pairs.append(torch.tensor([[starts[i], starts[i + 1]] for i in range(11)]).T)
+    e = torch.cat(pairs, 1)
+    n = base
+    g = I.to_numpy(I.pairs_to_csr(e[0], e[1], n,
+                                  w=((e[0] * 2654435761 + e[1]) % 7 + 1).to(torch.int32)))
+    w = g["w"]
+    src = np.repeat(np.arange(n), np.diff(g["off"]))
+    labels = np.zeros(n, np.int32)
+    labels[200:400] = 200
+    for st_, s_ in zip(starts, sizes):
+        labels[st_:st_ + s_] = st_
+    k = np.ones(n, np.int64)
+    G = L.lcc_load_csr(g["off"], g["nbr"], w, node_w=k)
+    mp, C = L.lcc_compress(G, O.NODEW_CUSTOM, labels)
+    off2, nbr2, w2, k2 = L.lcc_graph_export(C)
+    wmp, woff, wnbr, ww, wk = O.compress(g["off"], g["nbr"], w, k, labels)
+    assert np.array_equal(mp, wmp) and np.array_equal(off2, woff)
+    assert np.array_equal(nbr2, wnbr) and np.array_equal(w2, ww) and np.array_equal(k2, wk)
+    assert off2[1] - off2[0] == 1 and w2[0] == int(w[(src < 200) & (g["nbr"] >= 200)].sum())
+    C.free()
+    G.free()
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_objective_matches_oracle(L, name):
     g = GRAPHS[name]

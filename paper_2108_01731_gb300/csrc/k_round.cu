@@ -1171,7 +1171,7 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   };
   static int occ[10] = {0};
   static bool init = false;
-  static TableLaunch tl[6];
+  static TableLaunch tl[7];
   if (!init) {
     occ[0] = occ_blocks(k_bm_group<4, S>, 256, 0);
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
@@ -1243,6 +1243,9 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   if (b.seg_cap[B_T64K] > 0)
     launch_table<S, 8, 1024, TP_8K, 4, 2, false, B_T64K>(jobs, b, ctr, st, tl[5], launches);
   mark(B_T64K);
+  if (b.seg_cap[B_T128K] > 0)
+    launch_table<S, 16, 1024, TP_8K, 4, 2, false, B_T128K>(jobs, b, ctr, st, tl[6], launches);
+  mark(B_T128K);
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
     for (int64_t p = 0; p < hub_passes; ++p) {

@@ -55,8 +55,9 @@ enum Bucket : int {
   B_T16K = 10,  // deg <= 16384: cluster of 2 blocks, table in distributed shared memory
   B_T32K = 11,  // deg <= 32768: cluster of 4
   B_T64K = 12,  // deg <= 65536: cluster of 8
-  B_HUB = 13,   // larger: global-memory table, many blocks per vertex
-  NB = 14
+  B_T128K = 13, // deg <= 131072: cluster of 16 (a non-portable cluster size)
+  B_HUB = 14,   // larger: global-memory table, many blocks per vertex
+  NB = 15
 };
 constexpr int T_WARP = 256;
 constexpr int T_BLK = 1024;
@@ -85,6 +86,7 @@ __host__ __device__ inline int bucket_of(int64_t deg, int warp_max = T_WARP) {
   if (deg <= 16384) return B_T16K;
   if (deg <= 32768) return B_T32K;
   if (deg <= 65536) return B_T64K;
+  if (deg <= 131072) return B_T128K;
   return B_HUB;
 }
 

@@ -31,7 +31,8 @@ def graphs():
         "cl": I.to_numpy(I.chung_lu(30000, 2.1, 12, seed=4)),
         "rmat": I.to_numpy(I.rmat(14, 120000, seed=5)),
         "signed": I.to_numpy(I.random_signed_graph(300, 0.1, -4, 6, seed=6)),
-        "giant": I.to_numpy(I.hub_graph(150000, 5, 0, [5000, 12000, 25000, 50000, 100000],
+        "giant": I.to_numpy(I.hub_graph(150000, 5, 0,
+                                        [5000, 12000, 25000, 50000, 100000, 140000],
                                         seed=7, w_lo=1, w_hi=3)),
     }
 

@@ -1171,13 +1171,12 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   };
   static int occ[10] = {0};
   static bool init = false;
-  static TableLaunch tl[7];
+  static TableLaunch tl[8];
   if (!init) {
     occ[0] = occ_blocks(k_bm_group<4, S>, 256, 0);
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
     occ[2] = occ_blocks(k_bm_group<16, S>, 256, 0);
     occ[3] = occ_blocks(k_bm_group<32, S>, 256, 0);
-    occ[4] = occ_blocks(k_bm_warp<S, 8, B_WARP>, 128, 0);
     occ[7] = occ_blocks(k_bm_warp<S, 2, B_W64>, 128, 0);
     occ[8] = occ_blocks(k_bm_warp<S, 4, B_W128>, 128, 0);
     occ[5] = occ_blocks(k_hub_insert, 256, 0);
@@ -1220,10 +1219,8 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     ++*launches;
   }
   mark(B_W128);
-  if (b.seg_cap[B_WARP] > 0) {
-    k_bm_warp<S, 8, B_WARP><<<grid(B_WARP, occ[4], 4), 128, 0, st>>>(jobs, b, ctr);
-    ++*launches;
-  }
+  if (b.seg_cap[B_WARP] > 0)
+    launch_table<S, 1, 128, WARP_CAP, 2, 1, true, B_WARP>(jobs, b, ctr, st, tl[7], launches);
   mark(B_WARP);
   if (b.seg_cap[B_BLK] > 0)
     launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK>(jobs, b, ctr, st, tl[0], launches);

@@ -48,7 +48,7 @@ enum Bucket : int {
   B_G32 = 3,    // deg <= 32: one warp
   B_W64 = 4,    // deg <= 64: one warp, shared-memory table, 2 entries per lane
   B_W128 = 5,   // deg <= 128: 4 entries per lane
-  B_WARP = 6,   // deg <= 256: 8 entries per lane
+  B_WARP = 6,   // deg <= 256: one 128-thread block, 2 entries per thread
   B_BLK = 7,    // deg <= 1024: one 256-thread block, shared-memory table
   B_T4K = 8,    // deg <= 4096: one 1024-thread block
   B_T8K = 9,    // deg <= 8192: one 1024-thread block, two chunks per thread

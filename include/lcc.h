@@ -281,10 +281,11 @@ LCC_API lcc_status lcc_cluster_batch(const lcc_graph *const *graphs, int32_t cou
 /*
  * Kernel tuning of one device.  The paper routes rows by one fixed degree
  * threshold between a sequential scan and a parallel hash table (Appendix B);
- * here rows of 33..warp_max entries run one warp per row and longer rows up
- * to 1024 entries one 256-thread block per row.  A tuning changes which
- * kernel evaluates a vertex, never a result.  A level keeps the routing it
- * was bucketed with when it was built.
+ * here rows of 33..warp_max entries run in the kernels for rows up to 256
+ * entries (one warp per row up to 128 entries, one 128-thread block per row
+ * up to 256), and longer rows up to 1024 entries one 256-thread block per
+ * row.  A tuning changes which kernel evaluates a vertex, never a result.  A
+ * level keeps the routing it was bucketed with when it was built.
  */
 typedef struct lcc_tuning {
   int32_t warp_max;    /* 32, 64, 128 or 256 (the default) */

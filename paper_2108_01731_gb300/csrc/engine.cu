@@ -603,6 +603,8 @@ void Engine::contract(std::vector<Job *> &js) {
     c.w = L.w;
     c.L = L.L;
     c.K = L.K;
+    c.pos = L.pos;
+    c.gnbr = L.gnbr ? L.gnbr : L.nbr;
     c.n = L.n;
     c.wtype = L.wtype;
     vs[i] = vt;
@@ -625,6 +627,7 @@ void Engine::contract(std::vector<Job *> &js) {
   }
   int64_t *rank = tmp.alloc<int64_t>(vt + 1);
   int32_t *gmap = tmp.alloc<int32_t>(vt);
+  int32_t *gmapp = tmp.alloc<int32_t>(vt);
   int64_t *pcnt = tmp.alloc<int64_t>(vt + 1);
   int64_t *stmp = tmp.alloc<int64_t>(scan_tmp_elems(vt + 1));
   int64_t *jc = tmp.alloc<int64_t>(2 * nj);
@@ -635,8 +638,8 @@ void Engine::contract(std::vector<Job *> &js) {
   launch_occ(dt, dv, nj, vt, rank, err, st_, d_);
   scan_exclusive_i64(rank, vt, stmp, st_, d_);
   launch_job_counts(dv, nj, rank, jc, st_);
-  launch_relabel(dt, dv, nj, vt, rank, gmap, st_, d_);
-  launch_emit_count(dt, dv, nj, vt, gmap, pcnt, st_, d_);
+  launch_relabel(dt, dv, nj, vt, rank, gmap, gmapp, st_, d_);
+  launch_emit_count(dt, dv, nj, vt, gmap, gmapp, pcnt, st_, d_);
   scan_exclusive_i64(pcnt, vt, stmp, st_, d_);
   note_launches(12);
   int64_t *hb = (int64_t *)stage2((3 + 2 * nj) * 8);
@@ -664,7 +667,7 @@ void Engine::contract(std::vector<Job *> &js) {
   int64_t *vals = tmp.alloc<int64_t>(P);
   uint64_t *keys2 = tmp.alloc<uint64_t>(P + 1);
   int64_t *vals2 = tmp.alloc<int64_t>(P);
-  launch_emit_write(dt, dv, nj, vt, gmap, rank, pcnt, keys, vals, st_, d_);
+  launch_emit_write(dt, dv, nj, vt, gmap, gmapp, rank, pcnt, keys, vals, st_, d_);
   int64_t *knew = store->alloc<int64_t>(ntot);
   launch_knew(dt, dv, nj, vt, rank, knew, st_, d_);
   note_launches(2);

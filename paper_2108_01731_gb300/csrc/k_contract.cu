@@ -55,9 +55,12 @@ void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot
   k_occ<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, occ, err);
 }
 
+// gmap: global coarse id per flat vertex; gmapp: the same ids in the flat
+// positions of the gather layout, so that the emission kernels look
+// neighbours up through gnbr with the hot ids sharing an L2-sized region.
 __global__ void k_relabel(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
                           int njobs, int64_t vtot, const int64_t *__restrict__ rank,
-                          int32_t *gmap) {
+                          int32_t *gmap, int32_t *gmapp) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vtot;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int j = find_job(vstart, njobs, i);
@@ -65,14 +68,17 @@ __global__ void k_relabel(const CJob *__restrict__ jobs, const int64_t *__restri
     const int64_t v = i - vstart[j];
     const int64_t g = rank[vstart[j] + J->L[v]];
     gmap[i] = (int32_t)g;
+    gmapp[vstart[j] + (J->pos ? J->pos[v] : v)] = (int32_t)g;
     J->map[v] = (int32_t)(g - rank[vstart[j]]);
   }
 }
 
 void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                    const int64_t *rank, int32_t *gmap, cudaStream_t st, const Dev &d) {
+                    const int64_t *rank, int32_t *gmap, int32_t *gmapp, cudaStream_t st,
+                    const Dev &d) {
   if (vtot <= 0) return;
-  k_relabel<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, rank, gmap);
+  k_relabel<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, rank, gmap,
+                                                    gmapp);
 }
 
 // k' = K: the coarse vertex of occupied cluster c gets node weight K_c.
@@ -110,6 +116,7 @@ void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, in
 __global__ void __launch_bounds__(256) k_emit_count(const CJob *__restrict__ jobs,
                                                     const int64_t *__restrict__ vstart, int njobs,
                                                     int64_t vtot, const int32_t *__restrict__ gmap,
+                                                    const int32_t *__restrict__ gmapp,
                                                     int64_t *pcnt) {
   const int lane = threadIdx.x & 31;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(256) k_emit_count(const CJob *__restrict__ job
     const int32_t cu = gmap[i];
     int cnt = 0;
     for (int64_t e = J->off[v] + lane; e < J->off[v + 1]; e += 32)
-      cnt += gmap[vs + __ldg(J->nbr + e)] != cu;
+      cnt += gmapp[vs + __ldg(J->gnbr + e)] != cu;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
     if (lane == 0) pcnt[i] = cnt;
@@ -130,14 +137,17 @@ __global__ void __launch_bounds__(256) k_emit_count(const CJob *__restrict__ job
 }
 
 void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, int64_t *pcnt, cudaStream_t st, const Dev &d) {
+                       const int32_t *gmap, const int32_t *gmapp, int64_t *pcnt, cudaStream_t st,
+                       const Dev &d) {
   if (vtot <= 0) return;
-  k_emit_count<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap, pcnt);
+  k_emit_count<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap,
+                                                            gmapp, pcnt);
 }
 
 __global__ void __launch_bounds__(256) k_emit_write(const CJob *__restrict__ jobs,
                                                     const int64_t *__restrict__ vstart, int njobs,
                                                     int64_t vtot, const int32_t *__restrict__ gmap,
+                                                    const int32_t *__restrict__ gmapp,
                                                     const int64_t *__restrict__ rank,
                                                     const int64_t *__restrict__ ppos,
                                                     uint64_t *keys, int64_t *vals) {
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(256) k_emit_write(const CJob *__restrict__ job
       bool out = false;
       int32_t cv = 0;
       if (e < end) {
-        cv = gmap[vs + __ldg(J->nbr + e)];
+        cv = gmapp[vs + __ldg(J->gnbr + e)];
         out = (uint32_t)cv != (uint32_t)cu;
       }
       const unsigned m = __ballot_sync(FULL, out);
@@ -173,11 +183,12 @@ __global__ void __launch_bounds__(256) k_emit_write(const CJob *__restrict__ job
 }
 
 void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int64_t *rank, const int64_t *ppos,
-                       uint64_t *keys, int64_t *vals, cudaStream_t st, const Dev &d) {
+                       const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
+                       const int64_t *ppos, uint64_t *keys, int64_t *vals, cudaStream_t st,
+                       const Dev &d) {
   if (vtot <= 0) return;
-  k_emit_write<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap, rank,
-                                                            ppos, keys, vals);
+  k_emit_write<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap,
+                                                            gmapp, rank, ppos, keys, vals);
 }
 
 // ----------------------------------------------------------------- scan --

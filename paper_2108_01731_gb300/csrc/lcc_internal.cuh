@@ -185,6 +185,8 @@ struct CJob {
   const int32_t *L;
   const int64_t *K;
   int32_t *map;  // out: coarse vertex of each vertex (local id)
+  const int32_t *pos;   // gather layout of the level (null: identity)
+  const int32_t *gnbr;  // neighbour positions (= nbr without a layout)
   int64_t n;
   int32_t wtype;
   int32_t pad;
@@ -351,13 +353,18 @@ void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t 
 // Contraction kernels (k_contract.cu).
 void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot, int64_t *occ,
                 int32_t *err, cudaStream_t st, const Dev &d);
+// gmap[i] = global coarse id of flat vertex i; gmapp holds the same ids at
+// the flat positions of the gather layout (gmapp[vstart_j + pos[v]]).
 void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                    const int64_t *rank, int32_t *gmap, cudaStream_t st, const Dev &d);
+                    const int64_t *rank, int32_t *gmap, int32_t *gmapp, cudaStream_t st,
+                    const Dev &d);
 void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, int64_t *pcnt, cudaStream_t st, const Dev &d);
+                       const int32_t *gmap, const int32_t *gmapp, int64_t *pcnt, cudaStream_t st,
+                       const Dev &d);
 void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int64_t *rank, const int64_t *ppos,
-                       uint64_t *keys, int64_t *vals, cudaStream_t st, const Dev &d);
+                       const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
+                       const int64_t *ppos, uint64_t *keys, int64_t *vals, cudaStream_t st,
+                       const Dev &d);
 void launch_knew(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                  const int64_t *rank, int64_t *knew, cudaStream_t st, const Dev &d);
 void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out,

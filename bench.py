@@ -218,7 +218,7 @@ class Clocks:
 def oracle_sample(host, wl, seconds):
     """Times the CPU oracle on the first best-move round of the same graph for
     a window of vertices [0, X) sized to take about `seconds`.  Returns
-    (GEdges/s, description)."""
+    (GEdges/s, description, oracle seconds)."""
     import numpy as np
     import oracle as O
     off = host["off"]
@@ -250,7 +250,7 @@ def oracle_sample(host, wl, seconds):
             x *= 2
     return (done_edges / done_t / 1e9, "first best-move round of the same graph, vertices "
             "[0, %d) (%d of %d vertices, %d entries scanned), single-threaded oracle"
-            % (v0, v0, n, done_edges))
+            % (v0, v0, n, done_edges), done_t)
 
 
 def degree_shares(off):
@@ -359,20 +359,23 @@ def run_reference(args, rank, world, local):
     host = host_copy(g)
     del g
     n_entries = len(host["nbr"])
-    vals = []
+    vals, secs = [], []
     desc = ""
     per = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        v, desc = oracle_sample(host, wl, per)
+        v, desc, t = oracle_sample(host, wl, per)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(t)
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": "best-move GEdges/s", "value": round(value, 6),
             "unit": "GEdges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int128", "data": "synthetic",
+            "ms_per_step": round(1e3 * statistics.mean(secs), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int128", "data": "synthetic",
             "config": {"workload": args.workload, "description": wl["desc"],
-                       "csr_entries": n_entries, "l2": "inputs larger than L2"},
+                       "csr_entries": n_entries, "l2": "inputs larger than L2",
+                       "step": "a bounded sample of the workload: the oracle's first best-move "
+                               "round over a prefix of the vertices (see cpu_baseline.sample)"},
             "cpu_baseline": {"value": round(value, 6), "unit": "GEdges/s", "cores": 1,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": round(value, 6), "unit": "GEdges/s", "h2d_bytes_per_step": 0,
@@ -504,7 +507,7 @@ def run_ours(args, rank, world, local):
     cpu = None
     serving = None
     if rank == 0:
-        v, desc = oracle_sample(host, wl, args.cpu_seconds)
+        v, desc, _ = oracle_sample(host, wl, args.cpu_seconds)
         cpu = {"value": round(v, 6), "unit": "GEdges/s", "cores": 1, "kind": "oracle",
                "sample": desc}
         if args.serving > 0:

@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--serving", type=int, default=160,
                     help="graphs of the serving stream to run (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="tuning file for lcc_autotune: reuse this GPU's line if present, "
+                         "else measure and append (keeps the routing fixed across runs)")
     return ap.parse_args()
 
 
@@ -412,7 +415,7 @@ def run_ours(args, rank, world, local):
     sched = L.schedule(num_iter=wl["num_iter"], timing=True)
     # degree routing for this GPU and graph, chosen before the timed region
     t_tune = time.perf_counter()
-    warp_max = L.lcc_autotune(G, wl["p"], wl["q"], wl["mode"])
+    warp_max = L.lcc_autotune(G, wl["p"], wl["q"], wl["mode"], args.tuning_cache)
     t_tune = time.perf_counter() - t_tune
 
     def step():
@@ -529,8 +532,11 @@ def run_ours(args, rank, world, local):
                        "pairs_sorted": stats[-1]["pairs_sorted"],
                        "generation_s": round(t_gen, 2),
                        "tuning": {"warp_max": warp_max, "autotune_s": round(t_tune, 2),
-                                  "chosen_by": "lcc_autotune on this graph before timing "
-                                               "(3 best-move rounds per routing)"},
+                                  "chosen_by": ("lcc_autotune on this graph before timing "
+                                                "(3 best-move rounds per routing)"
+                                                if not args.tuning_cache else
+                                                "lcc_autotune with the tuning file "
+                                                + args.tuning_cache)},
                        "degree_buckets": degree_shares(host["off"]) if host else None,
                        "l2": "inputs larger than L2 (CSR ~16.5 GB vs 129 MB L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -158,8 +158,8 @@ def profile_traffic():
     want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].rsplit(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("k_round.cu sha256[:16]") != want:
         return None

@@ -1,5 +1,5 @@
 // Compress (Sec. 3.1, Appendix B) as relabel -> emit -> radix sort ->
-// segmented reduce -> CSR, over a table of jobs laid out in one flat vertex
+// reduce by key -> CSR, over a table of jobs laid out in one flat vertex
 // space (vstart[j] = first flat index of job j).
 //
 //   occ/rank   occupied cluster ids, exclusive scan -> dense coarse ids in
@@ -9,7 +9,8 @@
 //              key = (global coarse id of u) << 32 | (local coarse id of v)
 //              and value w; entries inside a cluster are dropped;
 //   sort       LSD radix sort, 8-bit digits, only on the bits in use;
-//   reduce     equal keys are summed (parallel edges merged);
+//   reduce     equal keys are summed (parallel edges merged): heads per tile,
+//              a scan of the tile counts, then keys and sums per tile;
 //   CSR        row r starts at the first unique key >= r << 32.
 #include "lcc_internal.cuh"
 
@@ -563,66 +564,6 @@ void launch_rb_write(const uint64_t *keys, const int64_t *vals, int64_t n, const
   k_rb_write<<<(unsigned)rb_tiles(n), RB_T, 0, st>>>(keys, vals, n, tile_off, ukeys, uvals);
 }
 
-// --------------------------------------------------- segmented reduce ----
-
-__global__ void k_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
-}
-
-void launch_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags, cudaStream_t st,
-                      const Dev &d) {
-  if (n <= 0) return;
-  k_seg_heads<<<grid_for(n, 256, d), 256, 0, st>>>(keys, n, flags);
-}
-
-// idx = exclusive scan of the head flags.  Each thread sums a chunk of 8
-// consecutive entries; a run that lies wholly inside the chunk is written
-// directly, runs crossing a chunk border are added atomically (uvals must be
-// zeroed beforehand).
-constexpr int SEG_C = 8;
-__global__ void k_seg_reduce(const uint64_t *__restrict__ keys, const int64_t *__restrict__ vals,
-                             const int64_t *__restrict__ idx, int64_t n, uint64_t *ukeys,
-                             int64_t *uvals) {
-  const int64_t nchunks = (n + SEG_C - 1) / SEG_C;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lo = c * SEG_C;
-    int64_t hi = lo + SEG_C;
-    if (hi > n) hi = n;
-    bool started_here = (lo == 0) || keys[lo] != keys[lo - 1];
-    int64_t sum = 0;
-    for (int64_t i = lo; i < hi; ++i) {
-      const bool head = (i == 0) || keys[i] != keys[i - 1];
-      if (head && i > lo) {
-        const int64_t u = idx[i] - 1;  // the run ending at i - 1
-        if (started_here)
-          uvals[u] = sum;
-        else
-          atomic_add_i64(uvals + u, sum);
-        sum = 0;
-        started_here = true;
-      }
-      if (head) ukeys[idx[i]] = keys[i];
-      sum += vals[i];
-    }
-    const int64_t i = hi - 1;
-    const int64_t u = idx[i] + ((i == 0 || keys[i] != keys[i - 1]) ? 1 : 0) - 1;
-    const bool ends_here = (hi == n) || keys[hi] != keys[hi - 1];
-    if (started_here && ends_here)
-      uvals[u] = sum;
-    else
-      atomic_add_i64(uvals + u, sum);
-  }
-}
-
-void launch_seg_reduce(const uint64_t *keys, const int64_t *vals, const int64_t *idx, int64_t n,
-                       uint64_t *ukeys, int64_t *uvals, cudaStream_t st, const Dev &d) {
-  if (n <= 0) return;
-  const int64_t nchunks = (n + SEG_C - 1) / SEG_C;
-  k_seg_reduce<<<grid_for(nchunks, 256, d), 256, 0, st>>>(keys, vals, idx, n, ukeys, uvals);
-}
 
 __global__ void k_csr_rows(const uint64_t *__restrict__ ukeys, int64_t nu, int64_t nrows,
                            int64_t *offg, int32_t *nbr_out) {

@@ -386,10 +386,6 @@ int64_t rb_tiles(int64_t n);
 void launch_rb_count(const uint64_t *keys, int64_t n, int64_t *tile_heads, cudaStream_t st);
 void launch_rb_write(const uint64_t *keys, const int64_t *vals, int64_t n, const int64_t *tile_off,
                      uint64_t *ukeys, int64_t *uvals, cudaStream_t st);
-void launch_seg_heads(const uint64_t *keys, int64_t n, int64_t *flags, cudaStream_t st,
-                      const Dev &d);
-void launch_seg_reduce(const uint64_t *keys, const int64_t *vals, const int64_t *idx, int64_t n,
-                       uint64_t *ukeys, int64_t *uvals, cudaStream_t st, const Dev &d);
 void launch_csr_rows(const uint64_t *ukeys, int64_t nu, int64_t nrows, int64_t *offg,
                      int32_t *nbr_out, cudaStream_t st, const Dev &d);
 

@@ -148,11 +148,11 @@ def random_gather_rate(dev):
     return rate
 
 
-def profile_traffic():
+def profile_traffic(path=None, src=None):
     """Per-edge DRAM traffic of the best-move kernels from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "bestmove_rmat.md")
-    src = os.path.join(ROOT, "paper_2108_01731_gb300", "csrc", "k_round.cu")
+    path = path or os.path.join(ROOT, "profiles", "bestmove_rmat.md")
+    src = src or os.path.join(ROOT, "paper_2108_01731_gb300", "csrc", "k_round.cu")
     if not os.path.exists(path):
         return None
     want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

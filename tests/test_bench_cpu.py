@@ -1,0 +1,52 @@
+"""Host-side logic of bench.py (no GPU): the profile parser behind
+roofline.traffic, and the reference arm's JSON line on a small workload."""
+import hashlib
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_profile_traffic_reads_both_keys(tmp_path):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "p.md"
+    prof.write_text("# title\n\n- dram bytes per edge scanned: 38.25\n"
+                    "- k_round.cu sha256[:16]: %s\n" % sha)
+    assert bench.profile_traffic(str(prof), str(src)) == 38.25
+    src.write_text("changed kernel source\n")
+    assert bench.profile_traffic(str(prof), str(src)) is None
+
+
+def test_committed_profile_is_parseable():
+    vals = {}
+    for line in open(os.path.join(ROOT, "profiles", "bestmove_rmat.md")):
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].rsplit(": ", 1)
+            vals[k] = v
+    assert float(vals["dram bytes per edge scanned"]) > 0
+    assert len(vals["k_round.cu sha256[:16]"]) == 16
+
+
+@pytest.mark.slow
+def test_reference_arm_line_on_cpu():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "sbm1e4", "--steps", "1", "--warmup", "0",
+                          "--cpu-seconds", "1"], capture_output=True, text=True, cwd=ROOT,
+                         timeout=600, env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

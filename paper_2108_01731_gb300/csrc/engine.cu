@@ -258,7 +258,10 @@ void Engine::build_layout(std::vector<Level *> &lvs, std::vector<Store *> &store
   std::vector<int64_t> vs(1, 0), es(1, 0);
   for (size_t i = 0; i < lvs.size(); ++i) {
     Level &L = *lvs[i];
-    if (!L.lk || L.n * (int64_t)sizeof(unsigned long long) <= layout_min_bytes()) continue;
+    // the layout kernels index a level's entries from 0
+    if (!L.lk || !L.entries_from_zero ||
+        L.n * (int64_t)sizeof(unsigned long long) <= layout_min_bytes())
+      continue;
     L.pos = stores[i]->alloc<int32_t>(L.n);
     L.gnbr = stores[i]->alloc<int32_t>(L.info.nnz);
     tab.push_back(ljob_of(L));
@@ -592,10 +595,12 @@ void Engine::contract(std::vector<Job *> &js) {
   const int nj = (int)js.size();
   if (timing) CK(cudaEventRecord(ev_[4], st_));
   std::vector<CJob> tab(nj);
-  std::vector<int64_t> vs(nj + 1);
-  int64_t vt = 0;
+  std::vector<int64_t> vs(nj + 1), es(nj + 1);
+  int64_t vt = 0, et = 0;
   for (int i = 0; i < nj; ++i) {
     Level &L = js[i]->lv[js[i]->depth];
+    es[i] = et;
+    et += L.info.nnz;
     CJob &c = tab[i];
     memset(&c, 0, sizeof(c));
     c.off = L.off;
@@ -611,46 +616,47 @@ void Engine::contract(std::vector<Job *> &js) {
     vt += L.n;
   }
   vs[nj] = vt;
+  es[nj] = et;
   auto store = std::make_shared<Store>(st_);
   int32_t *map_u = store->alloc<int32_t>(vt);
   for (int i = 0; i < nj; ++i) tab[i].map = map_u + vs[i];
 
   Store tmp(st_);
   CJob *dt = tmp.alloc<CJob>(nj);
-  int64_t *dv = tmp.alloc<int64_t>(nj + 1);
+  int64_t *dv = tmp.alloc<int64_t>(2 * (nj + 1));
+  int64_t *de = dv + (nj + 1);  // first flat entry of each job
   {
-    char *h = (char *)stage(nj * sizeof(CJob) + (nj + 1) * 8);
+    char *h = (char *)stage(nj * sizeof(CJob) + 2 * (nj + 1) * 8);
     memcpy(h, tab.data(), nj * sizeof(CJob));
     memcpy(h + nj * sizeof(CJob), vs.data(), (nj + 1) * 8);
+    memcpy(h + nj * sizeof(CJob) + (nj + 1) * 8, es.data(), (nj + 1) * 8);
     CK(cudaMemcpyAsync(dt, h, nj * sizeof(CJob), cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(dv, h + nj * sizeof(CJob), (nj + 1) * 8, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(dv, h + nj * sizeof(CJob), 2 * (nj + 1) * 8, cudaMemcpyHostToDevice,
+                       st_));
   }
   int64_t *rank = tmp.alloc<int64_t>(vt + 1);
   int32_t *gmap = tmp.alloc<int32_t>(vt);
   int32_t *gmapp = tmp.alloc<int32_t>(vt);
-  int64_t *pcnt = tmp.alloc<int64_t>(vt + 1);
   int64_t *stmp = tmp.alloc<int64_t>(scan_tmp_elems(vt + 1));
   int64_t *jc = tmp.alloc<int64_t>(2 * nj);
   int32_t *err = tmp.alloc<int32_t>(1);
+  unsigned long long *intra = tmp.alloc<unsigned long long>(1);
   CK(cudaMemsetAsync(rank, 0, (vt + 1) * 8, st_));
-  CK(cudaMemsetAsync(pcnt + vt, 0, 8, st_));
   CK(cudaMemsetAsync(err, 0, 4, st_));
+  CK(cudaMemsetAsync(intra, 0, 8, st_));
   launch_occ(dt, dv, nj, vt, rank, err, st_, d_);
   scan_exclusive_i64(rank, vt, stmp, st_, d_);
   launch_job_counts(dv, nj, rank, jc, st_);
   launch_relabel(dt, dv, nj, vt, rank, gmap, gmapp, st_, d_);
-  launch_emit_count(dt, dv, nj, vt, gmap, gmapp, pcnt, st_, d_);
-  scan_exclusive_i64(pcnt, vt, stmp, st_, d_);
-  note_launches(12);
+  note_launches(8);
   int64_t *hb = (int64_t *)stage2((3 + 2 * nj) * 8);
   CK(cudaMemcpyAsync(hb, rank + vt, 8, cudaMemcpyDeviceToHost, st_));
-  CK(cudaMemcpyAsync(hb + 1, pcnt + vt, 8, cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(hb + 2, err, 4, cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(hb + 3, jc, 2 * nj * 8, cudaMemcpyDeviceToHost, st_));
   sync_checked(st_);
   if ((int32_t)hb[2]) throw Error(LCC_ERR_INVALID, "label out of range in Compress");
   const int64_t ntot = hb[0];
-  const int64_t P = hb[1];
+  const int64_t P = et;  // every entry is emitted; those inside clusters sort last
   std::vector<int64_t> nprime(nj), cbase(nj);
   int64_t nmax = 1;
   for (int i = 0; i < nj; ++i) {
@@ -658,21 +664,21 @@ void Engine::contract(std::vector<Job *> &js) {
     cbase[i] = hb[3 + 2 * i + 1];
     nmax = std::max(nmax, nprime[i]);
   }
-  if (ntot >= ((int64_t)1 << 31)) throw Error(LCC_ERR_OVERFLOW, "too many coarse vertices");
-  stats.pairs += P;
+  if (ntot >= ((int64_t)1 << 31) - 1) throw Error(LCC_ERR_OVERFLOW, "too many coarse vertices");
 
-  // the buffers the sort leaves free are reused for head flags (P + 1) and
-  // unique keys (<= P)
-  uint64_t *keys = tmp.alloc<uint64_t>(P + 1);
+  // the buffer the sort leaves free is reused for the unique keys (<= P)
+  uint64_t *keys = tmp.alloc<uint64_t>(P);
   int64_t *vals = tmp.alloc<int64_t>(P);
-  uint64_t *keys2 = tmp.alloc<uint64_t>(P + 1);
+  uint64_t *keys2 = tmp.alloc<uint64_t>(P);
   int64_t *vals2 = tmp.alloc<int64_t>(P);
-  launch_emit_write(dt, dv, nj, vt, gmap, gmapp, rank, pcnt, keys, vals, st_, d_);
+  launch_emit_all(dt, dv, de, nj, vt, gmap, gmapp, rank, keys, vals, intra, st_, d_);
   int64_t *knew = store->alloc<int64_t>(ntot);
   launch_knew(dt, dv, nj, vt, rank, knew, st_, d_);
   note_launches(2);
   int shifts[16], np = 0;
-  const int lb = bits_for(nmax), hbits = bits_for(ntot);
+  // the high half on bits_for(ntot + 1) bits: no coarse id is all ones there,
+  // so the intra-cluster key (all ones) sorts after every real pair
+  const int lb = bits_for(nmax), hbits = bits_for(ntot + 1);
   for (int s = 0; s < lb; s += 8) shifts[np++] = s;
   for (int s = 32; s < 32 + hbits; s += 8) shifts[np++] = s;
   int64_t *rtmp = tmp.alloc<int64_t>(radix_tmp_elems(P, np));
@@ -692,12 +698,17 @@ void Engine::contract(std::vector<Job *> &js) {
   scan_exclusive_i64(toff, nt, stmp = tmp.alloc<int64_t>(scan_tmp_elems(nt + 1)), st_, d_);
   note_launches(3);
   CK(cudaMemcpyAsync(hb, toff + nt, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hb + 1, intra, 8, cudaMemcpyDeviceToHost, st_));
   sync_checked(st_);
-  const int64_t U = hb[0];
-  int64_t *uvals = store->alloc<int64_t>(U);
+  // the last run holds the intra-cluster entries, if there are any
+  const int64_t Uall = hb[0];
+  const int64_t nintra = hb[1];
+  const int64_t U = Uall - (nintra > 0 ? 1 : 0);
+  stats.pairs += P - nintra;
+  int64_t *uvals = store->alloc<int64_t>(Uall);
   int32_t *unbr = store->alloc<int32_t>(U);
   int64_t *offg = store->alloc<int64_t>(ntot + 1);
-  CK(cudaMemsetAsync(uvals, 0, (U > 0 ? U : 1) * 8, st_));
+  CK(cudaMemsetAsync(uvals, 0, (Uall > 0 ? Uall : 1) * 8, st_));
   launch_rb_write(sk, sv, P, toff, ukeys, uvals, st_);
   launch_csr_rows(ukeys, U, ntot, offg, unbr, st_, d_);
   note_launches(2);
@@ -724,6 +735,7 @@ void Engine::contract(std::vector<Job *> &js) {
     Level nl;
     nl.n = nprime[i];
     nl.warp_max = tuning_for(dev_).warp_max;
+    nl.entries_from_zero = cbase[i] == 0;
     nl.off = offg + cbase[i];
     nl.nbr = unbr;
     nl.w = uvals;

@@ -111,6 +111,10 @@ struct Level {
   int32_t *pos = nullptr;            // gather layout (null: identity), see JobDev
   int32_t *gnbr = nullptr;
   int32_t warp_max = T_WARP;         // degree routing the level was bucketed with
+  // the level's entries start at position 0 of nbr (the input level, or the
+  // first job of a contraction batch; the other jobs of a batch index a
+  // shared entry array from off[0] > 0)
+  bool entries_from_zero = true;
   int32_t *map = nullptr;  // vertex -> coarse vertex of the next level
   std::shared_ptr<Store> store;
   std::shared_ptr<Store> map_store;

@@ -7,7 +7,8 @@
 //              coarse id of cluster c of job j;
 //   emit       every entry (u, v) whose ends lie in different clusters gives
 //              key = (global coarse id of u) << 32 | (local coarse id of v)
-//              and value w; entries inside a cluster are dropped;
+//              and value w, at its own entry position; entries inside a
+//              cluster get a key that sorts last and are dropped there;
 //   sort       LSD radix sort, 8-bit digits, only on the bits in use;
 //   reduce     equal keys are summed (parallel edges merged): heads per tile,
 //              a scan of the tile counts, then keys and sums per tile;
@@ -114,82 +115,55 @@ void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, in
 
 // ------------------------------------------------------------- emission --
 
-__global__ void __launch_bounds__(256) k_emit_count(const CJob *__restrict__ jobs,
-                                                    const int64_t *__restrict__ vstart, int njobs,
-                                                    int64_t vtot, const int32_t *__restrict__ gmap,
-                                                    const int32_t *__restrict__ gmapp,
-                                                    int64_t *pcnt) {
+// Every entry (u, v) of every job is written at its flat entry position
+// estart[j] + (e - off[0]) (a coarse level of a contraction batch indexes a
+// shared entry array, so its offsets need not start at 0):
+// key = (global coarse id of u) << 32 | (local coarse id of v)
+// and value w; an entry inside a cluster gets the key EMIT_INTRA instead,
+// which sorts after every real pair (the sort covers the high half on
+// bits_for(ntot + 1) bits, on which no coarse id is all ones), so the sorted
+// array ends with the intra entries and the reduction stops before them.
+// `intra` counts them.
+__global__ void __launch_bounds__(256) k_emit_all(const CJob *__restrict__ jobs,
+                                                  const int64_t *__restrict__ vstart,
+                                                  const int64_t *__restrict__ estart, int njobs,
+                                                  int64_t vtot, const int32_t *__restrict__ gmap,
+                                                  const int32_t *__restrict__ gmapp,
+                                                  const int64_t *__restrict__ rank, uint64_t *keys,
+                                                  int64_t *vals, unsigned long long *intra) {
   const int lane = threadIdx.x & 31;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  long long my_intra = 0;
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
        i += warps_total) {
     const int j = find_job(vstart, njobs, i);
     const CJob *J = jobs + j;
     const int64_t v = i - vstart[j];
     const int64_t vs = vstart[j];
-    const int32_t cu = gmap[i];
-    int cnt = 0;
-    for (int64_t e = J->off[v] + lane; e < J->off[v + 1]; e += 32)
-      cnt += gmapp[vs + __ldg(J->gnbr + e)] != cu;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
-    if (lane == 0) pcnt[i] = cnt;
-  }
-}
-
-void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int32_t *gmapp, int64_t *pcnt, cudaStream_t st,
-                       const Dev &d) {
-  if (vtot <= 0) return;
-  k_emit_count<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap,
-                                                            gmapp, pcnt);
-}
-
-__global__ void __launch_bounds__(256) k_emit_write(const CJob *__restrict__ jobs,
-                                                    const int64_t *__restrict__ vstart, int njobs,
-                                                    int64_t vtot, const int32_t *__restrict__ gmap,
-                                                    const int32_t *__restrict__ gmapp,
-                                                    const int64_t *__restrict__ rank,
-                                                    const int64_t *__restrict__ ppos,
-                                                    uint64_t *keys, int64_t *vals) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
-       i += warps_total) {
-    const int j = find_job(vstart, njobs, i);
-    const CJob *J = jobs + j;
-    const int64_t v = i - vstart[j];
-    const int64_t vs = vstart[j];
+    const int64_t es = estart[j] - J->off[0];
     const int64_t cbase = rank[vs];
     const uint64_t cu = (uint64_t)(uint32_t)gmap[i];
-    int64_t pos = ppos[i];
     const int64_t beg = J->off[v], end = J->off[v + 1];
-    for (int64_t e0 = beg; e0 < end; e0 += 32) {
-      const int64_t e = e0 + lane;
-      bool out = false;
-      int32_t cv = 0;
-      if (e < end) {
-        cv = gmapp[vs + __ldg(J->gnbr + e)];
-        out = (uint32_t)cv != (uint32_t)cu;
-      }
-      const unsigned m = __ballot_sync(FULL, out);
-      if (out) {
-        const int64_t p = pos + __popc(m & lanemask_lt());
-        keys[p] = (cu << 32) | (uint64_t)(uint32_t)(cv - cbase);
-        vals[p] = load_w(J->w, J->wtype, e);
-      }
-      pos += __popc(m);
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      const int32_t cv = gmapp[vs + __ldg(J->gnbr + e)];
+      const bool in = (uint32_t)cv == (uint32_t)cu;
+      keys[es + e] = in ? EMIT_INTRA : ((cu << 32) | (uint64_t)(uint32_t)(cv - cbase));
+      vals[es + e] = load_w(J->w, J->wtype, e);
+      my_intra += in ? 1 : 0;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_intra += __shfl_xor_sync(FULL, my_intra, o);
+  if (lane == 0 && my_intra) atomicAdd(intra, (unsigned long long)my_intra);
 }
 
-void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
-                       const int64_t *ppos, uint64_t *keys, int64_t *vals, cudaStream_t st,
-                       const Dev &d) {
+void launch_emit_all(const CJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
+                     int64_t vtot, const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
+                     uint64_t *keys, int64_t *vals, unsigned long long *intra, cudaStream_t st,
+                     const Dev &d) {
   if (vtot <= 0) return;
-  k_emit_write<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, gmap,
-                                                            gmapp, rank, ppos, keys, vals);
+  k_emit_all<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, estart, njobs, vtot, gmap,
+                                                          gmapp, rank, keys, vals, intra);
 }
 
 // ----------------------------------------------------------------- scan --

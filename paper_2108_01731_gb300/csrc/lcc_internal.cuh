@@ -358,13 +358,14 @@ void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot
 void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                     const int64_t *rank, int32_t *gmap, int32_t *gmapp, cudaStream_t st,
                     const Dev &d);
-void launch_emit_count(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int32_t *gmapp, int64_t *pcnt, cudaStream_t st,
-                       const Dev &d);
-void launch_emit_write(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
-                       const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
-                       const int64_t *ppos, uint64_t *keys, int64_t *vals, cudaStream_t st,
-                       const Dev &d);
+// Key of an entry inside a cluster (sorts after every real pair).
+constexpr uint64_t EMIT_INTRA = ~0ull;
+// Every entry of every job at flat position estart[j] + e (see k_contract.cu);
+// intra (zeroed) receives the number of entries inside clusters.
+void launch_emit_all(const CJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
+                     int64_t vtot, const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
+                     uint64_t *keys, int64_t *vals, unsigned long long *intra, cudaStream_t st,
+                     const Dev &d);
 void launch_knew(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                  const int64_t *rank, int64_t *knew, cudaStream_t st, const Dev &d);
 void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out,

@@ -418,7 +418,15 @@ def test_input_validation(L):
 
 # --------------------------------------------------- batching and serving --
 
-def test_batch_equals_single(L):
+@pytest.mark.parametrize("force_layout", [False, True])
+def test_batch_equals_single(L, monkeypatch, force_layout):
+    """A batch gives every graph its single-run labels and objective.  The
+    coarse levels of a batch share one entry array, so every job but the
+    first indexes it from a nonzero offset; forcing the degree-ordered
+    layout (taken by the levels whose entries start at 0) mixes levels with
+    and without it in one contraction."""
+    if force_layout:
+        monkeypatch.setenv("LCC_LAYOUT_MIN_BYTES", "0")
     names = ["sbm", "hubs", "cl", "rmat", "signed", "hubs_w"]
     modes = [O.NODEW_UNIT, O.NODEW_DEGREE, O.NODEW_DEGREE, O.NODEW_DEGREE, O.NODEW_UNIT,
              O.NODEW_UNIT]

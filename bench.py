@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serving", type=int, default=160,
                     help="graphs of the serving stream to run (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-twin", action="store_true",
+                    help="skip the OpenMP CPU twin's timed first round")
     ap.add_argument("--tuning-cache", default=None,
                     help="tuning file for lcc_autotune: reuse this GPU's line if present, "
                          "else measure and append (keeps the routing fixed across runs)")
@@ -254,6 +256,31 @@ def oracle_sample(host, wl, seconds):
     return (done_edges / done_t / 1e9, "first best-move round of the same graph, vertices "
             "[0, %d) (%d of %d vertices, %d entries scanned), single-threaded oracle"
             % (v0, v0, n, done_edges), done_t)
+
+
+# ------------------------------------------------------- CPU OpenMP twin --
+
+def twin_round(host, wl, gpu_desired):
+    """Times the OpenMP CPU twin on the first full-frontier best-move round of
+    the same graph (every vertex, every host core) and compares its desired
+    clusters with the GPU library's for that round (gpu_desired(labels), the
+    library's lcc_desired on the resident graph)."""
+    import numpy as np
+    n = len(host["off"]) - 1
+    try:
+        import cpu_twin as T
+        k = None if wl["mode"] == 1 else np.ones(n, np.int64)
+        D, ent, secs, cores = T.first_round(host["off"], host["nbr"], host["w"], k,
+                                            wl["p"], wl["q"])
+    except Exception as e:  # no OpenMP toolchain or no host memory for it
+        return {"unavailable": "%s: %s" % (type(e).__name__, e)}
+    Dg = gpu_desired(np.arange(n, dtype=np.int32))
+    return {"value": round(ent / secs / 1e9, 4), "unit": "GEdges/s", "cores": cores,
+            "kind": "openmp twin (same synchronous schedule, all host cores)",
+            "seconds": round(secs, 3),
+            "sample": "first best-move round of the same graph over all %d vertices "
+                      "(%d entries scanned)" % (n, ent),
+            "desired_equal_gpu": bool(np.array_equal(D, Dg))}
 
 
 def degree_shares(off):
@@ -508,11 +535,15 @@ def run_ours(args, rank, world, local):
         del pinned
 
     cpu = None
+    twin = None
     serving = None
     if rank == 0:
         v, desc, _ = oracle_sample(host, wl, args.cpu_seconds)
         cpu = {"value": round(v, 6), "unit": "GEdges/s", "cores": 1, "kind": "oracle",
                "sample": desc}
+        if not args.no_twin:
+            twin = twin_round(host, wl, lambda lab: L.lcc_desired(G, wl["p"], wl["q"],
+                                                                  wl["mode"], lab))
         if args.serving > 0:
             serving = serving_bench(L, args.serving, dev)
     line = {"metric": "best-move GEdges/s", "value": round(value, 4), "unit": "GEdges/s",
@@ -542,6 +573,8 @@ def run_ours(args, rank, world, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks}
+    if twin is not None:
+        line["cpu_parallel"] = twin
     if serving is not None:
         line["serving"] = serving
     G.free()

@@ -50,3 +50,25 @@ def test_reference_arm_line_on_cpu():
     assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_twin_leg_reports_rate_and_agreement():
+    """The bench's OpenMP-twin leg on a small graph, with the oracle standing
+    in for the GPU's desired clusters: a positive rate, the cores used, and
+    agreement with the stand-in (or its absence when it differs)."""
+    import numpy as np
+    import oracle as O
+    from paper_2108_01731_gb300 import inputs as I
+    g = I.to_numpy(I.rmat(12, 30000, seed=3))
+    host = {"off": g["off"], "nbr": g["nbr"], "w": g["w"]}
+    wl = dict(bench.WORKLOADS["rmat22"])
+    k, two_m = O.weighted_degrees(g["off"], g["w"])
+
+    def oracle_desired(lab):
+        return O.desired(g["off"], g["nbr"], g["w"], k, 1, two_m, lab, k)
+
+    out = bench.twin_round(host, wl, oracle_desired)
+    assert out["value"] > 0 and out["cores"] >= 1 and out["desired_equal_gpu"] is True
+    assert "%d entries" % g["nnz"] in out["sample"]
+    out = bench.twin_round(host, wl, lambda lab: oracle_desired(lab)[::-1].copy())
+    assert out["desired_equal_gpu"] is False

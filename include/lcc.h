@@ -34,6 +34,13 @@
  *   - `stream` is a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
  *     or NULL for the legacy default stream.  Calls that return results on the
  *     host synchronise that stream before returning.
+ *
+ * Environment.  LCC_LAYOUT_MIN_BYTES (bytes, default 64 MiB): a level whose
+ * packed label words (8 bytes per vertex) exceed it stores them in a
+ * degree-ordered layout, at 4 bytes per vertex and 4 per CSR entry of extra
+ * device memory.  When one contraction builds the coarse levels of several
+ * graphs together, only the first graph's level takes it.  It moves storage
+ * only, never a result.
  */
 #ifndef LCC_H
 #define LCC_H

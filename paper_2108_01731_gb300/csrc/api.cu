@@ -127,7 +127,7 @@ static lcc_graph *load_graph(const int64_t *offsets, const int32_t *nbrs, const 
   // (a pinned buffer per call would cost more than the copies)
   unsigned long long h[10];
   CK(cudaMemsetAsync(v, 0, 64, st));
-  launch_validate(g->off, g->nbr, (const int32_t *)g->w, n, nnz, v, st, d);
+  launch_validate(g->off, n, nnz, v, st, d);
   CK(cudaMemcpyAsync(v + 8, g->off, 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(v + 9, g->off + n, 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h, v, 10 * 8, cudaMemcpyDeviceToHost, st));

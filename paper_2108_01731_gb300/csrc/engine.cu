@@ -681,7 +681,7 @@ void Engine::contract(std::vector<Job *> &js) {
   const int lb = bits_for(nmax), hbits = bits_for(ntot + 1);
   for (int s = 0; s < lb; s += 8) shifts[np++] = s;
   for (int s = 32; s < 32 + hbits; s += 8) shifts[np++] = s;
-  int64_t *rtmp = tmp.alloc<int64_t>(radix_tmp_elems(P, np));
+  int64_t *rtmp = tmp.alloc<int64_t>(radix_tmp_elems(P));
   bool in_alt = false;
   int lcount = 0;
   radix_sort_pairs(keys, vals, keys2, vals2, P, shifts, np, rtmp, st_, d_, &in_alt, &lcount);

@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(RS_T, 3) k_rs_scatter(const uint64_t *__restri
 
 constexpr size_t RS_SMEM = (size_t)RS_TILE * 16;
 
-int64_t radix_tmp_elems(int64_t n, int npasses) {
+int64_t radix_tmp_elems(int64_t n) {
   const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
   const int64_t m = 256 * ntiles;
   return m + 1 + scan_tmp_elems(m);

@@ -511,8 +511,8 @@ __global__ void __launch_bounds__(256) k_validate_rows(const int64_t *off, const
   }
 }
 
-void launch_validate(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
-                     int64_t nnz, unsigned long long *out8, cudaStream_t st, const Dev &d) {
+void launch_validate(const int64_t *off, int64_t n, int64_t nnz, unsigned long long *out8,
+                     cudaStream_t st, const Dev &d) {
   if (n <= 0) return;
   k_validate_off<<<grid_for(n, 256, d), 256, 0, st>>>(off, n, nnz, out8);
 }

@@ -345,8 +345,8 @@ void launch_canonical(const LJob *jobs, const int64_t *vstart, int njobs, int64_
                       cudaStream_t st, const Dev &d);
 void launch_objective(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                       ObjAcc *acc, cudaStream_t st, const Dev &d);
-void launch_validate(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
-                     int64_t nnz, unsigned long long *out8, cudaStream_t st, const Dev &d);
+void launch_validate(const int64_t *off, int64_t n, int64_t nnz, unsigned long long *out8,
+                     cudaStream_t st, const Dev &d);
 void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
                           unsigned long long *out8, cudaStream_t st, const Dev &d);
 
@@ -376,7 +376,7 @@ int64_t scan_tmp_elems(int64_t n);
 void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, const Dev &d);
 
 // LSD radix sort of (key, val) pairs on the given 8-bit digit positions.
-int64_t radix_tmp_elems(int64_t n, int npasses);
+int64_t radix_tmp_elems(int64_t n);
 void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,
                       int64_t n, const int *shifts, int npasses, int64_t *tmp,
                       cudaStream_t st, const Dev &d, bool *result_in_alt, int *launches);

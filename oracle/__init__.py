@@ -39,6 +39,9 @@ def lib():
                                      P, P, P]
         _lib.orc_best_moves.argtypes = [I64, P, P, P, P, I64, I64, C.c_int,
                                         C.c_int, P, P]
+        _lib.orc_sequential_cc.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
+                                           C.c_uint64, C.c_int, C.c_int, P, P, P,
+                                           P, P]
         _lib.orc_sequential_sweep.argtypes = [I64, P, P, P, P, I64, I64, P, I64]
         _lib.orc_sequential_sweep.restype = I64
         _lib.orc_weighted_degrees_i32.argtypes = [I64, P, P, P]
@@ -197,6 +200,31 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
     if v >= 1 << 127:
         v -= 1 << 128
     return labels, v, den.value, tuple(int(x) for x in st)
+
+
+def sequential_cc(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, seed=0,
+                  max_passes=1000, max_levels=64):
+    """Sequential-CC (Sec. 3.1, Algorithm 2): random-order local moving until a
+    pass moves nothing, then Compress, recursion and Flatten.
+
+    Returns (labels, num, den, stats) with CC = num / den exactly and
+    stats = (levels, passes, moves)."""
+    off, nbr, w = _graph(off, nbr, w)
+    n = len(off) - 1
+    kk = _c(k, np.int64) if k is not None else np.zeros(1, np.int64)
+    labels = np.empty(max(n, 1), np.int32)
+    hi, lo, den = C.c_int64(), C.c_uint64(), C.c_int64()
+    st = np.zeros(3, np.int64)
+    rc = lib().orc_sequential_cc(n, _p(off), _p(nbr), _p(w), _p(kk), mode, p, q,
+                                 seed & ((1 << 64) - 1), max_passes, max_levels,
+                                 _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
+                                 _p(st))
+    if rc:
+        raise ValueError("oracle sequential_cc failed: %d" % rc)
+    v = _i128(hi.value, lo.value)
+    if v >= 1 << 127:
+        v -= 1 << 128
+    return labels[:n], v, den.value, tuple(int(x) for x in st)
 
 
 def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES):

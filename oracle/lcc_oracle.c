@@ -24,6 +24,9 @@
  *                        neighbours of clusters)
  *   Compress, Flatten .. Sec. 3.1 and Appendix B
  *   Parallel-CC ........ Algorithm 1 with the refinement of Sec. 3.2.3
+ *   Sequential-CC ...... Sec. 3.1 (Algorithm 2 in the appendix): random-order
+ *                        local moving to convergence, then Compress, recursion
+ *                        and Flatten; the quality reference
  *
  * Readings where the paper is silent (kept identical on the CUDA side, and
  * listed with their reasons in the design notes):
@@ -438,6 +441,55 @@ static void parallel_cc(const level_t *g, int depth, run_t *r, int32_t *L) {
  * with 2m = sum_v k_v) or CUSTOM (k given).  labels_out receives the
  * canonical labels (R6); num_hi/num_lo receive q' * CC where q' is the
  * effective denominator returned in *den_out. */
+/* Node weights of the input level for a mode (Sec. 2): UNIT k = 1; DEGREE
+ * (modularity) k_v = weighted degree, with lambda = p / (q 2m) carried as the
+ * effective denominator *qe = q 2m; CUSTOM k given.  k is [n]. */
+static int node_weights(int64_t n, const int64_t *off, const int64_t *w,
+                        const int64_t *k_custom, int mode, int64_t q,
+                        int64_t *k, int64_t *qe) {
+  *qe = q;
+  if (mode == NODEW_UNIT) {
+    for (int64_t v = 0; v < n; ++v) k[v] = 1;
+  } else if (mode == NODEW_DEGREE) {
+    i128 two_m = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      i128 d = 0;
+      for (int64_t e = off[v]; e < off[v + 1]; ++e) d += w[e];
+      if (d < 0) return ORC_ERR_INVALID;
+      k[v] = (int64_t)d;
+      two_m += d;
+    }
+    if (two_m <= 0) return ORC_ERR_INVALID;
+    i128 qq = (i128)q * two_m;
+    if (qq > (i128)INT64_MAX) return ORC_ERR_INVALID;
+    *qe = (int64_t)qq;
+  } else if (mode == NODEW_CUSTOM) {
+    for (int64_t v = 0; v < n; ++v) {
+      if (k_custom[v] < 0) return ORC_ERR_INVALID;
+      k[v] = k_custom[v];
+    }
+  } else {
+    return ORC_ERR_INVALID;
+  }
+  return ORC_OK;
+}
+
+/* R6 labels (smallest vertex id of each cluster of L) into labels_out, and
+ * the exact objective of that clustering. */
+static int finish_labels(int64_t n, const int64_t *off, const int32_t *nbr,
+                         const int64_t *w, const int64_t *k, int64_t p,
+                         int64_t qe, const int32_t *L, int32_t *labels_out,
+                         int64_t *num_hi, uint64_t *num_lo) {
+  int32_t *minid = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!minid) return ORC_ERR_OOM;
+  for (int64_t c = 0; c < n; ++c) minid[c] = -1;
+  for (int64_t v = 0; v < n; ++v)
+    if (minid[L[v]] < 0) minid[L[v]] = (int32_t)v;
+  for (int64_t v = 0; v < n; ++v) labels_out[v] = minid[L[v]];
+  free(minid);
+  return orc_objective(n, off, nbr, w, k, p, qe, labels_out, num_hi, num_lo);
+}
+
 int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
                 const int64_t *w, const int64_t *k_custom, int mode,
                 int64_t p, int64_t q, int num_iter, int max_levels, int refine,
@@ -449,30 +501,8 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
   int64_t *k = (int64_t *)malloc(m * sizeof(int64_t));
   if (!k) return ORC_ERR_OOM;
   int64_t qe = q;
-  if (mode == NODEW_UNIT) {
-    for (int64_t v = 0; v < n; ++v) k[v] = 1;
-  } else if (mode == NODEW_DEGREE) {
-    i128 two_m = 0;
-    for (int64_t v = 0; v < n; ++v) {
-      i128 d = 0;
-      for (int64_t e = off[v]; e < off[v + 1]; ++e) d += w[e];
-      if (d < 0) { free(k); return ORC_ERR_INVALID; }
-      k[v] = (int64_t)d;
-      two_m += d;
-    }
-    if (two_m <= 0) { free(k); return ORC_ERR_INVALID; }
-    i128 qq = (i128)q * two_m;
-    if (qq > (i128)INT64_MAX) { free(k); return ORC_ERR_INVALID; }
-    qe = (int64_t)qq;
-  } else if (mode == NODEW_CUSTOM) {
-    for (int64_t v = 0; v < n; ++v) {
-      if (k_custom[v] < 0) { free(k); return ORC_ERR_INVALID; }
-      k[v] = k_custom[v];
-    }
-  } else {
-    free(k);
-    return ORC_ERR_INVALID;
-  }
+  int rc = node_weights(n, off, w, k_custom, mode, q, k, &qe);
+  if (rc != ORC_OK) { free(k); return rc; }
   orc_stats st = {0, 0, 0};
   run_t r = {p, qe, num_iter, max_levels, refine, vset, &st, ORC_OK};
   level_t g = {n, off, nbr, w, k};
@@ -480,15 +510,7 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
   if (!L) { free(k); return ORC_ERR_OOM; }
   parallel_cc(&g, 0, &r, L);
   if (r.err) { free(k); free(L); return r.err; }
-  /* R6: label = smallest vertex id of the cluster */
-  int32_t *minid = (int32_t *)malloc(m * sizeof(int32_t));
-  if (!minid) { free(k); free(L); return ORC_ERR_OOM; }
-  for (int64_t c = 0; c < n; ++c) minid[c] = -1;
-  for (int64_t v = 0; v < n; ++v)
-    if (minid[L[v]] < 0) minid[L[v]] = (int32_t)v;
-  for (int64_t v = 0; v < n; ++v) labels_out[v] = minid[L[v]];
-  free(minid);
-  int rc = orc_objective(n, off, nbr, w, k, p, qe, labels_out, num_hi, num_lo);
+  rc = finish_labels(n, off, nbr, w, k, p, qe, L, labels_out, num_hi, num_lo);
   *den_out = qe;
   if (stats_out) {
     stats_out[0] = st.levels;
@@ -548,6 +570,150 @@ int64_t orc_sequential_sweep(int64_t n, const int64_t *off,
   free(K);
   scratch_free(&s);
   return moves;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sequential-CC: the sequential Louvain method of Sec. 3.1 (Algorithm 2   */
+/* in the appendix), the quality reference of the parallel method          */
+/* ---------------------------------------------------------------------- */
+
+/* SplitMix64 (S. Vigna's public-domain generator after Steele, Lea and
+ * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+ * advances the state *x and returns the next output. */
+static uint64_t splitmix64(uint64_t *x) {
+  uint64_t z = (*x += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+/* sigma = a random permutation of 0..n-1: Fisher-Yates, the swap partner of
+ * position i taken as floor(r (i + 1) / 2^64) from the SplitMix64 stream
+ * that starts at state `stream`. */
+static void random_permutation(int64_t n, uint64_t stream, int32_t *sigma) {
+  uint64_t x = stream;
+  for (int64_t i = 0; i < n; ++i) sigma[i] = (int32_t)i;
+  for (int64_t i = n - 1; i > 0; --i) {
+    const uint64_t r = splitmix64(&x);
+    const int64_t j = (int64_t)(((unsigned __int128)r * (uint64_t)(i + 1)) >> 64);
+    const int32_t t = sigma[i];
+    sigma[i] = sigma[j];
+    sigma[j] = t;
+  }
+}
+
+typedef struct {
+  int64_t p, q;
+  uint64_t seed;
+  int max_passes, max_levels;
+  int64_t levels, passes, moves;
+  int err;
+} seq_run_t;
+
+/* One level: from singletons, passes over a fresh random order move each
+ * vertex at once to its best cluster (the Appendix A gain, readings R1 and
+ * R2), until a pass moves nothing; every move raises CC, so "the objective
+ * increased during the pass" is "the pass moved a vertex".  Then, if
+ * anything moved, Compress, recurse and Flatten; there is no refinement.
+ * The pass over level `depth` number `pass` draws its order from the stream
+ * seed + depth 2^32 + pass. */
+static void sequential_cc(const level_t *g, int depth, seq_run_t *r, int32_t *L) {
+  const int64_t n = g->n;
+  const size_t m = (size_t)(n > 0 ? n : 1);
+  if (r->levels < depth + 1) r->levels = depth + 1;
+  int64_t *K = (int64_t *)malloc(m * sizeof(int64_t));
+  int32_t *sigma = (int32_t *)malloc(m * sizeof(int32_t));
+  scratch_t s;
+  int rc = scratch_init(&s, n);
+  if (!K || !sigma || rc != ORC_OK) {
+    r->err = ORC_ERR_OOM;
+    free(K); free(sigma); scratch_free(&s);
+    return;
+  }
+  for (int64_t v = 0; v < n; ++v) { L[v] = (int32_t)v; K[v] = g->k[v]; }
+  int64_t level_moves = 0;
+  for (int pass = 0; pass < r->max_passes; ++pass) {
+    random_permutation(n, r->seed + ((uint64_t)depth << 32) + (uint64_t)pass, sigma);
+    int64_t moves = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t v = sigma[i];
+      const int32_t d = desired_cluster(v, g->off[v], g->off[v + 1], g->nbr,
+                                        g->w, g->k, r->p, r->q, L, K, &s);
+      if (d != L[v]) {
+        K[L[v]] -= g->k[v];
+        K[d] += g->k[v];
+        L[v] = d;
+        ++moves;
+      }
+    }
+    r->passes += 1;
+    level_moves += moves;
+    if (moves == 0) break;
+  }
+  scratch_free(&s);
+  free(sigma);
+  free(K);
+  r->moves += level_moves;
+  if (level_moves == 0 || depth + 1 >= r->max_levels) return;
+
+  int32_t *map = (int32_t *)malloc(m * sizeof(int32_t));
+  int64_t n2 = 0, nnz2 = 0;
+  int64_t *off2 = NULL, *w2 = NULL, *k2 = NULL;
+  int32_t *nbr2 = NULL;
+  if (!map) { r->err = ORC_ERR_OOM; return; }
+  rc = orc_compress(n, g->off, g->nbr, g->w, g->k, L, map, &n2, &nnz2, &off2,
+                    &nbr2, &w2, &k2);
+  if (rc != ORC_OK) { r->err = rc; free(map); return; }
+  if (n2 < n) {
+    level_t g2 = {n2, off2, nbr2, w2, k2};
+    int32_t *L2 = (int32_t *)malloc((size_t)(n2 > 0 ? n2 : 1) * sizeof(int32_t));
+    if (!L2) {
+      r->err = ORC_ERR_OOM;
+    } else {
+      sequential_cc(&g2, depth + 1, r, L2);
+      if (!r->err)
+        for (int64_t v = 0; v < n; ++v) L[v] = L2[map[v]];  /* Flatten */
+      free(L2);
+    }
+  }
+  free(off2); free(nbr2); free(w2); free(k2); free(map);
+}
+
+/* Sequential-CC on the input graph (node weights by `mode` as in
+ * orc_cluster).  max_passes caps the passes of one level (a level whose cap
+ * is reached proceeds as if it had converged); max_levels caps the depth.
+ * Outputs: R6 labels, q' CC in (num_hi, num_lo) with q' in *den_out, and
+ * stats = (levels, passes, moves). */
+int orc_sequential_cc(int64_t n, const int64_t *off, const int32_t *nbr,
+                      const int64_t *w, const int64_t *k_custom, int mode,
+                      int64_t p, int64_t q, uint64_t seed, int max_passes,
+                      int max_levels, int32_t *labels_out, int64_t *num_hi,
+                      uint64_t *num_lo, int64_t *den_out, int64_t *stats_out) {
+  if (n < 0 || p <= 0 || q <= 0 || max_passes < 1 || max_levels < 1)
+    return ORC_ERR_INVALID;
+  const size_t m = (size_t)(n > 0 ? n : 1);
+  int64_t *k = (int64_t *)malloc(m * sizeof(int64_t));
+  int32_t *L = (int32_t *)malloc(m * sizeof(int32_t));
+  if (!k || !L) { free(k); free(L); return ORC_ERR_OOM; }
+  int64_t qe = q;
+  int rc = node_weights(n, off, w, k_custom, mode, q, k, &qe);
+  if (rc == ORC_OK) {
+    seq_run_t r = {p, qe, seed, max_passes, max_levels, 0, 0, 0, ORC_OK};
+    level_t g = {n, off, nbr, w, k};
+    sequential_cc(&g, 0, &r, L);
+    rc = r.err;
+    if (rc == ORC_OK)
+      rc = finish_labels(n, off, nbr, w, k, p, qe, L, labels_out, num_hi, num_lo);
+    *den_out = qe;
+    if (stats_out) {
+      stats_out[0] = r.levels;
+      stats_out[1] = r.passes;
+      stats_out[2] = r.moves;
+    }
+  }
+  free(k);
+  free(L);
+  return rc;
 }
 
 /* Modularity node weights (Sec. 2): k_v = sum_u w_uv, from int32 weights

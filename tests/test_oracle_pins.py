@@ -472,3 +472,89 @@ def test_desired_list_equals_range():
     idx = np.concatenate(rows)
     D = O.desired_list(n, verts, off_l, g["nbr"][idx], g["w"][idx], k, 1, 7, L, K)
     assert np.array_equal(D, full[verts])
+
+
+# --------------------------------------------------------- Sequential-CC --
+
+def improving_neighbour_move(g, W, E, k, lam, labels):
+    """A vertex and neighbouring cluster whose move strictly raises the
+    objective definition, or None."""
+    off, nbr = g["off"], g["nbr"]
+    base = cc_definition(W, E, k, lam, labels)
+    for v in range(g["n"]):
+        for c in sorted(set(int(labels[u]) for u in nbr[off[v]:off[v + 1]]) - {int(labels[v])}):
+            L2 = labels.copy()
+            L2[v] = c
+            if cc_definition(W, E, k, lam, L2) > base:
+                return v, c
+    return None
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_sequential_cc_level_ends_at_local_optimum(seed):
+    """Sec. 3.1: local moving repeats until no vertex moves, so one level ends
+    where no vertex gains by joining a neighbouring cluster (checked by
+    re-evaluating the definition for every such move)."""
+    g = small_graph(800 + seed, n=8, p=0.5, lo=-3, hi=5)
+    W, E = dense(g)
+    k = np.ones(g["n"])
+    for p, q in [(1, 4), (1, 1)]:
+        labels, num, den, st = O.sequential_cc(g["off"], g["nbr"], g["w"], p, q,
+                                               seed=seed, max_levels=1)
+        assert improving_neighbour_move(g, W, E, k, Fraction(p, q), labels) is None
+        assert Fraction(num, den) == cc_definition(W, E, k, Fraction(p, q), labels)
+        assert st[0] == 1 and (num > 0) == (st[2] > 0) and num >= 0
+
+
+@pytest.mark.parametrize("r,s,p,q", [(5, 3, 1, 2), (4, 5, 1, 3), (3, 8, 2, 3)])
+def test_sequential_cc_recovers_disjoint_cliques_for_any_order(r, s, p, q):
+    """Inside a clique with lambda < 1 a vertex gains (1 - lambda)(s2 - s1 + 1)
+    by leaving its part of size s1 for another of size s2, so the only local
+    optimum is the whole clique: CC = r s (s - 1)(1 - lambda) whatever the
+    random order; the coarse level has no edges and ends the recursion."""
+    g, members = cliques(r, s, r * 10 + s)
+    for seed in range(4):
+        labels, num, den, st = O.sequential_cc(g["off"], g["nbr"], None, p, q, seed=seed)
+        for mem in members:
+            assert all(labels[v] == mem[0] for v in mem)
+        assert den == q and num == r * s * (s - 1) * (q - p)
+        assert st[0] == 2 and st[2] >= r * (s - 1)
+
+
+def test_sequential_cc_merges_the_edge_sync_rounds_swap():
+    """The isolated edge that the synchronous rounds swap forever (Sec. 3.1,
+    Figure 1's pathology) is merged by the sequential method: CC = 2 (1 - lambda)."""
+    import torch
+    g = I.to_numpy(I.pairs_to_csr(torch.tensor([0]), torch.tensor([1]), 2))
+    for seed in range(3):
+        labels, num, den, st = O.sequential_cc(g["off"], g["nbr"], None, 1, 3, seed=seed)
+        assert list(labels) == [0, 0] and (num, den) == (2 * (3 - 1), 3)
+        assert st == (2, 3, 1)  # level 0: a moving pass and a quiet one; level 1: one pass
+
+
+def test_sequential_cc_bounded_by_best_partition_and_deterministic():
+    for seed in range(3):
+        g = small_graph(900 + seed, n=7, p=0.5, lo=-2, hi=4)
+        W, E = dense(g)
+        k = np.ones(g["n"])
+        labels, num, den, _ = O.sequential_cc(g["off"], g["nbr"], g["w"], 1, 4, seed=seed)
+        best = max(cc_definition(W, E, k, Fraction(1, 4), np.array(a))
+                   for a in set_partitions(g["n"]))
+        assert Fraction(num, den) <= best
+        again = O.sequential_cc(g["off"], g["nbr"], g["w"], 1, 4, seed=seed)
+        assert np.array_equal(again[0], labels) and again[1:] == (num, den, again[3])
+
+
+def test_sequential_cc_planted_partition():
+    """Easy regime (as for the synchronous run): at least the planted
+    partition's objective, and the partition itself at lambda = 1/40."""
+    g = I.to_numpy(I.sbm([50] * 20, 0.3, 0.002, seed=9))
+    n = g["n"]
+    planted = g["planted"].astype(np.int32)
+    for q, exact in [(20, False), (40, True)]:
+        labels, num, den, _ = O.sequential_cc(g["off"], g["nbr"], None, 1, q, seed=1)
+        assert num >= O.objective_num(g["off"], g["nbr"], None, np.ones(n), 1, q, planted)
+        if exact:
+            assert len(set(int(x) for x in labels)) == 20
+            for b in range(20):
+                assert len(set(int(x) for x in labels[planted == b])) == 1

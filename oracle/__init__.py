@@ -35,10 +35,10 @@ def lib():
         _lib.orc_compress.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_free.argtypes = [P]
         _lib.orc_cluster.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
-                                     C.c_int, C.c_int, C.c_int, C.c_int, P, P,
-                                     P, P, P]
+                                     C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_int, C.c_uint64, P, P, P, P, P]
         _lib.orc_best_moves.argtypes = [I64, P, P, P, P, I64, I64, C.c_int,
-                                        C.c_int, P, P]
+                                        C.c_int, C.c_int, C.c_uint64, P, P]
         _lib.orc_sequential_cc.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
                                            C.c_uint64, C.c_int, C.c_int, P, P, P,
                                            P, P]
@@ -177,8 +177,9 @@ def compress(off, nbr, w, k, L):
 
 
 def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
-            max_levels=64, refine=True, vset=VSET_NBR_VERTICES):
-    """Parallel-CC (Algorithm 1, synchronous).
+            max_levels=64, refine=True, vset=VSET_NBR_VERTICES, coin=False, seed=0):
+    """Parallel-CC (Algorithm 1, synchronous; coin=True adds the seeded
+    symmetry-breaking coin of the library's LCC_SCHED_COIN schedule).
 
     Returns (labels, num, den, stats): the objective is CC = num / den exactly
     (den = q, or q * 2m in DEGREE mode); stats = (levels, rounds, edges)."""
@@ -192,6 +193,7 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
     st = np.zeros(3, np.int64)
     rc = lib().orc_cluster(n, _p(off), _p(nbr), _p(w), _p(kk), mode, p, q,
                            num_iter, max_levels, int(bool(refine)), vset,
+                           int(bool(coin)), seed & ((1 << 64) - 1),
                            _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
                            _p(st))
     if rc:
@@ -227,14 +229,16 @@ def sequential_cc(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, seed=0,
     return labels[:n], v, den.value, tuple(int(x) for x in st)
 
 
-def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES):
+def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES, coin=False,
+               seed=0):
     """Best-Moves on one level from labels L (modified copy returned)."""
     off, nbr, w = _graph(off, nbr, w)
     k = _c(k, np.int64)
     L = _c(L, np.int32).copy()
     rounds = C.c_int64()
     rc = lib().orc_best_moves(len(off) - 1, _p(off), _p(nbr), _p(w), _p(k), p,
-                              q, num_iter, vset, _p(L), C.byref(rounds))
+                              q, num_iter, vset, int(bool(coin)), seed & ((1 << 64) - 1),
+                              _p(L), C.byref(rounds))
     if rc < 0:
         raise ValueError("oracle best_moves failed: %d" % rc)
     return L, bool(rc), rounds.value

@@ -69,6 +69,38 @@ typedef struct {
   int64_t levels;
 } orc_stats;
 
+/* SplitMix64 (S. Vigna's public-domain generator after Steele, Lea and
+ * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014).
+ * The stream seeded with s has state s + i gamma after i steps; its i-th
+ * output (i >= 1) is splitmix64_mix(s + i gamma). */
+static const uint64_t SPLITMIX_GAMMA = 0x9e3779b97f4a7c15ull;
+
+static uint64_t splitmix64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+/* Symmetry-breaking coin of the synchronous schedule (an extension: the
+ * paper's synchronous rounds have none, and it notes their poor objectives
+ * for lack of symmetry breaking, Sec. 4).  In round t of a Best-Moves call
+ * (phase 0: the call that coarsens level `depth`; phase 1: its refinement
+ * after Flatten), a vertex v whose desired cluster differs from its own may
+ * move iff the top bit of output key + 1 of the stream seeded with `seed`
+ * is 1, key = v + t 2^32 + depth 2^48 + phase 2^56.  A vertex the coin holds
+ * back keeps its label and stays in the next V'. */
+typedef struct {
+  int on;
+  uint64_t seed;
+  int phase, depth;
+} coin_t;
+
+static int coin_allows(const coin_t *c, int round, int64_t v) {
+  const uint64_t key = (uint64_t)v + ((uint64_t)(round & 0xffff) << 32) +
+                       ((uint64_t)(c->depth & 0xff) << 48) + ((uint64_t)(c->phase & 1) << 56);
+  return (int)(splitmix64_mix(c->seed + (key + 1) * SPLITMIX_GAMMA) >> 63);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Objective, Sec. 2                                                       */
 /* ---------------------------------------------------------------------- */
@@ -221,21 +253,23 @@ int orc_desired_range(int64_t n, int64_t v0, int64_t v1, const int64_t *off_w,
 /* ---------------------------------------------------------------------- */
 
 /* Runs at most num_iter rounds on level g, starting from (L, K) with V' = V.
- * Returns 1 if any vertex moved in any round, else 0. */
+ * Returns 1 if any vertex moved in any round, else 0.  With the coin on,
+ * the rounds continue until no vertex wants to move (or num_iter). */
 static int best_moves(const level_t *g, int64_t p, int64_t q, int num_iter,
                       int vset, int32_t *L, int64_t *K, orc_stats *st,
-                      int *err) {
+                      int *err, const coin_t *coin) {
   const int64_t n = g->n;
   size_t m = (size_t)(n > 0 ? n : 1);
   uint8_t *in_vp = (uint8_t *)malloc(m);
   uint8_t *next_vp = (uint8_t *)malloc(m);
   uint8_t *moved = (uint8_t *)malloc(m);
   uint8_t *left = (uint8_t *)malloc(m);
+  uint8_t *held = (uint8_t *)malloc(m);
   int32_t *D = (int32_t *)malloc(m * sizeof(int32_t));
   scratch_t s;
   int rc = scratch_init(&s, n);
   int any = 0;
-  if (!in_vp || !next_vp || !moved || !left || !D || rc != ORC_OK) {
+  if (!in_vp || !next_vp || !moved || !left || !held || !D || rc != ORC_OK) {
     *err = ORC_ERR_OOM;
     goto done;
   }
@@ -252,13 +286,20 @@ static int best_moves(const level_t *g, int64_t p, int64_t q, int num_iter,
       }
     }
     st->rounds_total += 1;
-    int64_t nmoves = 0;
+    int64_t nwant = 0;
     for (int64_t v = 0; v < n; ++v) {
+      held[v] = 0;
+      if (D[v] != L[v]) {
+        ++nwant;
+        if (coin && coin->on && !coin_allows(coin, it, v)) {
+          D[v] = L[v];
+          held[v] = 1;
+        }
+      }
       moved[v] = (D[v] != L[v]);
-      nmoves += moved[v];
+      any |= moved[v];
     }
-    if (nmoves == 0) break;
-    any = 1;
+    if (nwant == 0) break;
     /* move every v to D[v] at once; K follows the moves */
     memset(left, 0, m);
     for (int64_t v = 0; v < n; ++v) {
@@ -283,10 +324,12 @@ static int best_moves(const level_t *g, int64_t p, int64_t q, int num_iter,
           for (int64_t e = g->off[x]; e < g->off[x + 1]; ++e)
             next_vp[g->nbr[e]] = 1;
     }
+    for (int64_t v = 0; v < n; ++v)
+      if (held[v]) next_vp[v] = 1;  /* held back by the coin: evaluated again */
     memcpy(in_vp, next_vp, m);
   }
 done:
-  free(in_vp); free(next_vp); free(moved); free(left); free(D);
+  free(in_vp); free(next_vp); free(moved); free(left); free(held); free(D);
   scratch_free(&s);
   return any;
 }
@@ -391,6 +434,8 @@ typedef struct {
   int num_iter, max_levels, refine, vset;
   orc_stats *st;
   int err;
+  int coin;
+  uint64_t seed;
 } run_t;
 
 /* Clusters level g (depth `depth`) and writes the labels to L. */
@@ -401,8 +446,9 @@ static void parallel_cc(const level_t *g, int depth, run_t *r, int32_t *L) {
   int64_t *K = (int64_t *)malloc(m * sizeof(int64_t));
   if (!K) { r->err = ORC_ERR_OOM; return; }
   for (int64_t v = 0; v < n; ++v) { L[v] = (int32_t)v; K[v] = g->k[v]; }
+  const coin_t coarsen = {r->coin, r->seed, 0, depth};
   int moved = best_moves(g, r->p, r->q, r->num_iter, r->vset, L, K, r->st,
-                         &r->err);
+                         &r->err, &coarsen);
   if (r->err || !moved || depth + 1 >= r->max_levels) { free(K); return; }
 
   int32_t *map = (int32_t *)malloc(m * sizeof(int32_t));
@@ -426,8 +472,9 @@ static void parallel_cc(const level_t *g, int depth, run_t *r, int32_t *L) {
         if (r->refine) {
           for (int64_t v = 0; v < n; ++v) K[v] = 0;
           for (int64_t v = 0; v < n; ++v) K[L[v]] += g->k[v];
+          const coin_t refine = {r->coin, r->seed, 1, depth};
           best_moves(g, r->p, r->q, r->num_iter, r->vset, L, K, r->st,
-                     &r->err);
+                     &r->err, &refine);
         }
       }
       free(L2);
@@ -493,8 +540,9 @@ static int finish_labels(int64_t n, const int64_t *off, const int32_t *nbr,
 int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
                 const int64_t *w, const int64_t *k_custom, int mode,
                 int64_t p, int64_t q, int num_iter, int max_levels, int refine,
-                int vset, int32_t *labels_out, int64_t *num_hi,
-                uint64_t *num_lo, int64_t *den_out, int64_t *stats_out) {
+                int vset, int coin, uint64_t seed, int32_t *labels_out,
+                int64_t *num_hi, uint64_t *num_lo, int64_t *den_out,
+                int64_t *stats_out) {
   if (n < 0 || p <= 0 || q <= 0 || num_iter < 0 || max_levels < 1)
     return ORC_ERR_INVALID;
   size_t m = (size_t)(n > 0 ? n : 1);
@@ -504,7 +552,7 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
   int rc = node_weights(n, off, w, k_custom, mode, q, k, &qe);
   if (rc != ORC_OK) { free(k); return rc; }
   orc_stats st = {0, 0, 0};
-  run_t r = {p, qe, num_iter, max_levels, refine, vset, &st, ORC_OK};
+  run_t r = {p, qe, num_iter, max_levels, refine, vset, &st, ORC_OK, coin, seed};
   level_t g = {n, off, nbr, w, k};
   int32_t *L = (int32_t *)malloc(m * sizeof(int32_t));
   if (!L) { free(k); return ORC_ERR_OOM; }
@@ -524,10 +572,12 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
 
 /* One synchronous Best-Moves call on a single level from given labels, for
  * round-by-round checks: runs at most num_iter rounds from (L, K = sum of k
- * per label) with V' = V and returns 1 if anything moved. */
+ * per label) with V' = V and returns 1 if anything moved.  With the coin on
+ * it draws the coin of phase 0 at depth 0. */
 int orc_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
                    const int64_t *w, const int64_t *k, int64_t p, int64_t q,
-                   int num_iter, int vset, int32_t *L, int64_t *rounds_out) {
+                   int num_iter, int vset, int coin, uint64_t seed, int32_t *L,
+                   int64_t *rounds_out) {
   size_t m = (size_t)(n > 0 ? n : 1);
   int64_t *K = (int64_t *)calloc(m, sizeof(int64_t));
   if (!K) return -ORC_ERR_OOM;
@@ -538,7 +588,8 @@ int orc_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
   orc_stats st = {0, 0, 0};
   int err = ORC_OK;
   level_t g = {n, off, nbr, w, k};
-  int any = best_moves(&g, p, q, num_iter, vset, L, K, &st, &err);
+  const coin_t c = {coin, seed, 0, 0};
+  int any = best_moves(&g, p, q, num_iter, vset, L, K, &st, &err, &c);
   free(K);
   if (rounds_out) *rounds_out = st.rounds_total;
   return err ? -err : any;
@@ -577,14 +628,10 @@ int64_t orc_sequential_sweep(int64_t n, const int64_t *off,
 /* in the appendix), the quality reference of the parallel method          */
 /* ---------------------------------------------------------------------- */
 
-/* SplitMix64 (S. Vigna's public-domain generator after Steele, Lea and
- * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
- * advances the state *x and returns the next output. */
+/* The next output of the SplitMix64 stream whose state is *x. */
 static uint64_t splitmix64(uint64_t *x) {
-  uint64_t z = (*x += 0x9e3779b97f4a7c15ull);
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
+  *x += SPLITMIX_GAMMA;
+  return splitmix64_mix(*x);
 }
 
 /* sigma = a random permutation of 0..n-1: Fisher-Yates, the swap partner of

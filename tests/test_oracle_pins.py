@@ -558,3 +558,120 @@ def test_sequential_cc_planted_partition():
             assert len(set(int(x) for x in labels)) == 20
             for b in range(20):
                 assert len(set(int(x) for x in labels[planted == b])) == 1
+
+
+# ------------------------------------------------- symmetry-breaking coin --
+
+GAMMA = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+
+def splitmix64_output(seed, i):
+    """Output i (i >= 1) of the SplitMix64 stream seeded with `seed`, from its
+    published definition (Vigna; Steele, Lea and Flood 2014)."""
+    z = (seed + i * GAMMA) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def coin(seed, phase, depth, t, v):
+    key = v + (t << 32) + (depth << 48) + (phase << 56)
+    return splitmix64_output(seed, key + 1) >> 63 == 1
+
+
+def test_coin_is_fair():
+    hits = sum(coin(7, 0, 0, t, v) for t in range(20) for v in range(10000))
+    assert abs(hits / 200000 - 0.5) < 0.005
+
+
+@pytest.mark.parametrize("vset", [O.VSET_ALL, O.VSET_NBR_VERTICES, O.VSET_NBR_CLUSTERS])
+def test_coin_rounds_by_brute_force(vset):
+    """With the coin, a round moves the vertices whose brute-force best move
+    differs from their label and whose coin allows it; the others keep their
+    label and are evaluated again next round, and the call ends when no
+    vertex wants to move."""
+    for gseed in range(3):
+        g = small_graph(60 + gseed, n=9, p=0.45, lo=-1, hi=4)
+        W, E = dense(g)
+        n = g["n"]
+        k = np.ones(n, np.int64)
+        p, q, seed = 1, 3, 1000 + gseed
+        off, nbr = g["off"], g["nbr"]
+        L = np.arange(n, dtype=np.int32)
+        vp = np.ones(n, bool)
+        sims, ended = [L.copy()], None
+        for t in range(8):
+            D = L.copy()
+            for v in range(n):
+                if vp[v]:
+                    D[v] = brute_desired(g, W, E, k, p, q, L, v)
+            want = D != L
+            if not want.any():
+                ended = t + 1
+                break
+            held = np.array([want[v] and not coin(seed, 0, 0, t, v) for v in range(n)])
+            D[held] = L[held]
+            moved = D != L
+            left = set(int(x) for x in L[moved])
+            L = D
+            nxt = np.zeros(n, bool)
+            if vset == O.VSET_ALL:
+                nxt[:] = True
+            elif vset == O.VSET_NBR_VERTICES:
+                for v in np.nonzero(moved)[0]:
+                    nxt[nbr[off[v]:off[v + 1]]] = True
+            else:
+                for x in range(n):
+                    if int(L[x]) in left:
+                        nxt[nbr[off[x]:off[x + 1]]] = True
+            vp = nxt | held
+            sims.append(L.copy())
+        for r in range(1, len(sims)):
+            Lr, _, rounds = O.best_moves(off, nbr, g["w"], k, p, q, np.arange(n, dtype=np.int32),
+                                         r, vset=vset, coin=True, seed=seed)
+            assert np.array_equal(Lr, sims[r]) and rounds == r, (gseed, r)
+        if ended is not None:
+            Lr, _, rounds = O.best_moves(off, nbr, g["w"], k, p, q, np.arange(n, dtype=np.int32),
+                                         50, vset=vset, coin=True, seed=seed)
+            assert rounds == ended and np.array_equal(Lr, sims[-1])
+
+
+def test_coin_level_ends_at_local_optimum():
+    """With V' = V every round, a coin run stops only when no vertex wants to
+    move, i.e. at a local optimum (the plain rounds may stop at the round cap
+    while swapping)."""
+    for gseed in range(4):
+        g = small_graph(70 + gseed, n=8, p=0.5, lo=-3, hi=5)
+        W, E = dense(g)
+        for p, q in [(1, 4), (1, 1)]:
+            labels, num, den, _ = O.cluster(g["off"], g["nbr"], g["w"], p, q, vset=O.VSET_ALL,
+                                            max_levels=1, num_iter=200, coin=True, seed=gseed)
+            assert improving_neighbour_move(g, W, E, np.ones(g["n"]), Fraction(p, q),
+                                            labels) is None
+
+
+def test_coin_merges_the_swapping_edge_and_recovers_cliques():
+    import torch
+    e = I.to_numpy(I.pairs_to_csr(torch.tensor([0]), torch.tensor([1]), 2))
+    for seed in range(5):
+        labels, num, den, _ = O.cluster(e["off"], e["nbr"], None, 1, 3, num_iter=20,
+                                        coin=True, seed=seed)
+        assert list(labels) == [0, 0] and (num, den) == (2 * (3 - 1), 3)
+    for r, s, p, q in [(5, 3, 1, 2), (3, 8, 2, 3)]:
+        g, members = cliques(r, s, r * 7 + s)
+        for seed in range(3):
+            labels, num, den, _ = O.cluster(g["off"], g["nbr"], None, p, q, num_iter=100,
+                                            coin=True, seed=seed)
+            for mem in members:
+                assert all(labels[v] == mem[0] for v in mem)
+            assert num == r * s * (s - 1) * (q - p)
+
+
+def test_coin_planted_partition():
+    g = I.to_numpy(I.sbm([50] * 20, 0.3, 0.002, seed=9))
+    n = g["n"]
+    planted = g["planted"].astype(np.int32)
+    for q in (20, 40):
+        _, num, _, _ = O.cluster(g["off"], g["nbr"], None, 1, q, num_iter=20, coin=True, seed=3)
+        assert num >= O.objective_num(g["off"], g["nbr"], None, np.ones(n), 1, q, planted)

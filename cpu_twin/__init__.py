@@ -27,9 +27,11 @@ def lib():
         build()
         _lib = C.CDLL(LIB)
         P, I64, I = C.c_void_p, C.c_int64, C.c_int
-        _lib.tw_cluster.argtypes = [I64, P, P, P, P, P, I, I64, I64, I, I, I, I, I,
+        U64 = C.c_uint64
+        _lib.tw_cluster.argtypes = [I64, P, P, P, P, P, I, I64, I64, I, I, I, I, I, U64, I,
                                     P, P, P, P, P, P]
-        _lib.tw_best_moves.argtypes = [I64, P, P, P, P, P, I64, I64, I, I, I, P, P, P]
+        _lib.tw_best_moves.argtypes = [I64, P, P, P, P, P, I64, I64, I, I, I, U64, I,
+                                       P, P, P]
         _lib.tw_compress.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P, P, P, P]
         _lib.tw_first_round.argtypes = [I64, P, P, P, P, I64, I64, I, P, P, P, P]
         _lib.tw_free.argtypes = [P]
@@ -59,8 +61,9 @@ def _check(rc, what):
 
 
 def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10, max_levels=64,
-            refine=True, vset=VSET_NBR_VERTICES, threads=0):
-    """Parallel-CC (Algorithm 1, synchronous) on `threads` cores (0 = all).
+            refine=True, vset=VSET_NBR_VERTICES, coin=False, seed=0, threads=0):
+    """Parallel-CC (Algorithm 1, synchronous; coin=True adds the seeded
+    symmetry-breaking coin) on `threads` cores (0 = all).
 
     Returns (labels, num, den, stats, threads_used) with CC = num / den
     exactly and stats = (levels, rounds, entries scanned)."""
@@ -71,7 +74,8 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10, max_levels=
     hi, lo, den, nt = C.c_int64(), C.c_uint64(), C.c_int64(), C.c_int()
     st = np.zeros(3, np.int64)
     rc = lib().tw_cluster(n, _p(off), _p(nbr), _p(w32), _p(w64), _p(kk), mode, p, q,
-                          num_iter, max_levels, int(bool(refine)), vset, threads,
+                          num_iter, max_levels, int(bool(refine)), vset, int(bool(coin)),
+                          seed & ((1 << 64) - 1), threads,
                           _p(labels), C.byref(hi), C.byref(lo), C.byref(den), _p(st),
                           C.byref(nt))
     _check(rc, "cluster")
@@ -81,14 +85,16 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10, max_levels=
     return labels[:n], v, den.value, tuple(int(x) for x in st), nt.value
 
 
-def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES, threads=0):
+def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES, coin=False, seed=0,
+               threads=0):
     """Best-Moves on one level from labels L; returns (labels, moved, rounds)."""
     off, nbr, w32, w64 = _graph(off, nbr, w)
     k = np.ascontiguousarray(k, dtype=np.int64)
     L = np.array(L, dtype=np.int32, copy=True)
     moved, rounds = C.c_int(), C.c_int64()
     rc = lib().tw_best_moves(len(off) - 1, _p(off), _p(nbr), _p(w32), _p(w64), _p(k), p, q,
-                             num_iter, vset, threads, _p(L), C.byref(moved), C.byref(rounds))
+                             num_iter, vset, int(bool(coin)), seed & ((1 << 64) - 1), threads,
+                             _p(L), C.byref(moved), C.byref(rounds))
     _check(rc, "best_moves")
     return L, bool(moved.value), rounds.value
 

@@ -125,6 +125,33 @@ static inline void table_add(tw_table *t, uint32_t mask, int64_t *nused,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Symmetry-breaking coin                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* With the coin on, a vertex whose best move differs from its cluster moves
+ * in round t of a Best-Moves call only if the top bit of output key + 1 of
+ * the SplitMix64 stream seeded with `seed` is 1 (Vigna's generator after
+ * Steele, Lea and Flood 2014: output i is the finaliser applied to
+ * seed + i * 0x9e3779b97f4a7c15), key = v + t 2^32 + depth 2^48 +
+ * phase 2^56, phase 1 for the refinement call after Flatten.  A vertex held
+ * back keeps its label and is evaluated again in the next round. */
+typedef struct {
+  int on;
+  uint64_t seed;
+  int phase, depth;
+} tw_coin;
+
+static inline int coin_allows(const tw_coin *c, int t, int64_t v) {
+  uint64_t z = c->seed + ((uint64_t)v + ((uint64_t)(t & 0xffff) << 32) +
+                          ((uint64_t)(c->depth & 0xff) << 48) +
+                          ((uint64_t)(c->phase & 1) << 56) + 1) * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return (int)(z >> 63);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Best move of one vertex (Appendix A gain)                                 */
 /* ------------------------------------------------------------------------ */
 
@@ -176,6 +203,8 @@ typedef struct {
   int64_t levels, rounds, scanned;
   tw_table *tabs; /* one per thread */
   int ntabs;
+  int coin;
+  uint64_t seed;
 } tw_run;
 
 static int run_tables(tw_run *r) {
@@ -268,15 +297,18 @@ static int check_bounds(const tw_level *g, int64_t p, int64_t q) {
 /* ------------------------------------------------------------------------ */
 
 /* At most num_iter rounds from (L, K) with V' = V.  *any = 1 if some vertex
- * moved in some round. */
+ * moved in some round.  With the coin on, rounds continue until no vertex
+ * wants to move (or num_iter); phase and depth key its draws. */
 static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
-                      int *any) {
+                      int *any, int phase, int depth) {
   const int64_t n = g->n;
   const size_t m = (size_t)(n > 0 ? n : 1);
   uint8_t *in = (uint8_t *)malloc(m), *nx = (uint8_t *)malloc(m);
   uint8_t *mv = (uint8_t *)malloc(m), *left = (uint8_t *)malloc(m);
+  uint8_t *held = (uint8_t *)malloc(m);
   int32_t *D = (int32_t *)malloc(m * sizeof(int32_t));
-  int err = (in && nx && mv && left && D) ? TW_OK : TW_ERR_OOM;
+  const tw_coin coin = {r->coin, r->seed, phase, depth};
+  int err = (in && nx && mv && left && held && D) ? TW_OK : TW_ERR_OOM;
   const int64_t p = r->p, q = r->q;
   *any = 0;
   if (!err) {
@@ -289,22 +321,31 @@ static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
   }
   if (!err) memset(in, 1, m);
   for (int it = 0; !err && it < r->num_iter; ++it) {
-    int64_t scanned = 0, nmoves = 0;
-#pragma omp parallel reduction(+ : scanned, nmoves)
+    int64_t scanned = 0, nwant = 0, nmoves = 0;
+#pragma omp parallel reduction(+ : scanned, nwant, nmoves)
     {
       tw_table *t = &r->tabs[omp_get_thread_num()];
 #pragma omp for schedule(dynamic, 64)
       for (int64_t v = 0; v < n; ++v) {
+        held[v] = 0;
         if (!in[v]) { D[v] = L[v]; continue; }
         D[v] = best_of(g, v, p, q, L, K, t);
         scanned += g->off[v + 1] - g->off[v];
-        nmoves += D[v] != L[v];
+        if (D[v] != L[v]) {
+          nwant += 1;
+          if (coin.on && !coin_allows(&coin, it, v)) {
+            D[v] = L[v];
+            held[v] = 1;
+          } else {
+            nmoves += 1;
+          }
+        }
       }
     }
     r->rounds += 1;
     r->scanned += scanned;
-    if (nmoves == 0) break;
-    *any = 1;
+    if (nwant == 0) break;
+    if (nmoves) *any = 1;
     /* every move at once; K follows by exact atomic sums */
     memset(left, 0, m);
 #pragma omp parallel for schedule(static)
@@ -331,9 +372,14 @@ static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
           __atomic_store_n(&nx[g->nbr[e]], 1, RELAXED);
       }
     }
+    if (coin.on) {
+#pragma omp parallel for schedule(static)
+      for (int64_t v = 0; v < n; ++v)
+        if (held[v]) nx[v] = 1;  /* held back: evaluated again */
+    }
     uint8_t *sw = in; in = nx; nx = sw;
   }
-  free(in); free(nx); free(mv); free(left); free(D);
+  free(in); free(nx); free(mv); free(left); free(held); free(D);
   return err;
 }
 
@@ -497,7 +543,7 @@ static int run_level(const tw_level *g, int depth, tw_run *r, int32_t *L) {
 #pragma omp parallel for schedule(static)
   for (int64_t v = 0; v < n; ++v) { L[v] = (int32_t)v; K[v] = g->k[v]; }
   int any = 0;
-  int err = best_moves(g, r, L, K, &any);
+  int err = best_moves(g, r, L, K, &any, 0, depth);
   if (err || !any || depth + 1 >= r->max_levels) { free(K); return err; }
 
   int32_t *map = (int32_t *)malloc(m * sizeof(int32_t));
@@ -515,7 +561,7 @@ static int run_level(const tw_level *g, int depth, tw_run *r, int32_t *L) {
         memset(K, 0, m * sizeof(int64_t));
 #pragma omp parallel for schedule(static)
         for (int64_t v = 0; v < n; ++v) __atomic_fetch_add(&K[L[v]], g->k[v], RELAXED);
-        err = best_moves(g, r, L, K, &any);
+        err = best_moves(g, r, L, K, &any, 1, depth);
       }
     }
     free(L2);
@@ -575,7 +621,8 @@ static int set_threads(int threads) {
 int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
                const int32_t *w32, const int64_t *w64, const int64_t *k_custom,
                int mode, int64_t p, int64_t q, int num_iter, int max_levels,
-               int refine, int vset, int threads, int32_t *labels_out,
+               int refine, int vset, int coin, uint64_t seed, int threads,
+               int32_t *labels_out,
                int64_t *num_hi, uint64_t *num_lo, int64_t *den_out,
                int64_t *stats_out, int *threads_used) {
   if (n < 0 || n >= ((int64_t)1 << 31) || p <= 0 || q <= 0 || num_iter < 0 ||
@@ -613,7 +660,7 @@ int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
     err = TW_ERR_INVALID;
   }
   if (!err) err = check_bounds(&g, p, qe);
-  tw_run r = {p, qe, num_iter, max_levels, refine, vset, 0, 0, 0, NULL, 0};
+  tw_run r = {p, qe, num_iter, max_levels, refine, vset, 0, 0, 0, NULL, 0, coin, seed};
   if (!err) err = run_tables(&r);
   if (!err) err = run_level(&g, 0, &r, L);
   run_free(&r);
@@ -644,12 +691,14 @@ int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
 }
 
 /* Best-Moves on one level from the labels L (updated in place), with
- * K = sum of k per label; node weights k given.  *moved = 1 if a vertex
- * moved, *rounds = rounds evaluated. */
+ * K = sum of k per label; node weights k given; the coin, if on, draws as
+ * the coarsening call at depth 0.  *moved = 1 if a vertex moved, *rounds =
+ * rounds evaluated. */
 int tw_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
                   const int32_t *w32, const int64_t *w64, const int64_t *k,
-                  int64_t p, int64_t q, int num_iter, int vset, int threads,
-                  int32_t *L, int *moved, int64_t *rounds) {
+                  int64_t p, int64_t q, int num_iter, int vset, int coin,
+                  uint64_t seed, int threads, int32_t *L, int *moved,
+                  int64_t *rounds) {
   if (n < 0 || n >= ((int64_t)1 << 31) || p < 0 || q <= 0 || num_iter < 0)
     return TW_ERR_INVALID;
   set_threads(threads);
@@ -661,9 +710,9 @@ int tw_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
   int64_t *K = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   if (!K) return TW_ERR_OOM;
   for (int64_t v = 0; v < n; ++v) K[L[v]] += k[v];
-  tw_run r = {p, q, num_iter, 1, 0, vset, 0, 0, 0, NULL, 0};
+  tw_run r = {p, q, num_iter, 1, 0, vset, 0, 0, 0, NULL, 0, coin, seed};
   err = run_tables(&r);
-  if (!err) err = best_moves(&g, &r, L, K, moved);
+  if (!err) err = best_moves(&g, &r, L, K, moved, 0, 0);
   *rounds = r.rounds;
   run_free(&r);
   free(K);
@@ -683,7 +732,7 @@ int tw_compress(int64_t n, const int64_t *off, const int32_t *nbr,
     if (L[v] < 0 || L[v] >= n) return TW_ERR_INVALID;
   tw_level g = {n, off, nbr, w32, w64, k}, g2;
   tw_coarse cg;
-  tw_run r = {1, 1, 0, 1, 0, 0, 0, 0, 0, NULL, 0};
+  tw_run r = {1, 1, 0, 1, 0, 0, 0, 0, 0, NULL, 0, 0, 0};
   int err = run_tables(&r);
   if (!err) err = compress(&g, L, &r, map, &g2, &cg);
   run_free(&r);
@@ -713,7 +762,7 @@ int tw_first_round(int64_t n, const int64_t *off, const int32_t *nbr,
   int32_t *L = (int32_t *)malloc(m * sizeof(int32_t));
   int64_t *K = (int64_t *)malloc(m * sizeof(int64_t));
   int64_t *kd = k ? NULL : (int64_t *)malloc(m * sizeof(int64_t));
-  tw_run r = {p, q, 1, 1, 0, TW_VSET_ALL, 0, 0, 0, NULL, 0};
+  tw_run r = {p, q, 1, 1, 0, TW_VSET_ALL, 0, 0, 0, NULL, 0, 0, 0};
   int err = (L && K && (k || kd)) ? run_tables(&r) : TW_ERR_OOM;
   tw_level g = {n, off, nbr, w32, NULL, k ? k : kd};
   if (!err && !k) {

@@ -159,3 +159,42 @@ def test_twin_edge_cases():
     h = GRAPHS["signed"]
     with pytest.raises(ValueError, match="status 1"):
         T.cluster(h["off"], h["nbr"], h["w"], 1, 1, mode=T.NODEW_DEGREE)
+
+
+COIN_CASES = [
+    ("sbm", O.NODEW_UNIT, 1, 50, {"num_iter": 20}),
+    ("hubs_w", O.NODEW_CUSTOM, 2, 9, {"vset": O.VSET_NBR_CLUSTERS}),
+    ("cl", O.NODEW_DEGREE, 1, 1, {}),
+    ("rmat", O.NODEW_DEGREE, 1, 1, {}),
+    ("signed", O.NODEW_UNIT, 1, 10, {"vset": O.VSET_ALL, "num_iter": 30}),
+]
+
+
+@pytest.mark.parametrize("threads", [1, 6])
+@pytest.mark.parametrize("case", COIN_CASES, ids=lambda c: "%s-%d-%d/%d" % c[:4])
+def test_twin_coin_schedule_matches_oracle(case, threads):
+    """The symmetry-breaking coin: same held-back vertices, rounds and labels
+    as the oracle for every seed and thread count."""
+    name, mode, p, q, kw = case
+    g = GRAPHS[name]
+    k = custom_k(g, 9) if mode == O.NODEW_CUSTOM else None
+    sched = dict(num_iter=kw.get("num_iter", 10), vset=kw.get("vset", O.VSET_NBR_VERTICES))
+    for seed in (0, 12345, (1 << 64) - 3):
+        wl, num, den, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k,
+                                      coin=True, seed=seed, **sched)
+        lab, tnum, tden, tst, _ = T.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k,
+                                            coin=True, seed=seed, threads=threads, **sched)
+        assert np.array_equal(lab, wl) and (tnum, tden) == (num, den) and tst == wst
+
+
+@pytest.mark.parametrize("vset", [O.VSET_ALL, O.VSET_NBR_VERTICES, O.VSET_NBR_CLUSTERS])
+def test_twin_coin_best_moves_matches_oracle(vset):
+    g = GRAPHS["hubs_w"]
+    rng = np.random.default_rng(4)
+    L0 = rng.integers(0, g["n"] // 5, g["n"]).astype(np.int32)
+    k = custom_k(g, 6)
+    for it in (1, 3, 40):
+        want = O.best_moves(g["off"], g["nbr"], g["w"], k, 1, 3, L0, it, vset, coin=True, seed=9)
+        got = T.best_moves(g["off"], g["nbr"], g["w"], k, 1, 3, L0, it, vset, coin=True, seed=9,
+                           threads=4)
+        assert np.array_equal(got[0], want[0]) and got[1:] == want[1:]

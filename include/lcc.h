@@ -97,6 +97,19 @@ typedef enum lcc_memspace { LCC_MEM_HOST = 0, LCC_MEM_DEVICE = 1 } lcc_memspace;
    an edge and keeping the label of each one none of whose neighbours moved.
    This flag always takes the first way. */
 #define LCC_SCHED_MARK_ONLY 2
+/* Symmetry-breaking coin.  The synchronous rounds have none, and the paper
+   notes that they often end at very poor, even negative, objectives (Sec. 4).
+   With this flag, a vertex whose best move differs from its cluster moves in
+   round t of a Best-Moves call only if a coin allows it: the top bit of
+   output key + 1 of the SplitMix64 stream seeded with `seed` (output i is the
+   SplitMix64 finaliser of seed + i * 0x9e3779b97f4a7c15), with
+   key = v + (t mod 2^16) 2^32 + (depth mod 2^8) 2^48 + phase 2^56, phase 1
+   for the refinement call after Flatten, else 0.  A vertex held back keeps
+   its label and is evaluated again in the next round; a call ends when no
+   vertex wants to move (or after num_iter rounds).  Results stay
+   deterministic for a given seed.  This schedule always marks V' (no pull
+   rounds). */
+#define LCC_SCHED_COIN 4
 
 typedef struct lcc_schedule {
   int32_t num_iter;   /* max rounds per Best-Moves call (Algorithm 1); >= 0 */
@@ -105,6 +118,7 @@ typedef struct lcc_schedule {
   int32_t vset;       /* lcc_vset */
   int32_t sync;       /* must be 1: the synchronous schedule (Sec. 3.2.1) */
   int32_t flags;      /* LCC_SCHED_* */
+  uint64_t seed;      /* seed of the LCC_SCHED_COIN coin (ignored without it) */
 } lcc_schedule;
 
 typedef struct lcc_stats {

@@ -56,6 +56,7 @@ static lcc_schedule default_schedule() {
   s.vset = LCC_VSET_NBR_VERTICES;
   s.sync = 1;
   s.flags = 0;
+  s.seed = 0;
   return s;
 }
 

@@ -428,9 +428,10 @@ void Engine::end_bm(Job *j) {
 void Engine::round(std::vector<Job *> &js) {
   const int nj = (int)js.size();
   std::vector<JobDev> tab(nj);
+  std::vector<CoinJob> coins(nj);
   std::vector<int64_t> vs(nj + 1);
   int64_t vt = 0, caps[NB] = {0}, hubcap = 0, hubs = 0, hub_su = 0, hub_max = 0;
-  bool wide = false, any_cl = false, any_mark = false, any_apply = false;
+  bool wide = false, any_cl = false, any_mark = false, any_apply = false, any_coin = false;
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
     Level &L = J->lv[J->depth];
@@ -453,6 +454,16 @@ void Engine::round(std::vector<Job *> &js) {
     x.wtype = L.wtype;
     x.pull_min = INT64_MAX;
     x.warp_max = L.warp_max;
+    // symmetry-breaking coin of this round (LCC_SCHED_COIN): draws keyed by
+    // vertex, round, depth and phase (1 = refinement after Flatten)
+    const bool coin = (J->sc.flags & LCC_SCHED_COIN) && !J->eval_only;
+    CoinJob &cj = coins[i];
+    cj.seed = J->sc.seed;
+    cj.key_hi = ((uint64_t)(J->round & 0xffff) << 32) + ((uint64_t)(J->depth & 0xff) << 48) +
+                ((uint64_t)(J->kind == BM_REFINE ? 1 : 0) << 56);
+    cj.on = coin ? 1 : 0;
+    cj.pad = 0;
+    any_coin |= coin;
     int32_t f = 0;
     if (J->eval_only) {
       f |= JF_EVAL_ONLY;
@@ -464,7 +475,8 @@ void Engine::round(std::vector<Job *> &js) {
         // neighbourhoods are most of the graph: the next round evaluates every
         // vertex with an edge and keeps the labels of those with no moved
         // neighbour, instead of marking V' entry by entry.
-        if (L.lk && !(J->sc.flags & LCC_SCHED_MARK_ONLY))
+        // (a vertex the coin holds back is marked, so coin rounds always mark)
+        if (L.lk && !(J->sc.flags & LCC_SCHED_MARK_ONLY) && !coin)
           x.pull_min = std::max<int64_t>(1, L.info.nnz / 4);
         if (J->round > 0 && J->pull) f |= JF_PULL;
       }
@@ -522,7 +534,18 @@ void Engine::round(std::vector<Job *> &js) {
   }
   JobDev *dt = s_jobs_.get<JobDev>(nj, st_);
   int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
-  upload_table(tab, vs, dt, dv, stage(nj * (sizeof(JobDev) + 8) + 8), st_);
+  const size_t tab_bytes = nj * (sizeof(JobDev) + 8) + 8;
+  char *hs = (char *)stage(tab_bytes + (any_coin ? nj * sizeof(CoinJob) : 0));
+  upload_table(tab, vs, dt, dv, hs, st_);
+  CoinJob *dcoin = nullptr;
+  int64_t *dheld = nullptr;
+  if (any_coin) {
+    dcoin = s_coin_.get<CoinJob>(nj, st_);
+    dheld = s_jheld_.get<int64_t>(nj, st_);
+    memcpy(hs + tab_bytes, coins.data(), nj * sizeof(CoinJob));
+    CK(cudaMemcpyAsync(dcoin, hs + tab_bytes, nj * sizeof(CoinJob), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemsetAsync(dheld, 0, nj * sizeof(int64_t), st_));
+  }
   CK(cudaMemsetAsync(b.cnt, 0, NB * sizeof(int64_t), st_));
   CK(cudaMemsetAsync(ctr, 0, NCTR * sizeof(int64_t), st_));
   CK(cudaMemsetAsync(jm, 0, 2 * nj * sizeof(int64_t), st_));
@@ -534,6 +557,10 @@ void Engine::round(std::vector<Job *> &js) {
   if (timing) CK(cudaEventRecord(ev_[1], st_));
   launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
+  if (any_coin) {
+    launch_coin(dt, dcoin, b, dheld, st_, d_);
+    ++launches;
+  }
   if (any_apply) {
     launch_apply(dt, b, jm, moved, vt, ctr, st_, d_);
     ++launches;
@@ -542,9 +569,12 @@ void Engine::round(std::vector<Job *> &js) {
   if (timing) CK(cudaEventRecord(ev_[3], st_));
   note_launches(launches);
 
-  int64_t *hbuf = (int64_t *)stage2((NCTR + 2 * nj) * sizeof(int64_t));
+  int64_t *hbuf = (int64_t *)stage2((NCTR + 3 * nj) * sizeof(int64_t));
   CK(cudaMemcpyAsync(hbuf, ctr, NCTR * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
   CK(cudaMemcpyAsync(hbuf + NCTR, jm, 2 * nj * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
+  if (any_coin)
+    CK(cudaMemcpyAsync(hbuf + NCTR + 2 * nj, dheld, nj * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       st_));
   sync_checked(st_);
   if (hbuf[C_ERR])
     throw Error(LCC_ERR_CUDA, "best-move round overflowed a work buffer (code " +
@@ -567,6 +597,7 @@ void Engine::round(std::vector<Job *> &js) {
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
     const int64_t mv = hbuf[NCTR + 2 * i];
+    const int64_t held = any_coin ? hbuf[NCTR + 2 * nj + i] : 0;
     // the mark kernel skipped this job under the same test
     J->pull = hbuf[NCTR + 2 * i + 1] >= tab[i].pull_min;
     J->round += 1;
@@ -579,7 +610,9 @@ void Engine::round(std::vector<Job *> &js) {
       J->moved_level = true;
       J->moved_any = true;
     }
-    if (mv == 0 || J->round >= J->sc.num_iter) end_bm(J);
+    // the call ends when no vertex wants to move: none moved and the coin
+    // held none back
+    if ((mv == 0 && held == 0) || J->round >= J->sc.num_iter) end_bm(J);
   }
 }
 

@@ -523,4 +523,63 @@ void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t 
   k_validate_rows<<<grid_for(n * 32, 256, d), 256, 0, st>>>(off, nbr, w, n, out8);
 }
 
+// ------------------------------------------------------ symmetry breaking --
+
+// SplitMix64 (Vigna's generator after Steele, Lea and Flood 2014): output
+// i >= 1 of the stream seeded with `seed` is the finaliser applied to
+// seed + i * 0x9e3779b97f4a7c15.  The coin of key allows a move when the top
+// bit of output key + 1 is 1.
+__device__ __forceinline__ bool coin_allows(uint64_t seed, uint64_t key) {
+  uint64_t z = seed + (key + 1) * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return (z >> 63) != 0;
+}
+
+// Runs between the best-move kernels and k_apply over the same bucket items
+// (the round's V').  Whole warps step together so the per-job counts of
+// held-back vertices combine before their atomic.
+__global__ void __launch_bounds__(256) k_coin(const JobDev *__restrict__ jobs,
+                                              const CoinJob *__restrict__ coins, Buckets b,
+                                              int64_t *held) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int bk = 0; bk < NB; ++bk) {
+    int64_t count = b.cnt[bk];
+    if (count > b.seg_cap[bk]) count = b.seg_cap[bk];
+    const uint64_t *items = b.items + b.seg_start[bk];
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+      const int64_t i = base + threadIdx.x;
+      int hj = -1;
+      if (i < count) {
+        const uint64_t item = items[i];
+        const int j = (int)(item >> 32);
+        const CoinJob c = coins[j];
+        if (c.on) {
+          const JobDev *J = jobs + j;
+          const int32_t v = (int32_t)(uint32_t)item;
+          const int32_t lv = J->L[v];
+          if (J->D[v] != lv && !coin_allows(c.seed, c.key_hi + (uint32_t)v)) {
+            J->D[v] = lv;     // keeps its cluster this round
+            J->fr[v] |= 1;    // and is evaluated again in the next
+            hj = j;
+          }
+        }
+      }
+      const unsigned peers = __match_any_sync(FULL, hj);
+      if (hj >= 0 && lane == __ffs(peers) - 1)
+        atomicAdd((unsigned long long *)(held + hj), (unsigned long long)__popc(peers));
+    }
+  }
+}
+
+void launch_coin(const JobDev *jobs, const CoinJob *coins, const Buckets &b, int64_t *held,
+                 cudaStream_t st, const Dev &d) {
+  int64_t tot = 0;
+  for (int i = 0; i < NB; ++i) tot += b.seg_cap[i];
+  if (tot == 0) return;
+  k_coin<<<grid_for(tot, 256, d), 256, 0, st>>>(jobs, coins, b, held);
+}
+
 }  // namespace lcc

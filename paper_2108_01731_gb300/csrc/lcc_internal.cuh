@@ -347,6 +347,20 @@ void launch_objective(const LJob *jobs, const int64_t *vstart, int njobs, int64_
                       ObjAcc *acc, cudaStream_t st, const Dev &d);
 void launch_validate(const int64_t *off, int64_t n, int64_t nnz, unsigned long long *out8,
                      cudaStream_t st, const Dev &d);
+
+// Symmetry-breaking coin of one job in one round (LCC_SCHED_COIN): the
+// draws of vertex v use key = key_hi + v.
+struct CoinJob {
+  uint64_t seed;
+  uint64_t key_hi;  // round 2^32 + depth 2^48 + phase 2^56
+  int32_t on;
+  int32_t pad;
+};
+// After the best-move kernels: every evaluated vertex of a coin job whose
+// desired cluster differs from its own and whose coin forbids the move keeps
+// its label (D[v] = L[v]) and is marked into the next V'; held[j] counts them.
+void launch_coin(const JobDev *jobs, const CoinJob *coins, const Buckets &b, int64_t *held,
+                 cudaStream_t st, const Dev &d);
 void launch_validate_rows(const int64_t *off, const int32_t *nbr, const int32_t *w, int64_t n,
                           unsigned long long *out8, cudaStream_t st, const Dev &d);
 

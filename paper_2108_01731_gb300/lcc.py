@@ -29,12 +29,13 @@ LCC_VSET_ALL, LCC_VSET_NBR_VERTICES, LCC_VSET_NBR_CLUSTERS = 0, 1, 2
 LCC_MEM_HOST, LCC_MEM_DEVICE = 0, 1
 LCC_SCHED_TIMING = 1
 LCC_SCHED_MARK_ONLY = 2
+LCC_SCHED_COIN = 4
 
 
 class lcc_schedule(C.Structure):
     _fields_ = [("num_iter", C.c_int32), ("max_levels", C.c_int32),
                 ("refine", C.c_int32), ("vset", C.c_int32), ("sync", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("seed", C.c_uint64)]
 
 
 class lcc_tuning(C.Structure):
@@ -153,9 +154,11 @@ def _ptr(a, dtype):
 
 
 def schedule(num_iter=10, max_levels=64, refine=True, vset=LCC_VSET_NBR_VERTICES,
-             timing=False, mark_only=False):
-    flags = (LCC_SCHED_TIMING if timing else 0) | (LCC_SCHED_MARK_ONLY if mark_only else 0)
-    return lcc_schedule(int(num_iter), int(max_levels), int(bool(refine)), int(vset), 1, flags)
+             timing=False, mark_only=False, coin=False, seed=0):
+    flags = ((LCC_SCHED_TIMING if timing else 0) | (LCC_SCHED_MARK_ONLY if mark_only else 0)
+             | (LCC_SCHED_COIN if coin else 0))
+    return lcc_schedule(int(num_iter), int(max_levels), int(bool(refine)), int(vset), 1, flags,
+                        int(seed) & ((1 << 64) - 1))
 
 
 class Graph:

@@ -36,8 +36,27 @@ def test_binding_covers_header():
     assert lib.lcc_status_str(lcc.LCC_ERR_NOT_SYMMETRIC).decode() == "graph not symmetric"
 
 
-def test_struct_layouts_match_header_sizes():
+def test_struct_layouts_match_header_sizes(tmp_path):
+    """The ctypes structs against the C compiler's view of include/lcc.h:
+    the size of every struct and the offset of every field."""
+    import subprocess
     from paper_2108_01731_gb300 import lcc
-    assert ctypes.sizeof(lcc.lcc_schedule) == 24
-    assert ctypes.sizeof(lcc.lcc_stats) == 4 * 2 + 8 * 7 + 8 * 6 + 8 * 3 + 8 * 16 * 3
-    assert ctypes.sizeof(lcc.lcc_job) == 8 * 7 + 8
+    structs = [lcc.lcc_schedule, lcc.lcc_stats, lcc.lcc_tuning, lcc.lcc_server_cfg, lcc.lcc_job]
+    lines = []
+    for st in structs:
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (st.__name__, st.__name__))
+        for f in st._fields_:
+            lines.append('printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));'
+                         % (st.__name__, f[0], st.__name__, f[0]))
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"lcc.h\"\n"
+                   "int main(void) {\n%s\nreturn 0;\n}\n" % "\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    want = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st in structs:
+        assert int(want[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for f in st._fields_:
+            assert int(want["%s.%s" % (st.__name__, f[0])]) == getattr(st, f[0]).offset, f[0]
+    assert ctypes.sizeof(lcc.lcc_schedule) == 32 and lcc.lcc_schedule.seed.offset == 24

@@ -275,6 +275,59 @@ def check_cluster_case(L, case):
     G.free()
 
 
+COIN_CASES = [
+    ("sbm", O.NODEW_UNIT, 1, 50, {"num_iter": 20}),
+    ("hubs", O.NODEW_DEGREE, 1, 1, {}),
+    ("hubs_w", O.NODEW_CUSTOM, 2, 9, {"vset": O.VSET_NBR_CLUSTERS}),
+    ("cl", O.NODEW_DEGREE, 1, 1, {}),
+    ("rmat", O.NODEW_DEGREE, 1, 1, {}),
+    ("signed", O.NODEW_UNIT, 1, 10, {"vset": O.VSET_ALL, "num_iter": 30}),
+    ("giant", O.NODEW_DEGREE, 1, 1, {}),
+]
+
+
+@pytest.mark.parametrize("case", COIN_CASES, ids=lambda c: "%s-%d-%d/%d" % c[:4])
+def test_coin_schedule_matches_oracle(L, case):
+    """LCC_SCHED_COIN: the same held-back vertices in every round as the
+    oracle (labels, objective, levels, rounds and scanned entries), for
+    several seeds, through every degree bucket and V' rule."""
+    name, mode, p, q, kw = case
+    g = GRAPHS[name]
+    k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+    ni, vset = kw.get("num_iter", 10), kw.get("vset", O.VSET_NBR_VERTICES)
+    for seed in (0, 977, (1 << 64) - 5):
+        sched = L.schedule(num_iter=ni, vset=vset, coin=True, seed=seed)
+        labels, obj, st = L.lcc_cluster(G, p, q, mode, sched)
+        wl, num, den, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k,
+                                      num_iter=ni, vset=vset, coin=True, seed=seed)
+        assert np.array_equal(labels, wl), (name, seed)
+        assert st["obj_num"] == num and st["obj_den"] == den
+        assert (st["levels"], st["rounds_total"], st["edges_scanned"]) == wst
+    G.free()
+
+
+def test_coin_batch_equals_single(L):
+    """Jobs of one batch draw their own coins (keys by vertex, round, depth
+    and phase of each job): the batch gives every graph its single-run result."""
+    names = ["sbm", "hubs", "cl", "rmat"]
+    modes = [O.NODEW_UNIT, O.NODEW_DEGREE, O.NODEW_DEGREE, O.NODEW_DEGREE]
+    ps, qs = [1, 1, 1, 1], [50, 1, 1, 1]
+    sched = L.schedule(num_iter=15, coin=True, seed=31)
+    Gs = [L.lcc_load_csr(GRAPHS[n]["off"], GRAPHS[n]["nbr"], GRAPHS[n]["w"]) for n in names]
+    outs, objs = L.lcc_cluster_batch(Gs, ps, qs, modes, sched)
+    for i, G in enumerate(Gs):
+        lab, obj, _ = L.lcc_cluster(G, ps[i], qs[i], modes[i], sched)
+        assert np.array_equal(outs[i], lab), names[i]
+        assert objs[i] == obj
+        g = GRAPHS[names[i]]
+        wl = O.cluster(g["off"], g["nbr"], g["w"], ps[i], qs[i], mode=modes[i], num_iter=15,
+                       coin=True, seed=31)[0]
+        assert np.array_equal(lab, wl), names[i]
+    for G in Gs:
+        G.free()
+
+
 def test_pull_and_mark_frontiers_agree(L):
     """V' = neighbours of the movers (Sec. 3.2.2), found by marking them or by
     evaluating every vertex with an edge and keeping the labels of those with

@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-twin", action="store_true",
                     help="skip the OpenMP CPU twin's timed first round")
+    ap.add_argument("--no-coin", action="store_true",
+                    help="skip the extra step with the symmetry-breaking coin")
     ap.add_argument("--tuning-cache", default=None,
                     help="tuning file for lcc_autotune: reuse this GPU's line if present, "
                          "else measure and append (keeps the routing fixed across runs)")
@@ -256,6 +258,33 @@ def oracle_sample(host, wl, seconds):
     return (done_edges / done_t / 1e9, "first best-move round of the same graph, vertices "
             "[0, %d) (%d of %d vertices, %d entries scanned), single-threaded oracle"
             % (v0, v0, n, done_edges), done_t)
+
+
+# --------------------------------------------------- symmetry-breaking coin --
+
+def modularity(st, q):
+    """Q = CC / 2m of a modularity-mode run (obj_den = q 2m)."""
+    return st["obj_num"] / st["obj_den"] / (st["obj_den"] / q)
+
+
+def coin_leg(run, wl):
+    """One whole step with the symmetry-breaking coin (LCC_SCHED_COIN, seed 0)
+    on the resident graph, beside the plain synchronous steps: its device
+    time, scanned entries, objective and clusters.  run() -> (ms, stats).
+    Any failure is reported, not raised: this leg runs after every number of
+    the line has been taken."""
+    try:
+        ms, st = run()
+    except Exception as e:  # noqa: BLE001
+        return {"unavailable": "%s: %s" % (type(e).__name__, e)}
+    out = {"schedule": "LCC_SCHED_COIN, seed 0", "ms_per_step": round(ms, 3),
+           "edges_scanned": int(st["edges_scanned"]),
+           "gedges_per_s": round(st["edges_scanned"] / (ms / 1e3) / 1e9, 4),
+           "levels": int(st["levels"]), "rounds": int(st["rounds_total"]),
+           "num_clusters": int(st["num_clusters"]), "objective": st["objective"]}
+    if wl["mode"] == 1:
+        out["modularity"] = modularity(st, wl["q"])
+    return out
 
 
 # ------------------------------------------------------- CPU OpenMP twin --
@@ -577,9 +606,24 @@ def run_ours(args, rank, world, local):
         line["cpu_parallel"] = twin
     if serving is not None:
         line["serving"] = serving
-    G.free()
+    if wl["mode"] == 1:
+        line["config"]["modularity"] = modularity(stats[-1], wl["q"])
+    if rank == 0 and not args.no_coin:
+        def run_coin():
+            sc = L.schedule(num_iter=wl["num_iter"], coin=True, seed=0)
+            torch.cuda.synchronize()
+            e0.record()
+            st = L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sc, labels_out=labels)[2]
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), st
+        line["coin_schedule"] = coin_leg(run_coin, wl)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    try:
+        G.free()
+    except Exception:  # noqa: BLE001  (the line is out; a failed release ends the run anyway)
+        pass
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -72,3 +72,17 @@ def test_twin_leg_reports_rate_and_agreement():
     assert "%d entries" % g["nnz"] in out["sample"]
     out = bench.twin_round(host, wl, lambda lab: oracle_desired(lab)[::-1].copy())
     assert out["desired_equal_gpu"] is False
+
+
+def test_coin_leg_reports_or_degrades():
+    wl = dict(bench.WORKLOADS["rmat22"])
+    st = {"edges_scanned": 2_000_000_000, "levels": 5, "rounds_total": 60, "num_clusters": 10,
+          "objective": 1000.0, "obj_num": 1000 * 8, "obj_den": 8}
+    out = bench.coin_leg(lambda: (500.0, st), wl)
+    assert out["gedges_per_s"] == 4.0 and out["rounds"] == 60
+    assert out["modularity"] == 1000.0 / 8  # CC / 2m with obj_den = q 2m, q = 1
+
+    def boom():
+        raise RuntimeError("CUDA error (status 7)")
+    out = bench.coin_leg(boom, wl)
+    assert "unavailable" in out and "status 7" in out["unavailable"]

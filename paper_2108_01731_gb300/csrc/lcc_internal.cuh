@@ -256,8 +256,6 @@ __device__ __forceinline__ int find_job(const int64_t *__restrict__ vstart, int 
   return lo;
 }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t c) { return c * 2654435769u; }
-
 __device__ __forceinline__ void atomic_add_i64(int64_t *a, int64_t v) {
   atomicAdd((unsigned long long *)a, (unsigned long long)v);
 }

@@ -155,6 +155,10 @@ def _ptr(a, dtype):
 
 def schedule(num_iter=10, max_levels=64, refine=True, vset=LCC_VSET_NBR_VERTICES,
              timing=False, mark_only=False, coin=False, seed=0):
+    """An lcc_schedule: rounds per Best-Moves call, level cap, refinement, the
+    V' rule, per-phase timing, V' by marking only, and the seeded
+    symmetry-breaking coin (LCC_SCHED_COIN; results are deterministic for a
+    seed)."""
     flags = ((LCC_SCHED_TIMING if timing else 0) | (LCC_SCHED_MARK_ONLY if mark_only else 0)
              | (LCC_SCHED_COIN if coin else 0))
     return lcc_schedule(int(num_iter), int(max_levels), int(bool(refine)), int(vset), 1, flags,

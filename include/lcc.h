@@ -150,6 +150,11 @@ typedef struct lcc_stats {
                                   round that marks no V', every row with an
                                   edge is processed) */
   int64_t bucket_vertices[16]; /* vertices processed per degree bucket */
+  int64_t bytes_contract_min;  /* least bytes the contractions must move: each
+                                  contracted level's offsets, neighbours, weights
+                                  and labels read once, and the coarse offsets,
+                                  neighbours, int64 weights and node weights
+                                  written once (compare with ms_contract) */
 } lcc_stats;
 
 typedef struct lcc_graph lcc_graph;

@@ -222,6 +222,7 @@ static void fill_stats(const Job &J, const Engine &E, lcc_stats *s, double ms_to
   s->bytes_bestmove = E.stats.edges * 8 + E.stats.wbytes + E.stats.verts * 32 + E.stats.cands * 8;
   s->pairs_sorted = E.stats.pairs;
   s->kernel_launches = launches;
+  s->bytes_contract_min = E.stats.contract_min_bytes;
   for (int i = 0; i < NB && i < 16; ++i) {
     s->ms_bucket[i] = E.stats.ms_bucket[i];
     s->bucket_entries[i] = E.stats.bucket_entries[i];

@@ -629,11 +629,14 @@ void Engine::contract(std::vector<Job *> &js) {
   if (timing) CK(cudaEventRecord(ev_[4], st_));
   std::vector<CJob> tab(nj);
   std::vector<int64_t> vs(nj + 1), es(nj + 1);
-  int64_t vt = 0, et = 0;
+  int64_t vt = 0, et = 0, read_min = 0;
   for (int i = 0; i < nj; ++i) {
     Level &L = js[i]->lv[js[i]->depth];
     es[i] = et;
     et += L.info.nnz;
+    // least reads: offsets, neighbours, weights and labels, once each
+    const int64_t wb = L.wtype == W_I32 ? 4 : (L.wtype == W_I64 ? 8 : 0);
+    read_min += (L.n + 1) * 8 + L.info.nnz * (4 + wb) + L.n * 4;
     CJob &c = tab[i];
     memset(&c, 0, sizeof(c));
     c.off = L.off;
@@ -738,6 +741,8 @@ void Engine::contract(std::vector<Job *> &js) {
   const int64_t nintra = hb[1];
   const int64_t U = Uall - (nintra > 0 ? 1 : 0);
   stats.pairs += P - nintra;
+  // least writes: coarse offsets, neighbours, int64 weights and node weights
+  stats.contract_min_bytes += read_min + (ntot + nj) * 8 + U * (4 + 8) + ntot * 8;
   int64_t *uvals = store->alloc<int64_t>(Uall);
   int32_t *unbr = store->alloc<int32_t>(U);
   int64_t *offg = store->alloc<int64_t>(ntot + 1);

@@ -160,6 +160,7 @@ struct Job {
 
 struct EngineStats {
   int64_t edges = 0, verts = 0, cands = 0, wbytes = 0, pairs = 0;
+  int64_t contract_min_bytes = 0;  // least bytes of the contractions (lcc_stats)
   int64_t rounds = 0;
   double ms_bm = 0, ms_round_other = 0, ms_contract = 0, ms_other = 0;
   double ms_bucket[NB] = {0};

@@ -53,7 +53,7 @@ class lcc_stats(C.Structure):
                 ("ms_total", C.c_double), ("bytes_bestmove", C.c_int64),
                 ("pairs_sorted", C.c_int64), ("kernel_launches", C.c_int64),
                 ("ms_bucket", C.c_double * 16), ("bucket_entries", C.c_int64 * 16),
-                ("bucket_vertices", C.c_int64 * 16)]
+                ("bucket_vertices", C.c_int64 * 16), ("bytes_contract_min", C.c_int64)]
 
 
 class lcc_server_cfg(C.Structure):

@@ -29,7 +29,7 @@ def lib():
         P, I64, I = C.c_void_p, C.c_int64, C.c_int
         U64 = C.c_uint64
         _lib.tw_cluster.argtypes = [I64, P, P, P, P, P, I, I64, I64, I, I, I, I, I, U64, I,
-                                    P, P, P, P, P, P]
+                                    P, I64, P, P, P, P, P, P, P]
         _lib.tw_best_moves.argtypes = [I64, P, P, P, P, P, I64, I64, I, I, I, U64, I,
                                        P, P, P]
         _lib.tw_compress.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P, P, P, P]
@@ -67,22 +67,48 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10, max_levels=
 
     Returns (labels, num, den, stats, threads_used) with CC = num / den
     exactly and stats = (levels, rounds, entries scanned)."""
+    return _cluster(off, nbr, w, p, q, mode, k, num_iter, max_levels, refine, vset, coin, seed,
+                    threads, None)
+
+
+TRACE_COLUMNS = ("level", "phase", "round", "vprime", "entries", "moved", "held")
+
+
+def cluster_trace(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10, max_levels=64,
+                  refine=True, vset=VSET_NBR_VERTICES, coin=False, seed=0, threads=0,
+                  max_rounds=100000):
+    """cluster() plus one row per best-move round (TRACE_COLUMNS): level
+    depth, phase (1 = refinement), round within the call, |V'|, entries
+    scanned, vertices moved and vertices the coin held back."""
+    buf = np.zeros((max_rounds, len(TRACE_COLUMNS)), np.int64)
+    res = _cluster(off, nbr, w, p, q, mode, k, num_iter, max_levels, refine, vset, coin, seed,
+                   threads, buf)
+    rows = res[-1]
+    if rows > max_rounds:
+        raise ValueError("more than %d rounds; raise max_rounds" % max_rounds)
+    return res[:-1], buf[:rows]
+
+
+def _cluster(off, nbr, w, p, q, mode, k, num_iter, max_levels, refine, vset, coin, seed,
+             threads, trace):
     off, nbr, w32, w64 = _graph(off, nbr, w)
     n = len(off) - 1
     kk = None if k is None else np.ascontiguousarray(k, dtype=np.int64)
     labels = np.empty(max(n, 1), np.int32)
-    hi, lo, den, nt = C.c_int64(), C.c_uint64(), C.c_int64(), C.c_int()
+    hi, lo, den, nt, tl = C.c_int64(), C.c_uint64(), C.c_int64(), C.c_int(), C.c_int64()
     st = np.zeros(3, np.int64)
     rc = lib().tw_cluster(n, _p(off), _p(nbr), _p(w32), _p(w64), _p(kk), mode, p, q,
                           num_iter, max_levels, int(bool(refine)), vset, int(bool(coin)),
-                          seed & ((1 << 64) - 1), threads,
+                          seed & ((1 << 64) - 1), threads, _p(trace),
+                          0 if trace is None else trace.shape[0], C.byref(tl),
                           _p(labels), C.byref(hi), C.byref(lo), C.byref(den), _p(st),
                           C.byref(nt))
     _check(rc, "cluster")
     v = (int(hi.value) << 64) | int(lo.value)
     if v >= 1 << 127:
         v -= 1 << 128
-    return labels[:n], v, den.value, tuple(int(x) for x in st), nt.value
+    out = (labels[:n], v, den.value, tuple(int(x) for x in st), nt.value)
+    return out + (tl.value,) if trace is not None else out
 
 
 def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES, coin=False, seed=0,

@@ -197,6 +197,11 @@ static int32_t best_of(const tw_level *g, int64_t v, int64_t p, int64_t q,
 /* Shared helpers                                                            */
 /* ------------------------------------------------------------------------ */
 
+/* Optional per-round record (TW_TRACE_COLS int64 per round): level depth,
+ * phase (0 coarsening, 1 refinement), round within the call, |V'|, entries
+ * scanned, vertices moved, vertices held back by the coin. */
+enum { TW_TRACE_COLS = 7 };
+
 typedef struct {
   int64_t p, q;
   int num_iter, max_levels, refine, vset;
@@ -205,6 +210,8 @@ typedef struct {
   int ntabs;
   int coin;
   uint64_t seed;
+  int64_t *trace;  /* [trace_cap][TW_TRACE_COLS] or NULL */
+  int64_t trace_cap, trace_len;
 } tw_run;
 
 static int run_tables(tw_run *r) {
@@ -321,8 +328,8 @@ static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
   }
   if (!err) memset(in, 1, m);
   for (int it = 0; !err && it < r->num_iter; ++it) {
-    int64_t scanned = 0, nwant = 0, nmoves = 0;
-#pragma omp parallel reduction(+ : scanned, nwant, nmoves)
+    int64_t scanned = 0, nwant = 0, nmoves = 0, nvp = 0;
+#pragma omp parallel reduction(+ : scanned, nwant, nmoves, nvp)
     {
       tw_table *t = &r->tabs[omp_get_thread_num()];
 #pragma omp for schedule(dynamic, 64)
@@ -331,6 +338,7 @@ static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
         if (!in[v]) { D[v] = L[v]; continue; }
         D[v] = best_of(g, v, p, q, L, K, t);
         scanned += g->off[v + 1] - g->off[v];
+        nvp += 1;
         if (D[v] != L[v]) {
           nwant += 1;
           if (coin.on && !coin_allows(&coin, it, v)) {
@@ -344,6 +352,12 @@ static int best_moves(const tw_level *g, tw_run *r, int32_t *L, int64_t *K,
     }
     r->rounds += 1;
     r->scanned += scanned;
+    if (r->trace && r->trace_len < r->trace_cap) {
+      int64_t *row = r->trace + r->trace_len * TW_TRACE_COLS;
+      row[0] = depth; row[1] = phase; row[2] = it; row[3] = nvp;
+      row[4] = scanned; row[5] = nmoves; row[6] = nwant - nmoves;
+    }
+    if (r->trace) r->trace_len += 1;
     if (nwant == 0) break;
     if (nmoves) *any = 1;
     /* every move at once; K follows by exact atomic sums */
@@ -617,11 +631,14 @@ static int set_threads(int threads) {
  * mode UNIT (k = 1), DEGREE (k_v = weighted degree, lambda = p / (q 2m)) or
  * CUSTOM (k_custom).  Outputs: canonical labels, q' CC as an int128 in
  * (num_hi, num_lo) with q' in *den_out, stats = (levels, rounds, entries
- * scanned), the thread count used.  Returns a TW_* status. */
+ * scanned), the thread count used, and, if trace is not NULL, up to
+ * trace_cap per-round rows (TW_TRACE_COLS each; *trace_len = rounds run).
+ * Returns a TW_* status. */
 int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
                const int32_t *w32, const int64_t *w64, const int64_t *k_custom,
                int mode, int64_t p, int64_t q, int num_iter, int max_levels,
                int refine, int vset, int coin, uint64_t seed, int threads,
+               int64_t *trace, int64_t trace_cap, int64_t *trace_len,
                int32_t *labels_out,
                int64_t *num_hi, uint64_t *num_lo, int64_t *den_out,
                int64_t *stats_out, int *threads_used) {
@@ -660,7 +677,8 @@ int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
     err = TW_ERR_INVALID;
   }
   if (!err) err = check_bounds(&g, p, qe);
-  tw_run r = {p, qe, num_iter, max_levels, refine, vset, 0, 0, 0, NULL, 0, coin, seed};
+  tw_run r = {p, qe, num_iter, max_levels, refine, vset, 0, 0, 0, NULL, 0, coin, seed,
+              trace, trace_cap, 0};
   if (!err) err = run_tables(&r);
   if (!err) err = run_level(&g, 0, &r, L);
   run_free(&r);
@@ -685,6 +703,7 @@ int tw_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
     stats_out[0] = r.levels;
     stats_out[1] = r.rounds;
     stats_out[2] = r.scanned;
+    if (trace_len) *trace_len = r.trace_len;
   }
   free(k); free(L); free(minid);
   return err;
@@ -710,7 +729,7 @@ int tw_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
   int64_t *K = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   if (!K) return TW_ERR_OOM;
   for (int64_t v = 0; v < n; ++v) K[L[v]] += k[v];
-  tw_run r = {p, q, num_iter, 1, 0, vset, 0, 0, 0, NULL, 0, coin, seed};
+  tw_run r = {p, q, num_iter, 1, 0, vset, 0, 0, 0, NULL, 0, coin, seed, NULL, 0, 0};
   err = run_tables(&r);
   if (!err) err = best_moves(&g, &r, L, K, moved, 0, 0);
   *rounds = r.rounds;
@@ -732,7 +751,7 @@ int tw_compress(int64_t n, const int64_t *off, const int32_t *nbr,
     if (L[v] < 0 || L[v] >= n) return TW_ERR_INVALID;
   tw_level g = {n, off, nbr, w32, w64, k}, g2;
   tw_coarse cg;
-  tw_run r = {1, 1, 0, 1, 0, 0, 0, 0, 0, NULL, 0, 0, 0};
+  tw_run r = {1, 1, 0, 1, 0, 0, 0, 0, 0, NULL, 0, 0, 0, NULL, 0, 0};
   int err = run_tables(&r);
   if (!err) err = compress(&g, L, &r, map, &g2, &cg);
   run_free(&r);
@@ -762,7 +781,7 @@ int tw_first_round(int64_t n, const int64_t *off, const int32_t *nbr,
   int32_t *L = (int32_t *)malloc(m * sizeof(int32_t));
   int64_t *K = (int64_t *)malloc(m * sizeof(int64_t));
   int64_t *kd = k ? NULL : (int64_t *)malloc(m * sizeof(int64_t));
-  tw_run r = {p, q, 1, 1, 0, TW_VSET_ALL, 0, 0, 0, NULL, 0, 0, 0};
+  tw_run r = {p, q, 1, 1, 0, TW_VSET_ALL, 0, 0, 0, NULL, 0, 0, 0, NULL, 0, 0};
   int err = (L && K && (k || kd)) ? run_tables(&r) : TW_ERR_OOM;
   tw_level g = {n, off, nbr, w32, NULL, k ? k : kd};
   if (!err && !k) {

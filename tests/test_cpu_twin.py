@@ -198,3 +198,34 @@ def test_twin_coin_best_moves_matches_oracle(vset):
         got = T.best_moves(g["off"], g["nbr"], g["w"], k, 1, 3, L0, it, vset, coin=True, seed=9,
                            threads=4)
         assert np.array_equal(got[0], want[0]) and got[1:] == want[1:]
+
+
+@pytest.mark.parametrize("coin", [False, True])
+def test_twin_round_trace(coin):
+    """Per-round records: one per round; entries sum to the scanned total;
+    each call's first round evaluates every vertex of its level; level 0's
+    coarsening rounds and moves agree with the oracle's Best-Moves; the same
+    records at every thread count."""
+    g = GRAPHS["cl"]
+    res, tr = T.cluster_trace(g["off"], g["nbr"], g["w"], 1, 1, mode=T.NODEW_DEGREE, coin=coin,
+                              seed=5, threads=4)
+    lab, num, den, st, _ = res
+    assert len(tr) == st[1] and int(tr[:, 4].sum()) == st[2]
+    firsts = tr[tr[:, 2] == 0]
+    assert firsts[0, 3] == g["n"] and (firsts[:, 3] > 0).all()
+    if not coin:
+        assert (tr[:, 6] == 0).all()
+    lvl0 = tr[(tr[:, 0] == 0) & (tr[:, 1] == 0)]
+    k, two_m = O.weighted_degrees(g["off"], g["w"])
+    L0 = np.arange(g["n"], dtype=np.int32)
+    prev = L0
+    for r in range(1, len(lvl0) + 1):
+        Lr, _, rounds = O.best_moves(g["off"], g["nbr"], g["w"], k, 1, two_m, L0, r,
+                                     coin=coin, seed=5)
+        assert rounds == r
+        moved = int((Lr != prev).sum())
+        assert moved == lvl0[r - 1, 5], r  # moves of round r (row r - 1)
+        prev = Lr
+    again = T.cluster_trace(g["off"], g["nbr"], g["w"], 1, 1, mode=T.NODEW_DEGREE, coin=coin,
+                            seed=5, threads=1)[1]
+    assert np.array_equal(again, tr)

@@ -25,3 +25,11 @@ def test_schedule_table_small_scale():
     coin = [r for r in rows if "| coin, V' = neighbours of moved vertices, refinement |" in r]
     plain = [r for r in rows if "| synchronous, V' = neighbours of moved vertices" in r]
     assert len(coin) == 2 and len(plain) == 2
+
+
+def test_vprime_table_small_scale():
+    rows = run(os.path.join("cpu_twin", "vprime.py"), "12")
+    assert len(rows) == 1 + 2 * 2 * 2  # header, then two graphs x two schedules x two rules
+    for r in rows[1:]:
+        first = r.rstrip(" |").split("|")[-1].split()[0]
+        assert first == "100.0"  # round 0 evaluates every vertex

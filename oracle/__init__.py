@@ -50,6 +50,19 @@ def lib():
     return _lib
 
 
+ERR_OVERFLOW = 5
+
+
+def _check(rc, what):
+    """Raise for an oracle status: OverflowError when the exact 128-bit range
+    would be left (q * sum|w| or p * (sum k)^2 reaching 2^125), else
+    ValueError."""
+    if rc == ERR_OVERFLOW:
+        raise OverflowError("oracle %s: outside the exact integer range" % what)
+    if rc:
+        raise ValueError("oracle %s failed: %d" % (what, rc))
+
+
 def _p(a):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -81,8 +94,7 @@ def objective_num(off, nbr, w, k, p, q, labels, literal=False):
     fn = lib().orc_objective_pairs if literal else lib().orc_objective
     rc = fn(len(off) - 1, _p(off), _p(nbr), _p(w), _p(k), p, q, _p(labels),
             C.byref(hi), C.byref(lo))
-    if rc:
-        raise ValueError("oracle objective failed: %d" % rc)
+    _check(rc, "objective")
     v = _i128(hi.value, lo.value)
     if v >= 1 << 127:
         v -= 1 << 128
@@ -103,8 +115,7 @@ def desired(off, nbr, w, k, p, q, L, K, v0=0, v1=None):
     D = np.empty(v1 - v0, np.int32)
     rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
                                  p, q, _p(L), _p(K), _p(D))
-    if rc:
-        raise ValueError("oracle desired failed: %d" % rc)
+    _check(rc, "desired")
     return D
 
 
@@ -119,8 +130,7 @@ def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K):
     D = np.empty(v1 - v0, np.int32)
     rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
                                  p, q, _p(L), _p(K), _p(D))
-    if rc:
-        raise ValueError("oracle desired failed: %d" % rc)
+    _check(rc, "desired")
     return D
 
 
@@ -136,8 +146,7 @@ def desired_list(n, verts, off_l, nbr_l, w_l, k, p, q, L, K):
     D = np.empty(len(verts), np.int32)
     rc = lib().orc_desired_list(n, len(verts), _p(verts), _p(off_l), _p(nbr_l), _p(w_l), _p(k),
                                 p, q, _p(L), _p(K), _p(D))
-    if rc:
-        raise ValueError("oracle desired_list failed: %d" % rc)
+    _check(rc, "desired_list")
     return D
 
 
@@ -157,8 +166,7 @@ def compress(off, nbr, w, k, L):
     rc = lib().orc_compress(n, _p(off), _p(nbr), _p(w), _p(k), _p(L), _p(mp),
                             C.byref(n2), C.byref(nnz2), C.byref(po),
                             C.byref(pn), C.byref(pw), C.byref(pk))
-    if rc:
-        raise ValueError("oracle compress failed: %d" % rc)
+    _check(rc, "compress")
 
     def take(ptr, cnt, ct, dt):
         if cnt == 0:
@@ -196,8 +204,7 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
                            int(bool(coin)), seed & ((1 << 64) - 1),
                            _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
                            _p(st))
-    if rc:
-        raise ValueError("oracle cluster failed: %d" % rc)
+    _check(rc, "cluster")
     v = _i128(hi.value, lo.value)
     if v >= 1 << 127:
         v -= 1 << 128
@@ -221,8 +228,7 @@ def sequential_cc(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, seed=0,
                                  seed & ((1 << 64) - 1), max_passes, max_levels,
                                  _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
                                  _p(st))
-    if rc:
-        raise ValueError("oracle sequential_cc failed: %d" % rc)
+    _check(rc, "sequential_cc")
     v = _i128(hi.value, lo.value)
     if v >= 1 << 127:
         v -= 1 << 128
@@ -240,7 +246,7 @@ def best_moves(off, nbr, w, k, p, q, L, num_iter, vset=VSET_NBR_VERTICES, coin=F
                               q, num_iter, vset, int(bool(coin)), seed & ((1 << 64) - 1),
                               _p(L), C.byref(rounds))
     if rc < 0:
-        raise ValueError("oracle best_moves failed: %d" % rc)
+        _check(-rc, "best_moves")
     return L, bool(rc), rounds.value
 
 

@@ -50,7 +50,7 @@
 
 typedef __int128 i128;
 
-enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_OOM = 4 };
+enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_OOM = 4, ORC_ERR_OVERFLOW = 5 };
 enum { VSET_ALL = 0, VSET_NBR_VERTICES = 1, VSET_NBR_CLUSTERS = 2 };
 enum { NODEW_UNIT = 0, NODEW_DEGREE = 1, NODEW_CUSTOM = 2 };
 
@@ -102,6 +102,44 @@ static int coin_allows(const coin_t *c, int round, int64_t v) {
 }
 
 /* ---------------------------------------------------------------------- */
+/* Range of the exact arithmetic                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Every q-scaled quantity is a difference of two terms: a gain (Appendix A)
+ * is q w(v,C) - p k_v K_C (or the stay form with K_c - k_v), and q CC is
+ * q S_in - p (sum_C K_C^2 - sum_v k_v^2) (Sec. 2).  With node weights k >= 0,
+ * W = sum of |w| over all entries and Ktot = sum_v k_v, the first term is at
+ * most q W and the second at most p Ktot^2 in magnitude.  Requiring
+ *   W < 2^62 (so that merged coarse weights and K fit int64),
+ *   q W < 2^125 and p Ktot^2 < 2^125
+ * keeps each term below 2^125 and every difference, and every comparison of
+ * two gains, inside a signed 128-bit integer.  Anything larger is refused
+ * with ORC_ERR_OVERFLOW instead of being computed with a wrapped value. */
+static int exact_range(i128 W, i128 Kt, int64_t p, int64_t q) {
+  const i128 lim = (i128)1 << 125;
+  if (W < 0 || Kt < 0) return ORC_ERR_INVALID;
+  if (W >= ((i128)1 << 62) || Kt >= ((i128)1 << 62)) return ORC_ERR_OVERFLOW;
+  if ((i128)q * W >= lim) return ORC_ERR_OVERFLOW;          /* < 2^63 * 2^62 */
+  if (Kt > 0 && (i128)p > (lim - 1) / (Kt * Kt)) return ORC_ERR_OVERFLOW;
+  return ORC_OK;
+}
+
+/* W over the entries [e0, e1) of w, and Ktot over k[0..n). */
+static i128 abs_weight(const int64_t *w, int64_t e0, int64_t e1) {
+  i128 W = 0;
+  for (int64_t e = e0; e < e1; ++e) W += w[e] < 0 ? -(i128)w[e] : (i128)w[e];
+  return W;
+}
+static i128 node_total(const int64_t *k, int64_t n) {
+  i128 Kt = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (k[v] < 0) return -1;
+    Kt += k[v];
+  }
+  return Kt;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Objective, Sec. 2                                                       */
 /* ---------------------------------------------------------------------- */
 
@@ -112,6 +150,8 @@ int orc_objective_pairs(int64_t n, const int64_t *off, const int32_t *nbr,
                         const int64_t *w, const int64_t *k, int64_t p,
                         int64_t q, const int32_t *labels, int64_t *num_hi,
                         uint64_t *num_lo) {
+  int rc = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, q);
+  if (rc != ORC_OK) return rc;
   i128 total = 0;
   for (int64_t i = 0; i < n; ++i) {
     for (int64_t j = 0; j < n; ++j) {
@@ -138,6 +178,8 @@ int orc_objective_pairs(int64_t n, const int64_t *off, const int32_t *nbr,
 int orc_objective(int64_t n, const int64_t *off, const int32_t *nbr,
                   const int64_t *w, const int64_t *k, int64_t p, int64_t q,
                   const int32_t *labels, int64_t *num_hi, uint64_t *num_lo) {
+  int rc = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, q);
+  if (rc != ORC_OK) return rc;
   i128 s_in = 0;
   for (int64_t u = 0; u < n; ++u)
     for (int64_t e = off[u]; e < off[u + 1]; ++e)
@@ -239,6 +281,9 @@ int orc_desired_range(int64_t n, int64_t v0, int64_t v1, const int64_t *off_w,
                       const int64_t *k, int64_t p, int64_t q, const int32_t *L,
                       const int64_t *K, int32_t *D) {
   if (v0 < 0 || v1 > n || v0 > v1 || q <= 0 || p < 0) return ORC_ERR_INVALID;
+  /* only the rows of the window are read: their |w| bounds every w(v,C) */
+  int rc = exact_range(abs_weight(w_w, 0, off_w[v1 - v0]), node_total(k, n), p, q);
+  if (rc != ORC_OK) return rc;
   scratch_t s;
   if (scratch_init(&s, n) != ORC_OK) { scratch_free(&s); return ORC_ERR_OOM; }
   for (int64_t v = v0; v < v1; ++v)
@@ -359,6 +404,9 @@ int orc_compress(int64_t n, const int64_t *off, const int32_t *nbr,
                  int64_t **off_out, int32_t **nbr_out, int64_t **w_out,
                  int64_t **k_out) {
   size_t m = (size_t)(n > 0 ? n : 1);
+  /* merged weights and coarse node weights are int64 sums */
+  if (abs_weight(w, 0, n > 0 ? off[n] : 0) >= ((i128)1 << 62)) return ORC_ERR_OVERFLOW;
+  if (node_total(k, n) >= ((i128)1 << 62)) return ORC_ERR_OVERFLOW;
   int32_t *rank = (int32_t *)malloc(m * sizeof(int32_t));
   if (!rank) return ORC_ERR_OOM;
   for (int64_t c = 0; c < n; ++c) rank[c] = -1;
@@ -508,7 +556,7 @@ static int node_weights(int64_t n, const int64_t *off, const int64_t *w,
     }
     if (two_m <= 0) return ORC_ERR_INVALID;
     i128 qq = (i128)q * two_m;
-    if (qq > (i128)INT64_MAX) return ORC_ERR_INVALID;
+    if (qq > (i128)INT64_MAX) return ORC_ERR_OVERFLOW;
     *qe = (int64_t)qq;
   } else if (mode == NODEW_CUSTOM) {
     for (int64_t v = 0; v < n; ++v) {
@@ -550,6 +598,8 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
   if (!k) return ORC_ERR_OOM;
   int64_t qe = q;
   int rc = node_weights(n, off, w, k_custom, mode, q, k, &qe);
+  if (rc == ORC_OK)
+    rc = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, qe);
   if (rc != ORC_OK) { free(k); return rc; }
   orc_stats st = {0, 0, 0};
   run_t r = {p, qe, num_iter, max_levels, refine, vset, &st, ORC_OK, coin, seed};
@@ -579,6 +629,9 @@ int orc_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
                    int num_iter, int vset, int coin, uint64_t seed, int32_t *L,
                    int64_t *rounds_out) {
   size_t m = (size_t)(n > 0 ? n : 1);
+  if (q <= 0 || p <= 0) return -ORC_ERR_INVALID;
+  const int range = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, q);
+  if (range != ORC_OK) return -range;
   int64_t *K = (int64_t *)calloc(m, sizeof(int64_t));
   if (!K) return -ORC_ERR_OOM;
   for (int64_t v = 0; v < n; ++v) {
@@ -604,6 +657,8 @@ int64_t orc_sequential_sweep(int64_t n, const int64_t *off,
                              const int64_t *k, int64_t p, int64_t q,
                              int32_t *L, int64_t max_moves) {
   size_t m = (size_t)(n > 0 ? n : 1);
+  if (exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, q) != ORC_OK)
+    return -1;
   int64_t *K = (int64_t *)calloc(m, sizeof(int64_t));
   scratch_t s;
   if (!K || scratch_init(&s, n) != ORC_OK) { free(K); return -1; }
@@ -744,6 +799,8 @@ int orc_sequential_cc(int64_t n, const int64_t *off, const int32_t *nbr,
   if (!k || !L) { free(k); free(L); return ORC_ERR_OOM; }
   int64_t qe = q;
   int rc = node_weights(n, off, w, k_custom, mode, q, k, &qe);
+  if (rc == ORC_OK)
+    rc = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, qe);
   if (rc == ORC_OK) {
     seq_run_t r = {p, qe, seed, max_passes, max_levels, 0, 0, 0, ORC_OK};
     level_t g = {n, off, nbr, w, k};
@@ -786,6 +843,8 @@ int orc_desired_list(int64_t n, int64_t nv, const int64_t *verts,
                      int64_t q, const int32_t *L, const int64_t *K,
                      int32_t *D) {
   if (nv < 0 || q <= 0 || p < 0) return ORC_ERR_INVALID;
+  int rc = exact_range(abs_weight(w_l, 0, off_l[nv]), node_total(k, n), p, q);
+  if (rc != ORC_OK) return rc;
   scratch_t s;
   if (scratch_init(&s, n) != ORC_OK) { scratch_free(&s); return ORC_ERR_OOM; }
   for (int64_t i = 0; i < nv; ++i) {

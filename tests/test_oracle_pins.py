@@ -445,6 +445,204 @@ def test_deterministic_and_refinement_flag():
     assert c[3][1] < a[3][1]
 
 
+# ------------------------------------- whole method, every level by brute force --
+
+def rows_graph(n, rows):
+    """CSR dict of a level given as rows[u] = [(v, w), ...] (sorted by v)."""
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    nbr = np.array([v for r in rows for v, _ in r], np.int32)
+    w = np.array([x for r in rows for _, x in r], np.int64)
+    return {"n": n, "off": off, "nbr": nbr, "w": w}
+
+
+def brute_best_moves(g, k, p, q, L, num_iter, vset, trace):
+    """Algorithm 1's Best-Moves with every desired cluster found by brute
+    force (re-evaluating the Sec. 2 definition per candidate), the moves of a
+    round applied together (Sec. 3.2.1) and V' per Sec. 3.2.2.  L is updated
+    in place; the moves of each round are appended to `trace`."""
+    W, E = dense(g)
+    n = g["n"]
+    off, nbr = g["off"], g["nbr"]
+    vp = np.ones(n, bool)
+    any_moved = False
+    for _ in range(num_iter):
+        D = L.copy()
+        for v in range(n):
+            if vp[v]:
+                D[v] = brute_desired(g, W, E, k, p, q, L, v)
+        moved = D != L
+        trace.append(int(moved.sum()))
+        if not moved.any():
+            break
+        any_moved = True
+        left = set(int(x) for x in L[moved])
+        L[:] = D
+        vp = np.zeros(n, bool)
+        if vset == O.VSET_ALL:
+            vp[:] = True
+        elif vset == O.VSET_NBR_VERTICES:
+            for v in np.nonzero(moved)[0]:
+                vp[nbr[off[v]:off[v + 1]]] = True
+        else:
+            for x in range(n):
+                if int(L[x]) in left:
+                    vp[nbr[off[x]:off[x + 1]]] = True
+    return any_moved
+
+
+def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log):
+    """Parallel-CC (Algorithm 1) on one level: singletons, Best-Moves, and
+    unless nothing moved or the level did not shrink, Compress (a dictionary
+    keyed by the two endpoint clusters, intra-cluster pairs dropped, coarse
+    node weight = cluster weight, coarse ids = occupied ids in order),
+    recursion, Flatten and -- with refinement (Sec. 3.2.3) -- a full
+    Best-Moves on this level from the flattened labels, at every depth."""
+    n = g["n"]
+    log["levels"] = max(log["levels"], depth + 1)
+    L = np.arange(n, dtype=np.int32)
+    trace = []
+    moved = brute_best_moves(g, k, p, q, L, num_iter, vset, trace)
+    log["rounds"] += len(trace)
+    if not moved:
+        return L
+    occupied = sorted(set(int(c) for c in L))
+    if len(occupied) == n:
+        return L
+    rank = {c: i for i, c in enumerate(occupied)}
+    n2 = len(occupied)
+    acc = {}
+    off, nbr, w = g["off"], g["nbr"], g["w"]
+    for u in range(n):
+        for e in range(off[u], off[u + 1]):
+            a, b = rank[int(L[u])], rank[int(L[nbr[e]])]
+            if a != b:
+                acc[(a, b)] = acc.get((a, b), 0) + int(w[e])
+    rows = [[] for _ in range(n2)]
+    for (a, b), x in sorted(acc.items()):
+        rows[a].append((b, x))
+    k2 = np.zeros(n2, np.int64)
+    for v in range(n):
+        k2[rank[int(L[v])]] += int(k[v])
+    L2 = brute_parallel_cc(rows_graph(n2, rows), k2, p, q, num_iter, vset, refine, depth + 1, log)
+    L = np.array([L2[rank[int(c)]] for c in L], np.int32)
+    if refine:
+        trace = []
+        brute_best_moves(g, k, p, q, L, num_iter, vset, trace)
+        log["rounds"] += len(trace)
+        log["refine"].append((depth, trace))
+    return L
+
+
+# (seed, n, lambda p, q, V' rule, node weights 1 or 1 + v mod 3): signed
+# graphs on which the method goes three or four levels deep
+DEEP_CASES = [(4, 9, 1, 3, O.VSET_ALL, 0), (0, 10, 1, 3, O.VSET_ALL, 0),
+              (8, 8, 1, 2, O.VSET_NBR_CLUSTERS, 1), (2, 9, 1, 4, O.VSET_NBR_VERTICES, 0),
+              (3, 10, 1, 4, O.VSET_NBR_VERTICES, 0)]
+
+
+@pytest.mark.parametrize("case", DEEP_CASES)
+@pytest.mark.parametrize("num_iter", [2, 4, 10])
+def test_multilevel_run_with_refinement_by_brute_force(case, num_iter):
+    """The oracle's whole run (labels, exact objective, levels, rounds)
+    equals Algorithm 1 simulated level by level from brute-force moves.  The
+    cases are chosen so that refinement moves vertices below the top level
+    and keeps moving for more than one round, which a refinement limited to
+    depth 0 or to a single round would not reproduce."""
+    seed, n, p, q, vset, kmode = case
+    g = small_graph(seed * 7 + n, n=n, p=0.45, lo=-2, hi=5)
+    k = np.ones(n, np.int64) if kmode == 0 else (np.arange(n) % 3 + 1).astype(np.int64)
+    log = {"levels": 0, "rounds": 0, "refine": []}
+    L = brute_parallel_cc(g, k, p, q, num_iter, vset, True, 0, log)
+    first = {}
+    for v in range(n):
+        first.setdefault(int(L[v]), v)
+    want = np.array([first[int(c)] for c in L], np.int32)
+    W, E = dense(g)
+    cc = cc_definition(W, E, k, Fraction(p, q), want)
+    labels, num, den, st = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=O.NODEW_CUSTOM,
+                                     k=k, num_iter=num_iter, vset=vset)
+    assert np.array_equal(labels, want)
+    assert Fraction(num, den) == cc
+    assert st[0] == log["levels"] and st[1] == log["rounds"]
+    assert log["levels"] >= 3
+    assert any(d >= 1 and sum(t) > 0 for d, t in log["refine"])
+    assert any(sum(1 for m in t if m > 0) >= 2 for _, t in log["refine"])
+
+
+# ------------------------------------------- range of the exact arithmetic --
+
+def heavy_graph(scale):
+    """Five vertices, six undirected edges whose weights are `scale` minus
+    small offsets (both directions stored)."""
+    edges = [(0, 1, 1), (1, 2, 3), (2, 3, 0), (3, 4, 5), (0, 4, 2), (1, 3, 7)]
+    rows = [[] for _ in range(5)]
+    for a, b, d in edges:
+        rows[a].append((b, scale - d))
+        rows[b].append((a, scale - d))
+    return rows_graph(5, [sorted(r) for r in rows])
+
+
+def brute_whole_run(g, k, p, q, num_iter=10):
+    log = {"levels": 0, "rounds": 0, "refine": []}
+    L = brute_parallel_cc(g, k, p, q, num_iter, O.VSET_NBR_VERTICES, True, 0, log)
+    first = {}
+    for v in range(g["n"]):
+        first.setdefault(int(L[v]), v)
+    return np.array([first[int(c)] for c in L], np.int32)
+
+
+def test_exact_range_degree_mode_refuses_at_the_bound():
+    """Modularity mode at gamma = 8 on a graph whose total weight 2m is just
+    above 2^61: p * (sum k)^2 = 8 (2m)^2 passes 2^125, so the run is refused
+    rather than computed with wrapped 128-bit gains.  Just below 2^61 it is
+    accepted, and then its labels and exact objective equal the brute-force
+    Algorithm 1 evaluated in unbounded Python integers."""
+    base = (1 << 61) // 12  # twelve entries
+    over = heavy_graph(base + 64)
+    assert int(np.abs(over["w"]).sum()) > 1 << 61
+    with pytest.raises(OverflowError):
+        O.cluster(over["off"], over["nbr"], over["w"], 8, 1, mode=O.NODEW_DEGREE)
+    under = heavy_graph(base - 64)
+    two_m = int(under["w"].sum())
+    assert two_m < 1 << 61 and 8 * two_m * two_m < 1 << 125
+    k = np.array([int(under["w"][under["off"][v]:under["off"][v + 1]].sum())
+                  for v in range(5)], np.int64)
+    labels, num, den, _ = O.cluster(under["off"], under["nbr"], under["w"], 8, 1,
+                                    mode=O.NODEW_DEGREE)
+    assert den == two_m
+    want = brute_whole_run(under, k, 8, two_m)
+    assert np.array_equal(labels, want)
+    W, E = dense(under)
+    assert Fraction(num, den) == cc_definition(W, E, k, Fraction(8, two_m), want)
+
+
+def test_exact_range_custom_node_weights_boundary():
+    """Custom node weights summing to 2^32: p = 2^61 puts p * (sum k)^2 at
+    exactly 2^125 and is refused; p = 2^61 - 1 is accepted and matches the
+    brute-force run.  The same holds for the single-round and objective
+    entry points."""
+    g = heavy_graph(1000)
+    k = np.full(5, 1 << 30, np.int64)
+    k[4] = (1 << 32) - 4 * (1 << 30)
+    k[3] -= 5
+    k[4] += 5
+    assert int(k.sum()) == 1 << 32 and (k >= 0).all()
+    L = np.arange(5, dtype=np.int32)
+    for fn in (lambda p: O.cluster(g["off"], g["nbr"], g["w"], p, 1, mode=O.NODEW_CUSTOM, k=k),
+               lambda p: O.objective_num(g["off"], g["nbr"], g["w"], k, p, 1, L),
+               lambda p: O.desired(g["off"], g["nbr"], g["w"], k, p, 1, L, k),
+               lambda p: O.best_moves(g["off"], g["nbr"], g["w"], k, p, 1, L, 3)):
+        with pytest.raises(OverflowError):
+            fn(1 << 61)
+        fn((1 << 61) - 1)
+    p = (1 << 61) - 1
+    labels, num, den, _ = O.cluster(g["off"], g["nbr"], g["w"], p, 1, mode=O.NODEW_CUSTOM, k=k)
+    assert np.array_equal(labels, brute_whole_run(g, k, p, 1))
+    W, E = dense(g)
+    assert Fraction(num, den) == cc_definition(W, E, k, Fraction(p, 1), labels)
+
+
 def test_weighted_degrees_match_numpy():
     for seed in range(3):
         g = I.to_numpy(I.random_signed_graph(50, 0.2, 0, 9, 600 + seed))

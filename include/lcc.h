@@ -18,7 +18,12 @@
  *
  * Arithmetic.  lambda is the rational p/q with p, q > 0.  Every gain is an
  * exact integer (gains are scaled by q), so labels are bit-identical from run
- * to run and independent of thread scheduling.  Ties between candidate
+ * to run and independent of thread scheduling.  Exactness has a range: with
+ * W = sum of |w| over all entries and Ktot = sum of the node weights, every
+ * call that computes gains or the objective returns LCC_ERR_OVERFLOW unless
+ * W < 2^62, Ktot < 2^62, q W < 2^125 and p Ktot^2 < 2^125 (q being q 2m in
+ * LCC_NODEW_DEGREE mode).  Inside it every gain term, every comparison of two
+ * gains and the objective fit a signed 128-bit integer on every level.  Ties between candidate
  * clusters go to the smallest cluster id, and a vertex moves only when the
  * best candidate is strictly better than staying.  Vertex v may also move to
  * cluster id v when that id has zero weight and none of v's neighbours is in
@@ -60,7 +65,11 @@ extern "C" {
 typedef enum lcc_status {
   LCC_OK = 0,
   LCC_ERR_INVALID = 1,       /* bad argument or malformed CSR */
-  LCC_ERR_NOT_SYMMETRIC = 2, /* the multiset {(u,v,w)} differs from {(v,u,w)} */
+  LCC_ERR_NOT_SYMMETRIC = 2, /* the multiset {(u,v,w)} differs from {(v,u,w)};
+                                lcc_load_csr compares two 128-bit hashes of the
+                                multisets, so an asymmetric graph passes only
+                                if the hashes collide (probability about
+                                2^-64 or less) */
   LCC_ERR_SELF_LOOP = 3,     /* an entry u -> u */
   LCC_ERR_OOM = 4,           /* device or host allocation failed */
   LCC_ERR_OVERFLOW = 5,      /* a total exceeds the exact integer range */
@@ -270,12 +279,19 @@ LCC_API lcc_status lcc_objective(const lcc_graph *g, int64_t lambda_p,
  * lambda = lambda_p / lambda_q > 0 (for modularity pass q * 2m).
  * Working memory is one fixed 16 MiB array inside the library, which every GPU
  * that loads the library keeps until the process exits; rows longer than 4096
- * entries do not fit and make the call return LCC_ERR_INVALID (the other rows
- * are still written).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls on a device share the array and the call clears what it
- * needs, but calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it: order them.  Synchronises `stream` before returning.
+ * entries do not fit and make the call return LCC_ERR_INVALID.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); under lazy module loading the first call on a device
+ * is the one that loads the library's device code, and with it the 16 MiB
+ * array, so make that first call during set-up, before any stream capture.
+ * All calls on a device share the array and the call clears what it needs,
+ * but calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it: order them.  Synchronises `stream` before returning.
+ * The kernel checks what it reads and the call then returns, instead of
+ * LCC_OK: LCC_ERR_INVALID for a neighbour id or label outside [0, n), a
+ * negative node or cluster weight, or a cluster weight above the total node
+ * weight; LCC_ERR_OVERFLOW outside the exact range stated at the top of this
+ * file.  d_desired is unspecified after an error.
  */
 LCC_API lcc_status lcc_desired_noalloc(const int64_t *d_off, const int32_t *d_nbr,
                                        const int32_t *d_w, const int64_t *d_k, int64_t n,
@@ -352,7 +368,13 @@ typedef struct lcc_job {
   int64_t n, nnz;
   int64_t lambda_p, lambda_q;
   int32_t mode;             /* LCC_NODEW_UNIT or LCC_NODEW_DEGREE */
-  int32_t reserved;
+  /* Fault injection, for testing a serving deployment's error handling
+     without a GPU fault: 0 (the normal value) does nothing; t > 0 makes the
+     job fail with LCC_ERR_CUDA ("injected fault") at the start of its t-th
+     engine tick, through the same path as a real error raised in a tick.
+     Such an error belongs to one job, so only that job fails; the jobs that
+     run with it continue and return their normal results. */
+  int32_t inject_fault_tick;
 } lcc_job;
 
 /*

@@ -639,6 +639,7 @@ struct SJob {
   bool weighted = false;
   int64_t n = 0, nnz = 0, p = 1, q = 1;
   int32_t mode = 0;
+  int32_t inject_fault_tick = 0;
   int64_t est = 0;
   SState state = S_QUEUED;
   bool cancel = false;
@@ -748,6 +749,7 @@ static void server_loop(lcc_server *s) {
         J.sc = s->cfg.sched;
         J.labels_out = j->labels.data();
         J.labels_space = LCC_MEM_HOST;
+        J.inject_fault_tick = j->inject_fault_tick;
         E.add_job(&J);
       } catch (const Error &e) {
         E.drop_job(&j->job);
@@ -778,16 +780,27 @@ static void server_loop(lcc_server *s) {
           finish_job(s, j, LCC_OK, "");
         }
       } catch (const std::exception &e) {
-        // a failing tick fails every job that was in it
         std::vector<SJob *> run;
         {
           std::lock_guard<std::mutex> lk(s->mu);
           run = s->running;
         }
         const Error *le = dynamic_cast<const Error *>(&e);
-        for (SJob *j : run) {
-          E.drop_job(&j->job);
-          finish_job(s, j, le ? le->st : LCC_ERR_CUDA, e.what());
+        SJob *culprit = nullptr;
+        if (le && le->job)
+          for (SJob *j : run)
+            if (&j->job == le->job) culprit = j;
+        if (culprit) {
+          // raised before any job's state changed in this tick: only that job
+          // fails, the others run on in the next tick
+          E.drop_job(&culprit->job);
+          finish_job(s, culprit, le->st, e.what());
+        } else {
+          // otherwise the tick's state is unknown: every job in it fails
+          for (SJob *j : run) {
+            E.drop_job(&j->job);
+            finish_job(s, j, le ? le->st : LCC_ERR_CUDA, e.what());
+          }
         }
       }
     }
@@ -827,6 +840,8 @@ lcc_status lcc_submit(lcc_server *s, const lcc_job *job, uint64_t *ticket) {
   j->p = job->lambda_p;
   j->q = job->lambda_q;
   j->mode = job->mode;
+  if (job->inject_fault_tick < 0) fail(LCC_ERR_INVALID, "inject_fault_tick must be >= 0");
+  j->inject_fault_tick = job->inject_fault_tick;
   j->weighted = job->weights != nullptr;
   j->est = job_estimate(job->n, job->nnz, j->weighted);
   if (j->est > s->cfg.hbm_budget_bytes) {

@@ -367,8 +367,20 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
       if (qq > (i128)INT64_MAX) throw Error(LCC_ERR_OVERFLOW, "q * 2m exceeds int64");
       j->q = (int64_t)qq;
     }
-    if ((i128)I.ksum * (i128)I.ksum >= ((i128)1 << 126))
-      throw Error(LCC_ERR_OVERFLOW, "total node weight too large for exact arithmetic");
+    // Range of the exact arithmetic.  A q-scaled gain is q w(v,C) - p k_v K_C
+    // and q CC is q S_in - p (sum K^2 - sum k^2); with k >= 0 the first terms
+    // are at most q * sum|w| and the second at most p * (sum k)^2.  Both
+    // below 2^125 keep every gain, every comparison of two gains and the
+    // objective inside a signed 128-bit integer on every level (coarse levels
+    // keep sum k and never raise sum|w|).
+    {
+      const i128 lim = (i128)1 << 125;
+      const i128 kt = (i128)I.ksum, wa = (i128)I.wabs;
+      if (I.ksat || kt >= ((i128)1 << 62) || wa >= ((i128)1 << 62) || (i128)j->q * wa >= lim ||
+          (kt > 0 && (i128)j->p > (lim - 1) / (kt * kt)))
+        throw Error(LCC_ERR_OVERFLOW,
+                    "q * sum|w| or p * (sum k)^2 reaches 2^125: outside the exact integer range");
+    }
     j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
     // cluster weights fit the 32-bit half of the packed label word
     if (j->ktot >= (int64_t)KNONE) j->lv[0].lk = nullptr;
@@ -1001,6 +1013,14 @@ void Engine::compress_to_graph(Job *J, int32_t *map_host, lcc_graph **out) {
 // ---------------------------------------------------------------- tick ----
 
 std::vector<Job *> Engine::tick() {
+  // Per-job checks come first, while no job's state has changed in this
+  // tick: an error raised here names its job, and the caller can drop that
+  // job and tick the others again.
+  for (Job *J : active_) {
+    J->ticks += 1;
+    if (J->inject_fault_tick > 0 && J->ticks >= J->inject_fault_tick)
+      throw Error(LCC_ERR_CUDA, "injected fault (tick " + std::to_string(J->ticks) + ")", J);
+  }
   std::vector<Job *> bm;
   for (Job *J : active_)
     if (J->phase == P_BM) bm.push_back(J);

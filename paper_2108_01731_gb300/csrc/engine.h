@@ -18,7 +18,12 @@ namespace lcc {
 
 struct Error : std::runtime_error {
   lcc_status st;
-  Error(lcc_status s, const std::string &m) : std::runtime_error(m), st(s) {}
+  // The one job this error belongs to, when it is raised before any other
+  // job's state changed in the current tick (the others can go on); null
+  // when the whole tick must be failed.
+  const void *job = nullptr;
+  Error(lcc_status s, const std::string &m, const void *j = nullptr)
+      : std::runtime_error(m), st(s), job(j) {}
 };
 
 void check_cuda(cudaError_t e, const char *what, int line);
@@ -156,6 +161,11 @@ struct Job {
   int32_t labels_space = LCC_MEM_HOST;
   // owned node-weight / state storage of level 0
   std::shared_ptr<Store> base;
+  // ticks this job has been in (Engine::tick), and the fault-injection hook
+  // of the serving API: > 0 makes tick number inject_fault_tick raise an
+  // error for this job alone
+  int64_t ticks = 0;
+  int64_t inject_fault_tick = 0;
 };
 
 struct EngineStats {

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
   int cur = -1;
   int64_t bc[NB];
   int64_t hcap = 0, hun = 0, hsu = 0, rmax = 0, kmax = 0, ksum = 0, wabs = 0, kneg = 0, hmax = 0,
-          ents = 0;
+          ents = 0, ksat = 0;
   for (int i = 0; i < NB; ++i) bc[i] = 0;
   auto flush = [&]() {
     if (cur < 0) return;
@@ -48,13 +48,19 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
     if (hsu) atomicAdd((unsigned long long *)&I->hub_sunits, (unsigned long long)hsu);
     atomicMax((unsigned long long *)&I->rmax, (unsigned long long)rmax);
     atomicMax((unsigned long long *)&I->kmax, (unsigned long long)kmax);
-    if (ksum) atomicAdd((unsigned long long *)&I->ksum, (unsigned long long)ksum);
+    if (ksum) {
+      // node weights are non-negative and each addend is below 2^62, so the
+      // add that carries the total past 2^62 sees it before any wrap
+      const unsigned long long old = atomicAdd((unsigned long long *)&I->ksum, (unsigned long long)ksum);
+      if (old >= (1ull << 62) || old + (unsigned long long)ksum >= (1ull << 62)) ksat = 1;
+    }
+    if (ksat) atomicOr((unsigned long long *)&I->ksat, 1ull);
     if (wabs) atomicAdd((unsigned long long *)&I->wabs, (unsigned long long)wabs);
     if (kneg) atomicAdd((unsigned long long *)&I->pad, (unsigned long long)kneg);
     if (hmax) atomicMax((unsigned long long *)&I->hub_maxcap, (unsigned long long)hmax);
     if (ents) atomicAdd((unsigned long long *)&I->nnz, (unsigned long long)ents);
     for (int i = 0; i < NB; ++i) bc[i] = 0;
-    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = hmax = ents = 0;
+    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = hmax = ents = ksat = 0;
   };
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
        i += warps_total) {
@@ -91,9 +97,13 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
       if (ra > rmax) rmax = ra;
       wabs += ra;
       const int64_t kv = J->k[v];
-      if (kv < 0) kneg += 1;
-      else if (kv > kmax) kmax = kv;
-      ksum += kv;
+      if (kv < 0) {
+        kneg += 1;
+      } else {
+        if (kv > kmax) kmax = kv;
+        if (kv >= ((int64_t)1 << 62) - ksum) ksat = 1;  // the running total would reach 2^62
+        else ksum += kv;
+      }
     }
   }
   if (lane == 0) flush();

@@ -229,6 +229,7 @@ struct LevelInfo {
   int64_t pad;          // vertices with a negative node weight
   int64_t hub_maxcap;   // largest hub table
   int64_t nnz;          // entries (sum of deg)
+  int64_t ksat;         // nonzero: the sum of node weights reached 2^62 (ksum is then not exact)
 };
 
 // Per-job accumulators of the objective kernels.

@@ -17,7 +17,6 @@
 // streams) race on the array, so such calls must be ordered by the caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "engine.h"
@@ -52,11 +51,47 @@ __device__ __forceinline__ bool na_better(lcc::i128 s1, int32_t c1, lcc::i128 s2
   return s1 > s2 || (s1 == s2 && c1 < c2);
 }
 
+// Words of the 256-byte control block at the start of the scratch array.
+enum : int {
+  NA_LONG_ROW = 0,  // a row is longer than NA_MAX_DEG
+  NA_MAX_ROW = 1,   // the longest such row
+  NA_BAD_ID = 2,    // a neighbour id or a label outside [0, n)
+  NA_NEG = 3,       // a negative node weight or cluster weight
+  NA_WABS = 4,      // sum of |w| over the rows evaluated
+  NA_WSAT = 5,      // ... reached 2^62
+  NA_KSUM = 6,      // sum of the node weights
+  NA_KSAT = 7,      // ... reached 2^62
+  NA_KMAX = 8       // largest cluster weight K[c]
+};
+constexpr unsigned long long NA_LIM62 = 1ull << 62;
+
+// Adds a non-negative x < 2^62 to a running total, raising *sat instead once
+// the total would reach 2^62.
+__device__ __forceinline__ void na_add_sat(unsigned long long &acc, unsigned long long x,
+                                           unsigned long long &sat) {
+  if (x >= NA_LIM62 - acc) sat = 1;
+  else acc += x;
+}
+
+// Adds a partial total (< 2^62) into a control word; the add that carries the
+// word past 2^62 sees it, so wrapping cannot hide a large total.
+__device__ __forceinline__ void na_flush_sat(unsigned long long *ctl, int word, int satword,
+                                             unsigned long long acc, unsigned long long sat) {
+  if (acc) {
+    const unsigned long long old = atomicAdd(ctl + word, acc);
+    if (old >= NA_LIM62 || old + acc >= NA_LIM62) sat = 1;
+  }
+  if (sat) atomicOr(ctl + satword, 1ull);
+}
+
 // Same rule as the library's best-move kernels (gain of moving v from its
 // cluster to a neighbouring one, scaled by q, exact in 128 bits; ties to the
 // smallest cluster id; strict improvement over staying; cluster id v with
 // zero weight and no neighbour in it as a gain-0 candidate).  One block per
 // vertex at a time; the block's table is its slice of the static array.
+// Besides D, the kernel records in the control block what the host needs to
+// refuse inputs it cannot handle exactly: ids out of range (those entries are
+// skipped), negative weights, the totals sum|w| and sum k, and the largest K.
 __global__ void __launch_bounds__(NA_THREADS)
     k_desired_noalloc(unsigned char *scratch, const int64_t *__restrict__ off,
                       const int32_t *__restrict__ nbr, const int32_t *__restrict__ w,
@@ -71,16 +106,33 @@ __global__ void __launch_bounds__(NA_THREADS)
   int32_t *tkey = (int32_t *)(scratch + 256 + (size_t)blockIdx.x * NA_TABLE_BYTES);
   unsigned long long *tval = (unsigned long long *)(tkey + NA_CAP);
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  unsigned long long wacc = 0, wsat = 0, kacc = 0, ksat = 0, kmaxK = 0;
+  int bad = 0, neg = 0;
   for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
     const int64_t beg = off[v];
     const int64_t deg = off[v + 1] - beg;
     const int32_t Lv = L[v];
+    const int64_t kv64 = k[v];
+    if (tid == 0) {
+      // node weight of v and cluster weight of id v: every id is visited once
+      const int64_t Kv = K[v];
+      if (kv64 < 0 || Kv < 0) neg = 1;
+      else {
+        na_add_sat(kacc, (unsigned long long)kv64, ksat);
+        if ((unsigned long long)Kv > kmaxK) kmaxK = (unsigned long long)Kv;
+      }
+      if (Lv < 0 || (int64_t)Lv >= n) bad = 1;
+    }
     if (deg > NA_MAX_DEG) {
       if (tid == 0) {
-        atomicExch(ctl, 1ull);
-        atomicMax(ctl + 1, (unsigned long long)deg);
+        atomicExch(ctl + NA_LONG_ROW, 1ull);
+        atomicMax(ctl + NA_MAX_ROW, (unsigned long long)deg);
         D[v] = Lv;
       }
+      continue;
+    }
+    if (Lv < 0 || (int64_t)Lv >= n) {  // uniform over the block
+      if (tid == 0) D[v] = Lv;
       continue;
     }
     int cap = 2;
@@ -92,8 +144,18 @@ __global__ void __launch_bounds__(NA_THREADS)
     }
     __syncthreads();
     for (int64_t e = tid; e < deg; e += NA_THREADS) {
-      const int32_t c = L[nbr[beg + e]];
+      const int32_t u = nbr[beg + e];
       const long long wt = w ? (long long)w[beg + e] : 1;
+      na_add_sat(wacc, (unsigned long long)(wt < 0 ? -wt : wt), wsat);
+      if (u < 0 || (int64_t)u >= n) {
+        bad = 1;
+        continue;
+      }
+      const int32_t c = L[u];
+      if (c < 0 || (int64_t)c >= n) {
+        bad = 1;
+        continue;
+      }
       uint32_t s = na_slot(c, lg);
       for (int t = 0; t < cap; ++t) {
         const int32_t prev = atomicCAS(tkey + s, -1, c);
@@ -105,7 +167,7 @@ __global__ void __launch_bounds__(NA_THREADS)
       }
     }
     __syncthreads();
-    const lcc::i128 kv = (lcc::i128)k[v];
+    const lcc::i128 kv = (lcc::i128)kv64;
     lcc::i128 best = (lcc::i128)((unsigned __int128)1 << 127);
     int32_t bc = INT32_MAX;
     long long w_stay = 0;
@@ -168,10 +230,12 @@ __global__ void __launch_bounds__(NA_THREADS)
     }
     __syncthreads();
   }
+  if (bad) atomicOr(ctl + NA_BAD_ID, 1ull);
+  if (neg) atomicOr(ctl + NA_NEG, 1ull);
+  na_flush_sat(ctl, NA_WABS, NA_WSAT, wacc, wsat);
+  na_flush_sat(ctl, NA_KSUM, NA_KSAT, kacc, ksat);
+  if (kmaxK) atomicMax(ctl + NA_KMAX, kmaxK);
 }
-
-std::mutex g_na_mu;
-void *g_na_addr[256] = {nullptr};
 
 }  // namespace
 
@@ -186,40 +250,51 @@ extern "C" lcc_status lcc_desired_noalloc(const int64_t *d_off, const int32_t *d
       throw lcc::Error(LCC_ERR_INVALID, "lambda_p and lambda_q must be positive");
     if (!d_off || (n > 0 && (!d_nbr || !d_k || !d_labels || !d_K || !d_desired)))
       throw lcc::Error(LCC_ERR_INVALID, "NULL device pointer");
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) throw lcc::Error(LCC_ERR_INVALID, "device index out of range");
+    // Device address of the static array on the current device.  In host code
+    // the array's name only stands in for it; the address is looked up on
+    // every call (a cheap query once the module is loaded), so it stays right
+    // after a device reset reloads the module.  The first call on a device may
+    // be the one that loads the module, and with it the array.
     void *base = nullptr;
     {
-      // First call on this device: look up where the static array lives.
-      std::lock_guard<std::mutex> lk(g_na_mu);
-      if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-          cudaGetLastError();
-          throw lcc::Error(LCC_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") +
-                                             cudaGetErrorString(e));
-        }
-        g_na_addr[dev] = p;
+      const cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+      if (e != cudaSuccess || !base) {
+        cudaGetLastError();
+        throw lcc::Error(LCC_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") +
+                                           cudaGetErrorString(e));
       }
-      base = g_na_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaMemsetAsync(base, 0, 256, st));  // control block: error flag, longest row
+    CK(cudaMemsetAsync(base, 0, 256, st));  // control block
     if (n > 0) {
       k_desired_noalloc<<<NA_BLOCKS, NA_THREADS, 0, st>>>(
           (unsigned char *)base, d_off, d_nbr, d_w, d_k, n, lambda_p, lambda_q, d_labels, d_K,
           d_desired);
       CK(cudaGetLastError());
     }
-    unsigned long long ctl[2] = {0, 0};
+    unsigned long long ctl[16] = {0};
     CK(cudaMemcpyAsync(ctl, base, sizeof(ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (ctl[0])
+    if (ctl[NA_BAD_ID])
+      throw lcc::Error(LCC_ERR_INVALID, "a neighbour id or a label is outside [0, n)");
+    if (ctl[NA_NEG]) throw lcc::Error(LCC_ERR_INVALID, "negative node or cluster weight");
+    if (ctl[NA_LONG_ROW])
       throw lcc::Error(LCC_ERR_INVALID,
-                       "a row has " + std::to_string(ctl[1]) + " entries; the allocation-free "
-                       "path handles rows of at most " + std::to_string(NA_MAX_DEG));
+                       "a row has " + std::to_string(ctl[NA_MAX_ROW]) + " entries; the "
+                       "allocation-free path handles rows of at most " + std::to_string(NA_MAX_DEG));
+    // the exact range of the library's other entry points: every gain term
+    // (q w(v,C) and p k_v K_C, with K_C at most the total node weight) below 2^125
+    {
+      typedef lcc::i128 I;
+      const I lim = (I)1 << 125;
+      const I wa = (I)ctl[NA_WABS], kt = (I)ctl[NA_KSUM];
+      if (ctl[NA_WSAT] || ctl[NA_KSAT] || wa >= ((I)1 << 62) || kt >= ((I)1 << 62) ||
+          (I)lambda_q * wa >= lim || (kt > 0 && (I)lambda_p > (lim - 1) / (kt * kt)))
+        throw lcc::Error(LCC_ERR_OVERFLOW,
+                         "q * sum|w| or p * (sum k)^2 reaches 2^125: outside the exact integer range");
+      if ((I)ctl[NA_KMAX] > kt)
+        throw lcc::Error(LCC_ERR_INVALID, "a cluster weight exceeds the total node weight");
+    }
     return LCC_OK;
   } catch (const lcc::Error &e) {
     lcc::set_last_error(e.what());

@@ -65,7 +65,7 @@ class lcc_job(C.Structure):
     _fields_ = [("offsets", C.c_void_p), ("nbrs", C.c_void_p),
                 ("weights", C.c_void_p), ("n", C.c_int64), ("nnz", C.c_int64),
                 ("lambda_p", C.c_int64), ("lambda_q", C.c_int64),
-                ("mode", C.c_int32), ("reserved", C.c_int32)]
+                ("mode", C.c_int32), ("inject_fault_tick", C.c_int32)]
 
 
 class LccError(RuntimeError):
@@ -367,12 +367,15 @@ class Server:
         _check(lib.lcc_server_create(C.byref(cfg), C.byref(self.h)))
         self.sizes = {}
 
-    def submit(self, off, nbr, w, lambda_p, lambda_q, mode):
+    def submit(self, off, nbr, w, lambda_p, lambda_q, mode, inject_fault_tick=0):
+        """Queue a job; inject_fault_tick > 0 is the fault-injection hook of
+        lcc_job (the job fails at the start of that engine tick)."""
         off = np.ascontiguousarray(off, np.int64)
         nbr = np.ascontiguousarray(nbr, np.int32)
         w = None if w is None else np.ascontiguousarray(w, np.int32)
         job = lcc_job(off.ctypes.data, nbr.ctypes.data, None if w is None else w.ctypes.data,
-                      len(off) - 1, len(nbr), int(lambda_p), int(lambda_q), int(mode), 0)
+                      len(off) - 1, len(nbr), int(lambda_p), int(lambda_q), int(mode),
+                      int(inject_fault_tick))
         t = C.c_uint64()
         _check(load().lcc_submit(self.h, C.byref(job), C.byref(t)))
         self.sizes[t.value] = len(off) - 1

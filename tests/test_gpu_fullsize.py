@@ -1,14 +1,25 @@
 """Parity at the full sizes of the benchmark configurations.
 
+* Planted partition, 10^4 vertices in 100 blocks, lambda = 1/100, 20 rounds
+  per Best-Moves call: whole runs (labels, exact objective, levels, rounds,
+  entries scanned) element by element.
 * R-MAT, 2^26 vertices, 2^31 entries (the benchmark workload): the first
   best-move round of every vertex on the GPU, compared with the oracle on a
   sample of vertices (random ones plus the highest-degree hubs), and the
-  invariants of a whole run.
+  invariants of a whole run.  With LCC_TEST_RMAT26_WHOLE=1 the labels and
+  exact objective of the whole benchmark step are also compared with the
+  OpenMP CPU twin on every host core: the twin is checked bit for bit
+  against the oracle at 1-8 threads by tests/test_cpu_twin.py, so the chain
+  GPU = twin = oracle holds without a single-threaded oracle run of
+  ~190 G scanned entries.
 * Chung-Lu, 2^20 vertices, ~32M entries: three synchronous rounds, the
-  compression of their labels and a two-level run, element by element.
+  compression of their labels, and whole multi-level runs to convergence,
+  element by element.
 * kNN similarity graph, 10^6 points (signed fixed-point weights): two rounds
-  element by element and sampled first rounds for the three resolutions.
+  element by element, and whole runs at the three resolutions.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -92,6 +103,33 @@ def test_chung_lu_2e20_rounds_compress_and_levels(L):
     wl, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, 1, mode=O.NODEW_DEGREE,
                                 num_iter=3, max_levels=2)
     assert np.array_equal(lab, wl) and st["obj_num"] == num and st["obj_den"] == den
+    # the configuration as benchmarked: modularity, num_iter 10 per call,
+    # refinement, levels until the recursion ends
+    same_run(L, G, g, 1, 1, L.LCC_NODEW_DEGREE, L.schedule())
+    G.free()
+
+
+def same_run(L, G, g, p, q, mode, sched, **kw):
+    """lcc_cluster and the oracle's Parallel-CC on the same graph and
+    schedule: labels, exact objective, levels, rounds and scanned entries."""
+    lab, obj, st = L.lcc_cluster(G, p, q, mode, sched)
+    wl, num, den, ws = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode,
+                                 num_iter=sched.num_iter, max_levels=sched.max_levels,
+                                 refine=bool(sched.refine), vset=sched.vset, **kw)
+    assert np.array_equal(lab, wl)
+    assert st["obj_num"] == num and st["obj_den"] == den
+    assert (st["levels"], st["rounds_total"], st["edges_scanned"]) == ws
+    return st
+
+
+def test_planted_partition_config1_whole_runs(L):
+    """10^4 vertices, 100 blocks of 100, p_in = 0.05, p_out = 0.0005, unit
+    node weights, lambda = 1/100, 20 rounds per Best-Moves call."""
+    g = I.to_numpy(I.sbm([100] * 100, 0.05, 0.0005, seed=I.BASE_SEED + 0))
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    for vset in (L.LCC_VSET_NBR_VERTICES, L.LCC_VSET_ALL, L.LCC_VSET_NBR_CLUSTERS):
+        st = same_run(L, G, g, 1, 100, L.LCC_NODEW_UNIT, L.schedule(num_iter=20, vset=vset))
+        assert st["levels"] >= 2
     G.free()
 
 
@@ -119,4 +157,29 @@ def test_knn_1e6_signed_weights(L):
         D = L.lcc_desired(G, p, q, L.LCC_NODEW_UNIT, L0)
         wantd = O.desired_list(n, verts, off_l, nbr_l, w_l, k, p, q, L0, k)
         assert np.array_equal(D[verts], wantd)
+    # whole multi-level runs at the three resolutions, element by element
+    gh = {"off": off, "nbr": nbr, "w": w}
+    for p, q in [(16384, 25), (32768, 5), (32768, 1)]:
+        same_run(L, G, gh, p, q, L.LCC_NODEW_UNIT, L.schedule())
     G.free()
+
+
+@pytest.mark.skipif(os.environ.get("LCC_TEST_RMAT26_WHOLE") != "1",
+                    reason="about ten minutes of host time: set LCC_TEST_RMAT26_WHOLE=1")
+def test_rmat_2e26_whole_run_equals_cpu_twin(L):
+    """The benchmark step itself (R-MAT 2^26, modularity, default schedule):
+    labels, exact objective, levels, rounds and scanned entries of the GPU
+    run equal those of the OpenMP CPU twin on all host cores."""
+    import torch
+    import cpu_twin as T
+    g = I.rmat(26, 1 << 30, seed=I.BASE_SEED + 4, device="cuda")
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    off, nbr, w = (g[x].cpu().numpy() for x in ("off", "nbr", "w"))
+    del g
+    torch.cuda.empty_cache()
+    lab, obj, st = L.lcc_cluster(G, 1, 1, L.LCC_NODEW_DEGREE)
+    G.free()
+    tl, num, den, ts, _ = T.cluster(off, nbr, w, 1, 1, mode=T.NODEW_DEGREE)
+    assert np.array_equal(lab, tl)
+    assert st["obj_num"] == num and st["obj_den"] == den
+    assert (st["levels"], st["rounds_total"], st["edges_scanned"]) == tuple(ts)

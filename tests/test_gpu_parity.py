@@ -362,17 +362,6 @@ def test_pull_and_mark_frontiers_agree(L):
     assert extra > 0
 
 
-def test_config1_planted_partition_full_size(L):
-    """SBM, 10,000 vertices in 100 blocks, p_in 0.05, p_out 0.0005, lambda
-    1/100, 20 rounds per Best-Moves, contraction and refinement."""
-    g = I.to_numpy(I.sbm([100] * 100, 0.05, 0.0005, seed=I.BASE_SEED + 1))
-    G = L.lcc_load_csr(g["off"], g["nbr"])
-    labels, obj, st = L.lcc_cluster(G, 1, 100, O.NODEW_UNIT, L.schedule(num_iter=20))
-    wl, num, den, _ = O.cluster(g["off"], g["nbr"], None, 1, 100, num_iter=20)
-    assert np.array_equal(labels, wl) and st["obj_num"] == num
-    G.free()
-
-
 def test_device_labels_and_device_csr(L):
     import torch
     g = GRAPHS["hubs"]
@@ -469,6 +458,66 @@ def test_input_validation(L):
     G.free()
 
 
+def test_exact_range_guard(L):
+    """The 128-bit gains stay exact only while q * sum|w| and p * (sum k)^2
+    are below 2^125; past that the library refuses with LCC_ERR_OVERFLOW
+    instead of returning wrapped scores, exactly where the oracle refuses.
+
+    Custom node weights: one vertex of weight 2^40 and the rest of weight 1,
+    q = 2^62.  The largest accepted p has p * (sum k)^2 just below 2^125, and
+    the unit-weight vertices still merge (lambda = p / q is about 2^-17), so
+    the accepted run moves vertices with gains near 2^66 and is compared
+    with the oracle; p + 1 is refused by both.  In modularity mode, int32
+    weights near 2^31 and a resolution numerator at the limit do the same."""
+    g = GRAPHS["signed"]
+    n = g["n"]
+    k = np.ones(n, np.int64)
+    k[n // 2] = 1 << 40
+    kt = int(k.sum())
+    q = 1 << 62
+    pmax = ((1 << 125) - 1) // (kt * kt)
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+    Lb = np.arange(n, dtype=np.int32)
+    for fn in (lambda p: L.lcc_cluster(G, p, q, O.NODEW_CUSTOM),
+               lambda p: L.lcc_desired(G, p, q, O.NODEW_CUSTOM, Lb),
+               lambda p: L.lcc_objective(G, p, q, O.NODEW_CUSTOM, Lb)):
+        with pytest.raises(L.LccError) as e:
+            fn(pmax + 1)
+        assert e.value.status == L.LCC_ERR_OVERFLOW
+    with pytest.raises(OverflowError):
+        O.cluster(g["off"], g["nbr"], g["w"], pmax + 1, q, mode=O.NODEW_CUSTOM, k=k)
+    labels, obj, st = L.lcc_cluster(G, pmax, q, O.NODEW_CUSTOM)
+    wl, num, den, ws = O.cluster(g["off"], g["nbr"], g["w"], pmax, q, mode=O.NODEW_CUSTOM, k=k)
+    assert np.array_equal(labels, wl) and st["obj_num"] == num and st["obj_den"] == den
+    assert (st["levels"], st["rounds_total"], st["edges_scanned"]) == ws
+    assert len(np.unique(labels)) < n // 2  # the unit-weight vertices merged
+    G.free()
+    # modularity mode: heavy int32 weights, gamma = p / 1 at the limit
+    rng = np.random.default_rng(5)
+    h = GRAPHS["hubs_w"]
+    off, nbr = h["off"], h["nbr"]
+    src = np.repeat(np.arange(h["n"]), np.diff(off))
+    a, b = np.minimum(src, nbr), np.maximum(src, nbr)
+    # one weight per undirected edge, the same in both directions
+    key = a.astype(np.int64) * h["n"] + b
+    uniq, inv = np.unique(key, return_inverse=True)
+    w = rng.integers(1 << 29, (1 << 31) - 1, len(uniq)).astype(np.int64)[inv].astype(np.int32)
+    two_m = int(w.astype(np.int64).sum())
+    pmax = ((1 << 125) - 1) // (two_m * two_m)
+    assert 1 < pmax < (1 << 62)
+    G = L.lcc_load_csr(off, nbr, w)
+    with pytest.raises(L.LccError) as e:
+        L.lcc_cluster(G, pmax + 1, 1, O.NODEW_DEGREE)
+    assert e.value.status == L.LCC_ERR_OVERFLOW
+    with pytest.raises(OverflowError):
+        O.cluster(off, nbr, w, pmax + 1, 1, mode=O.NODEW_DEGREE)
+    labels, obj, st = L.lcc_cluster(G, pmax, 1, O.NODEW_DEGREE, L.schedule(num_iter=4))
+    wl, num, den, ws = O.cluster(off, nbr, w, pmax, 1, mode=O.NODEW_DEGREE, num_iter=4)
+    assert np.array_equal(labels, wl) and st["obj_num"] == num and st["obj_den"] == den
+    assert (st["levels"], st["rounds_total"], st["edges_scanned"]) == ws
+    G.free()
+
+
 # --------------------------------------------------- batching and serving --
 
 @pytest.mark.parametrize("force_layout", [False, True])
@@ -515,6 +564,53 @@ def test_server_results_match_single_runs(L):
         assert lat > 0
     c = srv.counters()
     assert c["done"] == len(graphs) and c["peak_jobs"] <= 5
+    srv.close()
+
+
+def test_server_isolates_failing_jobs(L):
+    """Bad jobs mixed into a stream fail alone: an asymmetric CSR and a CSR
+    with a self loop are refused when admitted, and a job whose fault
+    injection raises an error inside an engine tick fails with that error;
+    every other job of the stream, including those that ran in the same
+    ticks, returns the oracle's labels."""
+    import time
+    good = [I.to_numpy(I.serving_graph(i)) for i in range(20, 29)]
+    asym = dict(good[0])
+    asym["nbr"] = good[0]["nbr"].copy()
+    r0 = slice(asym["off"][0], asym["off"][1])
+    asym["nbr"][r0] = (asym["nbr"][r0] + 1) % asym["n"]  # row 0 points elsewhere
+    asym["nbr"][r0] = np.where(asym["nbr"][r0] == 0, 1, asym["nbr"][r0])
+    loop = dict(good[1])
+    loop["nbr"] = good[1]["nbr"].copy()
+    loop["nbr"][loop["off"][3]] = 3
+    srv = L.Server(hbm_budget_bytes=8 << 30, max_slots=6)
+    tickets, kinds = [], []
+    for i, g in enumerate(good):
+        if i == 2:
+            tickets.append(srv.submit(asym["off"], asym["nbr"], None, 1, 1, O.NODEW_DEGREE))
+            kinds.append(("bad", (L.LCC_ERR_NOT_SYMMETRIC, L.LCC_ERR_INVALID)))
+        if i == 4:
+            tickets.append(srv.submit(loop["off"], loop["nbr"], None, 1, 1, O.NODEW_DEGREE))
+            kinds.append(("bad", (L.LCC_ERR_SELF_LOOP, L.LCC_ERR_NOT_SYMMETRIC)))
+        fault = 3 if i == 5 else 0
+        tickets.append(srv.submit(g["off"], g["nbr"], None, 1, 1, O.NODEW_DEGREE,
+                                  inject_fault_tick=fault))
+        kinds.append(("fault", (L.LCC_ERR_CUDA,)) if fault else ("good", g))
+        if i % 3 == 2:
+            time.sleep(0.005)
+    srv.wait_idle(600000)
+    for t, (kind, x) in zip(tickets, kinds):
+        if kind == "good":
+            labels, obj, lat = srv.poll(t)
+            wl, num, den, _ = O.cluster(x["off"], x["nbr"], None, 1, 1, mode=O.NODEW_DEGREE)
+            assert np.array_equal(labels, wl)
+        else:
+            with pytest.raises(L.LccError) as e:
+                srv.poll(t)
+            assert e.value.status in x, (kind, e.value)
+            if kind == "fault":
+                assert "injected fault" in str(e.value)
+    assert srv.counters()["done"] == len(tickets)
     srv.close()
 
 

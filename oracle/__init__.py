@@ -36,7 +36,7 @@ def lib():
         _lib.orc_free.argtypes = [P]
         _lib.orc_cluster.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
                                      C.c_int, C.c_int, C.c_int, C.c_int,
-                                     C.c_int, C.c_uint64, P, P, P, P, P]
+                                     C.c_int, C.c_uint64, P, P, P, P, P, P, I64, P]
         _lib.orc_best_moves.argtypes = [I64, P, P, P, P, I64, I64, C.c_int,
                                         C.c_int, C.c_int, C.c_uint64, P, P]
         _lib.orc_sequential_cc.argtypes = [I64, P, P, P, P, C.c_int, I64, I64,
@@ -46,6 +46,11 @@ def lib():
         _lib.orc_sequential_sweep.restype = I64
         _lib.orc_weighted_degrees_i32.argtypes = [I64, P, P, P]
         _lib.orc_desired_list.argtypes = [I64, I64, P, P, P, P, P, I64, I64, P, P, P]
+        _lib.orc_scratch_new.argtypes = [I64]
+        _lib.orc_scratch_new.restype = P
+        _lib.orc_scratch_free.argtypes = [P]
+        _lib.orc_desired_scratch.argtypes = [P, I64, I64, I64, P, P, P, P, I64, I64,
+                                             P, P, P]
         _lib.orc_weighted_degrees_i32.restype = I64
     return _lib
 
@@ -119,8 +124,28 @@ def desired(off, nbr, w, k, p, q, L, K, v0=0, v1=None):
     return D
 
 
-def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K):
-    """As desired(), with rows [v0, v1) already cut out as a CSR window."""
+class Scratch:
+    """The oracle's per-vertex aggregation scratch for an n-vertex graph, made
+    (and its pages touched) once, for many desired_window calls."""
+
+    def __init__(self, n):
+        self.n = n
+        self.h = lib().orc_scratch_new(n)
+        if not self.h:
+            raise MemoryError("oracle scratch")
+
+    def close(self):
+        if self.h:
+            lib().orc_scratch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K, scratch=None):
+    """As desired(), with rows [v0, v1) already cut out as a CSR window;
+    `scratch` (a Scratch of n) avoids re-making the scratch per call."""
     offw = _c(offw, np.int64)
     nbrw = _c(nbrw, np.int32)
     ww = _c(ww, np.int64)
@@ -128,8 +153,13 @@ def desired_window(n, v0, v1, offw, nbrw, ww, k, p, q, L, K):
     L = _c(L, np.int32)
     K = _c(K, np.int64)
     D = np.empty(v1 - v0, np.int32)
-    rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
-                                 p, q, _p(L), _p(K), _p(D))
+    if scratch is not None:
+        assert scratch.n == n
+        rc = lib().orc_desired_scratch(scratch.h, n, v0, v1, _p(offw), _p(nbrw), _p(ww),
+                                       _p(k), p, q, _p(L), _p(K), _p(D))
+    else:
+        rc = lib().orc_desired_range(n, v0, v1, _p(offw), _p(nbrw), _p(ww), _p(k),
+                                     p, q, _p(L), _p(K), _p(D))
     _check(rc, "desired")
     return D
 
@@ -184,13 +214,20 @@ def compress(off, nbr, w, k, L):
     return mp, off2, nbr2, w2, k2
 
 
+TRACE_COLUMNS = ("level", "phase", "round", "vprime", "entries", "moved", "held")
+
+
 def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
-            max_levels=64, refine=True, vset=VSET_NBR_VERTICES, coin=False, seed=0):
+            max_levels=64, refine=True, vset=VSET_NBR_VERTICES, coin=False, seed=0,
+            trace=False, max_rounds=100000):
     """Parallel-CC (Algorithm 1, synchronous; coin=True adds the seeded
     symmetry-breaking coin of the library's LCC_SCHED_COIN schedule).
 
     Returns (labels, num, den, stats): the objective is CC = num / den exactly
-    (den = q, or q * 2m in DEGREE mode); stats = (levels, rounds, edges)."""
+    (den = q, or q * 2m in DEGREE mode); stats = (levels, rounds, edges).
+    With trace=True a fifth element holds one row per best-move round
+    (TRACE_COLUMNS): depth, phase (1 = refinement after Flatten), round of
+    the call, |V'|, entries scanned, vertices moved, vertices held back."""
     off, nbr, w = _graph(off, nbr, w)
     n = len(off) - 1
     kk = _c(k, np.int64) if k is not None else np.zeros(1, np.int64)
@@ -199,16 +236,24 @@ def cluster(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, num_iter=10,
     lo = C.c_uint64()
     den = C.c_int64()
     st = np.zeros(3, np.int64)
+    buf = np.zeros((max_rounds if trace else 1, len(TRACE_COLUMNS)), np.int64)
+    tl = C.c_int64()
     rc = lib().orc_cluster(n, _p(off), _p(nbr), _p(w), _p(kk), mode, p, q,
                            num_iter, max_levels, int(bool(refine)), vset,
                            int(bool(coin)), seed & ((1 << 64) - 1),
                            _p(labels), C.byref(hi), C.byref(lo), C.byref(den),
-                           _p(st))
+                           _p(st), _p(buf) if trace else None,
+                           max_rounds if trace else 0, C.byref(tl))
     _check(rc, "cluster")
     v = _i128(hi.value, lo.value)
     if v >= 1 << 127:
         v -= 1 << 128
-    return labels, v, den.value, tuple(int(x) for x in st)
+    out = (labels, v, den.value, tuple(int(x) for x in st))
+    if trace:
+        if tl.value > max_rounds:
+            raise ValueError("more than %d rounds; raise max_rounds" % max_rounds)
+        out = out + (buf[:tl.value].copy(),)
+    return out
 
 
 def sequential_cc(off, nbr, w, p, q, mode=NODEW_UNIT, k=None, seed=0,

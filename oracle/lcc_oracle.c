@@ -67,7 +67,14 @@ typedef struct {
   int64_t rounds_total;
   int64_t edges_scanned;
   int64_t levels;
+  /* optional per-round record (the paper's plot of |V'| per round, appendix):
+   * rows of ORC_TRACE_COLS = depth, phase (1 = refinement after Flatten),
+   * round of the Best-Moves call, |V'|, entries scanned, vertices moved,
+   * vertices the coin held back */
+  int64_t *trace;
+  int64_t trace_cap, trace_len;
 } orc_stats;
+enum { ORC_TRACE_COLS = 7 };
 
 /* SplitMix64 (S. Vigna's public-domain generator after Steele, Lea and
  * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014).
@@ -272,25 +279,53 @@ static int32_t desired_cluster(int64_t v, int64_t rb, int64_t re,
   return cv;
 }
 
+/* A scratch made once for many calls of orc_desired_scratch (the timed CPU
+ * sample evaluates a large graph in windows): its pages are touched here, so
+ * no timed window pays for allocating or first-touching them. */
+void *orc_scratch_new(int64_t n) {
+  scratch_t *s = (scratch_t *)calloc(1, sizeof(scratch_t));
+  if (!s) return NULL;
+  if (scratch_init(s, n) != ORC_OK) { scratch_free(s); free(s); return NULL; }
+  size_t m = (size_t)(n > 0 ? n : 1);
+  memset(s->acc, 0, m * sizeof(i128));
+  memset(s->seen, 0, m);
+  memset(s->touched, 0, m * sizeof(int32_t));
+  return s;
+}
+void orc_scratch_free(void *s) {
+  if (!s) return;
+  scratch_free((scratch_t *)s);
+  free(s);
+}
+
 /* One synchronous evaluation for the vertices v in [v0, v1): D[v - v0] is the
  * desired cluster of v under the snapshot (L, K) of all n vertices.  The rows
  * come as a window: row v is nbr_w[off_w[v-v0] .. off_w[v-v0+1]).  Used for the
- * parity checks of a single round and for the timed CPU sample. */
+ * parity checks of a single round and for the timed CPU sample.  `scratch`
+ * comes from orc_scratch_new(n) (it is left empty after the call). */
+int orc_desired_scratch(void *scratch, int64_t n, int64_t v0, int64_t v1,
+                        const int64_t *off_w, const int32_t *nbr_w, const int64_t *w_w,
+                        const int64_t *k, int64_t p, int64_t q, const int32_t *L,
+                        const int64_t *K, int32_t *D) {
+  if (!scratch || v0 < 0 || v1 > n || v0 > v1 || q <= 0 || p < 0) return ORC_ERR_INVALID;
+  /* only the rows of the window are read: their |w| bounds every w(v,C) */
+  int rc = exact_range(abs_weight(w_w, 0, off_w[v1 - v0]), node_total(k, n), p, q);
+  if (rc != ORC_OK) return rc;
+  for (int64_t v = v0; v < v1; ++v)
+    D[v - v0] = desired_cluster(v, off_w[v - v0], off_w[v - v0 + 1], nbr_w,
+                                w_w, k, p, q, L, K, (scratch_t *)scratch);
+  return ORC_OK;
+}
+
 int orc_desired_range(int64_t n, int64_t v0, int64_t v1, const int64_t *off_w,
                       const int32_t *nbr_w, const int64_t *w_w,
                       const int64_t *k, int64_t p, int64_t q, const int32_t *L,
                       const int64_t *K, int32_t *D) {
-  if (v0 < 0 || v1 > n || v0 > v1 || q <= 0 || p < 0) return ORC_ERR_INVALID;
-  /* only the rows of the window are read: their |w| bounds every w(v,C) */
-  int rc = exact_range(abs_weight(w_w, 0, off_w[v1 - v0]), node_total(k, n), p, q);
-  if (rc != ORC_OK) return rc;
-  scratch_t s;
-  if (scratch_init(&s, n) != ORC_OK) { scratch_free(&s); return ORC_ERR_OOM; }
-  for (int64_t v = v0; v < v1; ++v)
-    D[v - v0] = desired_cluster(v, off_w[v - v0], off_w[v - v0 + 1], nbr_w,
-                                w_w, k, p, q, L, K, &s);
-  scratch_free(&s);
-  return ORC_OK;
+  void *s = orc_scratch_new(n);
+  if (!s) return ORC_ERR_OOM;
+  const int rc = orc_desired_scratch(s, n, v0, v1, off_w, nbr_w, w_w, k, p, q, L, K, D);
+  orc_scratch_free(s);
+  return rc;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -321,17 +356,20 @@ static int best_moves(const level_t *g, int64_t p, int64_t q, int num_iter,
   for (int64_t v = 0; v < n; ++v) in_vp[v] = 1; /* V' <- V */
   for (int it = 0; it < num_iter; ++it) {
     /* parfor v in V': D[v] from the snapshot (L, K) of this round */
+    int64_t nvp = 0, nent = 0;
     for (int64_t v = 0; v < n; ++v) {
       if (in_vp[v]) {
         D[v] = desired_cluster(v, g->off[v], g->off[v + 1], g->nbr, g->w,
                                g->k, p, q, L, K, &s);
-        st->edges_scanned += g->off[v + 1] - g->off[v];
+        nvp += 1;
+        nent += g->off[v + 1] - g->off[v];
       } else {
         D[v] = L[v];
       }
     }
+    st->edges_scanned += nent;
     st->rounds_total += 1;
-    int64_t nwant = 0;
+    int64_t nwant = 0, nmoved = 0, nheld = 0;
     for (int64_t v = 0; v < n; ++v) {
       held[v] = 0;
       if (D[v] != L[v]) {
@@ -339,11 +377,24 @@ static int best_moves(const level_t *g, int64_t p, int64_t q, int num_iter,
         if (coin && coin->on && !coin_allows(coin, it, v)) {
           D[v] = L[v];
           held[v] = 1;
+          ++nheld;
         }
       }
       moved[v] = (D[v] != L[v]);
+      nmoved += moved[v];
       any |= moved[v];
     }
+    if (st->trace && st->trace_len < st->trace_cap) {
+      int64_t *row = st->trace + st->trace_len * ORC_TRACE_COLS;
+      row[0] = coin ? coin->depth : 0;
+      row[1] = coin ? coin->phase : 0;
+      row[2] = it;
+      row[3] = nvp;
+      row[4] = nent;
+      row[5] = nmoved;
+      row[6] = nheld;
+    }
+    st->trace_len += 1;
     if (nwant == 0) break;
     /* move every v to D[v] at once; K follows the moves */
     memset(left, 0, m);
@@ -590,7 +641,8 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
                 int64_t p, int64_t q, int num_iter, int max_levels, int refine,
                 int vset, int coin, uint64_t seed, int32_t *labels_out,
                 int64_t *num_hi, uint64_t *num_lo, int64_t *den_out,
-                int64_t *stats_out) {
+                int64_t *stats_out, int64_t *trace, int64_t trace_cap,
+                int64_t *trace_len) {
   if (n < 0 || p <= 0 || q <= 0 || num_iter < 0 || max_levels < 1)
     return ORC_ERR_INVALID;
   size_t m = (size_t)(n > 0 ? n : 1);
@@ -601,7 +653,7 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
   if (rc == ORC_OK)
     rc = exact_range(abs_weight(w, 0, n > 0 ? off[n] : 0), node_total(k, n), p, qe);
   if (rc != ORC_OK) { free(k); return rc; }
-  orc_stats st = {0, 0, 0};
+  orc_stats st = {0, 0, 0, trace, trace_cap, 0};
   run_t r = {p, qe, num_iter, max_levels, refine, vset, &st, ORC_OK, coin, seed};
   level_t g = {n, off, nbr, w, k};
   int32_t *L = (int32_t *)malloc(m * sizeof(int32_t));
@@ -615,6 +667,7 @@ int orc_cluster(int64_t n, const int64_t *off, const int32_t *nbr,
     stats_out[1] = st.rounds_total;
     stats_out[2] = st.edges_scanned;
   }
+  if (trace_len) *trace_len = st.trace_len;
   free(k);
   free(L);
   return rc;
@@ -638,7 +691,7 @@ int orc_best_moves(int64_t n, const int64_t *off, const int32_t *nbr,
     if (L[v] < 0 || L[v] >= n) { free(K); return -ORC_ERR_INVALID; }
     K[L[v]] += k[v];
   }
-  orc_stats st = {0, 0, 0};
+  orc_stats st = {0, 0, 0, NULL, 0, 0};
   int err = ORC_OK;
   level_t g = {n, off, nbr, w, k};
   const coin_t c = {coin, seed, 0, 0};

@@ -456,11 +456,12 @@ def rows_graph(n, rows):
     return {"n": n, "off": off, "nbr": nbr, "w": w}
 
 
-def brute_best_moves(g, k, p, q, L, num_iter, vset, trace):
+def brute_best_moves(g, k, p, q, L, num_iter, vset, trace, rows=None, depth=0, phase=0):
     """Algorithm 1's Best-Moves with every desired cluster found by brute
     force (re-evaluating the Sec. 2 definition per candidate), the moves of a
     round applied together (Sec. 3.2.1) and V' per Sec. 3.2.2.  L is updated
-    in place; the moves of each round are appended to `trace`."""
+    in place; the moves of each round are appended to `trace`, and with
+    `rows` a record (depth, phase, round, |V'|, entries, moved, 0) too."""
     W, E = dense(g)
     n = g["n"]
     off, nbr = g["off"], g["nbr"]
@@ -473,6 +474,10 @@ def brute_best_moves(g, k, p, q, L, num_iter, vset, trace):
                 D[v] = brute_desired(g, W, E, k, p, q, L, v)
         moved = D != L
         trace.append(int(moved.sum()))
+        if rows is not None:
+            deg = np.diff(off)
+            rows.append((depth, phase, len(trace) - 1, int(vp.sum()), int(deg[vp].sum()),
+                         int(moved.sum()), 0))
         if not moved.any():
             break
         any_moved = True
@@ -502,7 +507,7 @@ def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log):
     log["levels"] = max(log["levels"], depth + 1)
     L = np.arange(n, dtype=np.int32)
     trace = []
-    moved = brute_best_moves(g, k, p, q, L, num_iter, vset, trace)
+    moved = brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 0)
     log["rounds"] += len(trace)
     if not moved:
         return L
@@ -528,7 +533,7 @@ def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log):
     L = np.array([L2[rank[int(c)]] for c in L], np.int32)
     if refine:
         trace = []
-        brute_best_moves(g, k, p, q, L, num_iter, vset, trace)
+        brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 1)
         log["rounds"] += len(trace)
         log["refine"].append((depth, trace))
     return L
@@ -568,6 +573,23 @@ def test_multilevel_run_with_refinement_by_brute_force(case, num_iter):
     assert log["levels"] >= 3
     assert any(d >= 1 and sum(t) > 0 for d, t in log["refine"])
     assert any(sum(1 for m in t if m > 0) >= 2 for _, t in log["refine"])
+
+
+@pytest.mark.parametrize("case", DEEP_CASES[1:4])
+def test_round_trace_by_brute_force(case):
+    """The oracle's per-round record (depth, phase, round, |V'|, entries,
+    moved) of a whole multi-level run equals the brute-force Algorithm 1's,
+    round by round, in the same order (coarsening calls on the way down,
+    refinement calls on the way up)."""
+    seed, n, p, q, vset, kmode = case
+    g = small_graph(seed * 7 + n, n=n, p=0.45, lo=-2, hi=5)
+    k = np.ones(n, np.int64) if kmode == 0 else (np.arange(n) % 3 + 1).astype(np.int64)
+    log = {"levels": 0, "rounds": 0, "refine": [], "rows": []}
+    brute_parallel_cc(g, k, p, q, 4, vset, True, 0, log)
+    *_, tr = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=O.NODEW_CUSTOM, k=k, num_iter=4,
+                       vset=vset, trace=True)
+    assert [tuple(int(x) for x in r) for r in tr] == log["rows"]
+    assert any(r[3] < n for r in log["rows"])  # V' shrank below V in some round
 
 
 # ------------------------------------------- range of the exact arithmetic --

@@ -47,6 +47,17 @@ WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, m=1 << 26, mode=1, p=1, q=1, num_iter=10,
                    desc="R-MAT a=0.57 b=c=0.19 d=0.05, 2^22 vertices, 2^26 undirected edges, "
                         "modularity (gamma=1)"),
+    # the paper's R-MAT density sweep (Sec. 4, scalability; its generator's
+    # a=0.5, b=c=0.1, d=0.3) at 2^20 vertices: m = 5n, 50n and n^1.5
+    "rmat20_5n": dict(kind="rmat", scale=20, m=5 << 20, abc=(0.5, 0.1, 0.1), mode=1, p=1, q=1,
+                      num_iter=10, desc="R-MAT a=0.5 b=c=0.1 d=0.3, 2^20 vertices, m = 5n, "
+                                        "modularity (gamma=1)"),
+    "rmat20_50n": dict(kind="rmat", scale=20, m=50 << 20, abc=(0.5, 0.1, 0.1), mode=1, p=1,
+                       q=1, num_iter=10, desc="R-MAT a=0.5 b=c=0.1 d=0.3, 2^20 vertices, "
+                                               "m = 50n, modularity (gamma=1)"),
+    "rmat20_n15": dict(kind="rmat", scale=20, m=1 << 30, abc=(0.5, 0.1, 0.1), mode=1, p=1, q=1,
+                       num_iter=10, desc="R-MAT a=0.5 b=c=0.1 d=0.3, 2^20 vertices, "
+                                         "m = n^1.5 = 2^30, modularity (gamma=1)"),
     "sbm1e4": dict(kind="sbm", mode=0, p=1, q=100, num_iter=20,
                    desc="planted partition, 100 blocks of 100, p_in 0.05, p_out 0.0005, "
                         "lambda 1/100, 20 rounds"),
@@ -69,6 +80,9 @@ def parse():
                     help="skip the OpenMP CPU twin's timed first round")
     ap.add_argument("--no-coin", action="store_true",
                     help="skip the extra step with the symmetry-breaking coin")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also run the R-MAT density sweep (2^20 vertices, m = 5n, 50n, n^1.5) "
+                         "and report it as density_sweep")
     ap.add_argument("--tuning-cache", default=None,
                     help="tuning file for lcc_autotune: reuse this GPU's line if present, "
                          "else measure and append (keeps the routing fixed across runs)")
@@ -111,7 +125,8 @@ def make_graph(wl, device):
     from paper_2108_01731_gb300 import inputs as I
     seed = I.BASE_SEED
     if wl["kind"] == "rmat":
-        return I.rmat(wl["scale"], wl["m"], seed=seed + 4, device=device)
+        a, b, c = wl.get("abc", (0.57, 0.19, 0.19))
+        return I.rmat(wl["scale"], wl["m"], a=a, b=b, c=c, seed=seed + 4, device=device)
     if wl["kind"] == "chunglu":
         return I.chung_lu(wl["n"], wl["beta"], wl["deg"], seed=seed + 2, device=device)
     if wl["kind"] == "sbm":
@@ -405,6 +420,43 @@ def serving_bench(L, count, device):
     return out
 
 
+def density_sweep(L, dev, steps):
+    """The paper's scalability sweep over edge density (Sec. 4): R-MAT with
+    its generator parameters at 2^20 vertices and m = 5n, 50n and n^1.5, one
+    whole modularity run per step; time is linear in m if the throughput per
+    entry stays flat."""
+    import torch
+    out = []
+    for name in ("rmat20_5n", "rmat20_50n", "rmat20_n15"):
+        wl = WORKLOADS[name]
+        g = make_graph(wl, dev)
+        G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+        n, nnz = g["n"], g["nnz"]
+        del g
+        torch.cuda.empty_cache()
+        sched = L.schedule(num_iter=wl["num_iter"], timing=True)
+        L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sched)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            _, _, st = L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sched)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        G.free()
+        out.append({"workload": name, "n": n, "m": nnz // 2, "csr_entries": nnz,
+                    "ms_per_step": round(ms, 3),
+                    "gedges_per_s": round(st["edges_scanned"] / (ms / 1e3) / 1e9, 3),
+                    "edges_scanned": int(st["edges_scanned"]), "levels": int(st["levels"]),
+                    "rounds": int(st["rounds_total"]),
+                    "ms_bestmove": round(st["ms_bestmove"], 3),
+                    "ms_contract": round(st["ms_contract"], 3),
+                    "modularity": modularity(st, wl["q"])})
+    return out
+
+
 # ------------------------------------------------------------------- arms --
 
 def run_reference(args, rank, world, local):
@@ -460,6 +512,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     n, nnz = g["n"], g["nnz"]
+    csr_bytes = (n + 1) * 8 + nnz * (8 if g["w"] is not None else 4)
     stream = torch.cuda.current_stream().cuda_stream
     G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], stream=stream)
     host = None
@@ -471,7 +524,7 @@ def run_ours(args, rank, world, local):
     sched = L.schedule(num_iter=wl["num_iter"], timing=True)
     # degree routing for this GPU and graph, chosen before the timed region
     t_tune = time.perf_counter()
-    warp_max = L.lcc_autotune(G, wl["p"], wl["q"], wl["mode"], args.tuning_cache)
+    tuning = L.lcc_autotune(G, wl["p"], wl["q"], wl["mode"], args.tuning_cache)
     t_tune = time.perf_counter() - t_tune
 
     def step():
@@ -602,14 +655,18 @@ def run_ours(args, rank, world, local):
                        "ms_other": round(statistics.mean(s["ms_other"] for s in stats), 3),
                        "pairs_sorted": stats[-1]["pairs_sorted"],
                        "generation_s": round(t_gen, 2),
-                       "tuning": {"warp_max": warp_max, "autotune_s": round(t_tune, 2),
+                       "tuning": {"warp_max": tuning["warp_max"],
+                                  "fuse_small": tuning["fuse_small"],
+                                  "autotune_s": round(t_tune, 2),
                                   "chosen_by": ("lcc_autotune on this graph before timing "
                                                 "(3 best-move rounds per routing)"
                                                 if not args.tuning_cache else
                                                 "lcc_autotune with the tuning file "
                                                 + args.tuning_cache)},
                        "degree_buckets": degree_shares(host["off"]) if host else None,
-                       "l2": "inputs larger than L2 (CSR ~16.5 GB vs 129 MB L2)",
+                       "l2": ("inputs larger than L2 (CSR %.1f GB vs 129 MB L2)" % (csr_bytes / 1e9)
+                              if csr_bytes > (129 << 20) else
+                              "CSR of %.1f MB fits L2; no flush between steps" % (csr_bytes / 1e6)),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "contraction": contraction, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks}
@@ -629,6 +686,11 @@ def run_ours(args, rank, world, local):
             torch.cuda.synchronize()
             return e0.elapsed_time(e1), st
         line["coin_schedule"] = coin_leg(run_coin, wl)
+    if rank == 0 and args.sweep:
+        try:
+            line["density_sweep"] = density_sweep(L, dev, max(1, min(args.steps, 3)))
+        except Exception as e:  # noqa: BLE001  (an extra leg: reported, never fatal)
+            line["density_sweep"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     try:

@@ -164,6 +164,13 @@ typedef struct lcc_stats {
                                   and labels read once, and the coarse offsets,
                                   neighbours, int64 weights and node weights
                                   written once (compare with ms_contract) */
+  /* Best-Moves calls (each coarsening and each refinement call with at least
+     one round), and those that stopped at num_iter rounds while some vertex
+     still wanted to move.  The paper's run-to-convergence variant (Sec. 4,
+     the ^CON runs) is a schedule whose num_iter is never reached:
+     calls_capped == 0 shows that every call converged. */
+  int64_t calls;
+  int64_t calls_capped;
 } lcc_stats;
 
 typedef struct lcc_graph lcc_graph;
@@ -208,6 +215,33 @@ LCC_API lcc_status lcc_cluster(const lcc_graph *g, int64_t lambda_p, int64_t lam
                        int32_t mode, const lcc_schedule *sched,
                        int32_t *labels_out, int32_t labels_memspace,
                        double *objective_out, lcc_stats *stats_out);
+
+/* One Best-Moves round of a run.  The paper plots the size of V' per round
+ * for its vertex-subset rules (appendix); this is that record. */
+typedef struct lcc_round {
+  int32_t level;   /* depth of the level (0 = the input graph) */
+  int32_t phase;   /* 0: the call that coarsens the level; 1: its refinement
+                      after Flatten (Sec. 3.2.3) */
+  int32_t round;   /* round within that Best-Moves call, from 0 */
+  int32_t pad;
+  int64_t vprime;  /* |V'|: vertices examined by the round (Sec. 3.2.2) */
+  int64_t entries; /* CSR entries scanned: the sum of their degrees */
+  int64_t moved;   /* vertices that moved */
+  int64_t held;    /* vertices whose move the LCC_SCHED_COIN coin held back */
+} lcc_round;
+
+/*
+ * lcc_cluster_trace -- lcc_cluster plus one lcc_round per Best-Moves round,
+ * in the order the rounds ran (coarsening calls on the way down, refinement
+ * calls on the way up).  trace [trace_cap] (host, caller-owned) receives the
+ * first trace_cap records; *trace_len (nullable) the number of rounds run,
+ * which may exceed trace_cap.  The other arguments are those of lcc_cluster.
+ */
+LCC_API lcc_status lcc_cluster_trace(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q,
+                                     int32_t mode, const lcc_schedule *sched,
+                                     int32_t *labels_out, int32_t labels_memspace,
+                                     double *objective_out, lcc_stats *stats_out,
+                                     lcc_round *trace, int64_t trace_cap, int64_t *trace_len);
 
 /*
  * lcc_desired -- one synchronous best-move evaluation (Algorithm 1, the body
@@ -331,7 +365,11 @@ LCC_API lcc_status lcc_cluster_batch(const lcc_graph *const *graphs, int32_t cou
  */
 typedef struct lcc_tuning {
   int32_t warp_max;    /* 32, 64, 128 or 256 (the default) */
-  int32_t reserved[7]; /* zero */
+  int32_t fuse_small;  /* 1 (the default): rows of at most 32 entries of every
+                          graph in one resident launch whose warps take work
+                          units from a device counter; 0: one launch per
+                          bucket of <= 4, 8, 16 and 32 entries */
+  int32_t reserved[6]; /* zero */
 } lcc_tuning;
 
 /* lcc_get_tuning / lcc_set_tuning -- the tuning used by later calls on CUDA

@@ -9,7 +9,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcc.so")
-SOURCES = ["k_round.cu", "k_level.cu", "k_contract.cu", "engine.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["k_round.cu", "k_level.cu", "k_contract.cu", "k_rows.cu", "engine.cu", "api.cu",
+           "noalloc.cu"]
 HEADERS = ["lcc_internal.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -223,6 +223,8 @@ static void fill_stats(const Job &J, const Engine &E, lcc_stats *s, double ms_to
   s->pairs_sorted = E.stats.pairs;
   s->kernel_launches = launches;
   s->bytes_contract_min = E.stats.contract_min_bytes;
+  s->calls = J.calls;
+  s->calls_capped = J.calls_capped;
   for (int i = 0; i < NB && i < 16; ++i) {
     s->ms_bucket[i] = E.stats.ms_bucket[i];
     s->bucket_entries[i] = E.stats.bucket_entries[i];
@@ -230,10 +232,40 @@ static void fill_stats(const Job &J, const Engine &E, lcc_stats *s, double ms_to
   }
 }
 
+static void cluster_one(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, int32_t mode,
+                        const lcc_schedule *sched, int32_t *labels_out, int32_t labels_memspace,
+                        double *objective_out, lcc_stats *stats_out,
+                        std::vector<lcc_round> *trace);
+
 lcc_status lcc_cluster(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, int32_t mode,
                        const lcc_schedule *sched, int32_t *labels_out, int32_t labels_memspace,
                        double *objective_out, lcc_stats *stats_out) {
   API_BEGIN
+  cluster_one(g, lambda_p, lambda_q, mode, sched, labels_out, labels_memspace, objective_out,
+              stats_out, nullptr);
+  API_END
+}
+
+lcc_status lcc_cluster_trace(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q,
+                             int32_t mode, const lcc_schedule *sched, int32_t *labels_out,
+                             int32_t labels_memspace, double *objective_out,
+                             lcc_stats *stats_out, lcc_round *trace, int64_t trace_cap,
+                             int64_t *trace_len) {
+  API_BEGIN
+  if (trace_cap < 0 || (trace_cap > 0 && !trace)) fail(LCC_ERR_INVALID, "bad trace buffer");
+  std::vector<lcc_round> rec;
+  cluster_one(g, lambda_p, lambda_q, mode, sched, labels_out, labels_memspace, objective_out,
+              stats_out, &rec);
+  const int64_t m = std::min<int64_t>(trace_cap, (int64_t)rec.size());
+  if (m > 0) memcpy(trace, rec.data(), m * sizeof(lcc_round));
+  if (trace_len) *trace_len = (int64_t)rec.size();
+  API_END
+}
+
+static void cluster_one(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, int32_t mode,
+                        const lcc_schedule *sched, int32_t *labels_out, int32_t labels_memspace,
+                        double *objective_out, lcc_stats *stats_out,
+                        std::vector<lcc_round> *trace) {
   check_graph(g);
   check_lambda(lambda_p, lambda_q, mode);
   const lcc_schedule sc = check_schedule(sched);
@@ -259,6 +291,7 @@ lcc_status lcc_cluster(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, i
   J.sc = sc;
   J.labels_out = labels_out;
   J.labels_space = labels_memspace;
+  J.trace = trace;
   try {
     E->add_job(&J);
     while (!E->idle()) E->tick();
@@ -280,7 +313,6 @@ lcc_status lcc_cluster(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, i
   if (stats_out) fill_stats(J, *E, stats_out, ms, g_launches.load() - l0, J.nclusters);
   J.lv.clear();
   J.base.reset();
-  API_END
 }
 
 lcc_status lcc_desired(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, int32_t mode,
@@ -366,7 +398,8 @@ static void check_tuning(const lcc_tuning *t) {
   const int w = t->warp_max;
   if (w != 32 && w != 64 && w != 128 && w != 256)
     fail(LCC_ERR_INVALID, "warp_max must be 32, 64, 128 or 256");
-  for (int i = 0; i < 7; ++i)
+  if (t->fuse_small != 0 && t->fuse_small != 1) fail(LCC_ERR_INVALID, "fuse_small must be 0 or 1");
+  for (int i = 0; i < 6; ++i)
     if (t->reserved[i]) fail(LCC_ERR_INVALID, "reserved tuning fields must be zero");
 }
 
@@ -445,10 +478,15 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
       char line[512];
       bool found = false;
       while (!found && fgets(line, sizeof(line), f)) {
+        // "<device name>|<SMs> <warp_max> [<fuse_small>]"
         std::string l(line);
-        const size_t sp = l.rfind(' ');
-        if (sp == std::string::npos || l.compare(0, sp, key) != 0 || sp != key.size()) continue;
-        t.warp_max = atoi(l.c_str() + sp + 1);
+        if (l.size() <= key.size() || l.compare(0, key.size(), key) != 0 || l[key.size()] != ' ')
+          continue;
+        int wm = 0, fs = 1;
+        const int nread = sscanf(l.c_str() + key.size() + 1, "%d %d", &wm, &fs);
+        if (nread < 1) fail(LCC_ERR_INVALID, "malformed tuning line for this device");
+        t.warp_max = wm;
+        t.fuse_small = nread >= 2 ? fs : 1;
         found = true;
       }
       fclose(f);
@@ -463,28 +501,32 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
   const lcc_tuning before = tuning_for(g->dev);
   const int cand[4] = {32, 64, 128, 256};
   double best_ms = 0;
-  int best = T_WARP;
+  lcc_tuning best = before;
+  bool first = true;
   try {
     time_rounds(g, lambda_p, lambda_q, mode, 1);  // first-use costs outside the comparison
-    for (int c : cand) {
-      t.warp_max = c;
-      set_tuning(g->dev, t);
-      const double ms = time_rounds(g, lambda_p, lambda_q, mode, 3);
-      if (c == cand[0] || ms < best_ms) {
-        best_ms = ms;
-        best = c;
+    for (int fs = 0; fs <= 1; ++fs)
+      for (int c : cand) {
+        t.warp_max = c;
+        t.fuse_small = fs;
+        set_tuning(g->dev, t);
+        const double ms = time_rounds(g, lambda_p, lambda_q, mode, 3);
+        if (first || ms < best_ms) {
+          best_ms = ms;
+          best = t;
+          first = false;
+        }
       }
-    }
   } catch (...) {
     set_tuning(g->dev, before);
     throw;
   }
-  t.warp_max = best;
+  t = best;
   set_tuning(g->dev, t);
   if (cache_path) {
     FILE *f = fopen(cache_path, "a");
     if (!f) fail(LCC_ERR_INVALID, std::string("cannot write the tuning file ") + cache_path);
-    fprintf(f, "%s %d\n", key.c_str(), best);
+    fprintf(f, "%s %d %d\n", key.c_str(), t.warp_max, t.fuse_small);
     fclose(f);
   }
   if (out) *out = t;
@@ -656,15 +698,17 @@ struct SJob {
 struct lcc_server {
   lcc_server_cfg cfg;
   int dev = 0;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;      // the engine's stream
+  cudaStream_t st_adm = nullptr;  // copies and validation of arriving graphs
   std::unique_ptr<Engine> eng;
-  std::thread worker;
+  std::thread worker, admitter;
   std::mutex mu;
-  std::condition_variable cv, cv_idle;
+  std::condition_variable cv, cv_adm, cv_idle;
   bool stop = false;
-  std::deque<SJob *> queue;
+  std::deque<SJob *> queue;   // submitted, not yet admitted
+  std::deque<SJob *> loaded;  // admitted and loaded, waiting for the next tick
   std::unordered_map<uint64_t, SJob *> all;
-  std::vector<SJob *> running;
+  std::vector<SJob *> running;  // admitted (loading, loaded or in the engine)
   uint64_t next = 1;
   int64_t resident = 0;
   int64_t c_done = 0, c_ticks = 0, c_peak_bytes = 0, c_peak_jobs = 0, c_rejected = 0;
@@ -679,11 +723,19 @@ static int64_t job_estimate(int64_t n, int64_t nnz, bool weighted) {
   return 2 * csr + n * 64 + nnz * 56 + layout + (1 << 20);
 }
 
-static void finish_job(lcc_server *s, SJob *j, lcc_status st, const std::string &err) {
+// Releases a job's graph without waiting: its memory returns to the pool in
+// the order of the stream it was allocated on, and nothing of the engine
+// uses it any more (the tick that finished the job has completed).
+static void release_graph(SJob *j) {
   if (j->g) {
-    lcc_free_graph(j->g);
+    j->g->store.reset();
+    delete j->g;
     j->g = nullptr;
   }
+}
+
+static void finish_job(lcc_server *s, SJob *j, lcc_status st, const std::string &err) {
+  release_graph(j);
   std::lock_guard<std::mutex> lk(s->mu);
   j->status = st;
   j->err = err;
@@ -694,16 +746,23 @@ static void finish_job(lcc_server *s, SJob *j, lcc_status st, const std::string 
   s->c_done += 1;
   s->pending -= 1;
   s->cv_idle.notify_all();
+  s->cv_adm.notify_all();  // a slot and budget came free
 }
 
-static void server_loop(lcc_server *s) {
+// Admission: takes queued jobs while a slot and the HBM budget allow,
+// copies and validates their graphs on its own stream (overlapping the
+// engine's ticks), and hands them to the worker.
+static void admit_loop(lcc_server *s) {
   cudaSetDevice(s->dev);
-  Engine &E = *s->eng;
   while (true) {
-    std::vector<SJob *> admit;
-    std::vector<SJob *> cancelled;
+    std::vector<SJob *> take;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_adm.wait_for(lk, std::chrono::milliseconds(20), [&] {
+        return s->stop ||
+               (!s->queue.empty() && (int64_t)s->running.size() < s->cfg.max_slots &&
+                s->resident + s->queue.front()->est <= s->cfg.hbm_budget_bytes);
+      });
       if (s->stop) break;
       while (!s->queue.empty() && (int64_t)s->running.size() < s->cfg.max_slots &&
              s->resident + s->queue.front()->est <= s->cfg.hbm_budget_bytes) {
@@ -720,13 +779,47 @@ static void server_loop(lcc_server *s) {
         j->state = S_RUNNING;
         s->running.push_back(j);
         s->resident += j->est;
-        admit.push_back(j);
+        take.push_back(j);
       }
-      for (SJob *j : s->running)
-        if (j->cancel && std::find(admit.begin(), admit.end(), j) == admit.end())
-          cancelled.push_back(j);
       s->c_peak_bytes = std::max(s->c_peak_bytes, s->resident);
       s->c_peak_jobs = std::max(s->c_peak_jobs, (int64_t)s->running.size());
+    }
+    for (SJob *j : take) {
+      try {
+        j->g = load_graph(j->off.data(), j->nbr.data(), j->weighted ? j->w.data() : nullptr, j->n,
+                          j->nnz, nullptr, LCC_MEM_HOST, s->st_adm);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->loaded.push_back(j);
+        s->cv.notify_all();
+      } catch (const Error &e) {
+        finish_job(s, j, e.st, e.what());
+      } catch (const std::exception &e) {
+        finish_job(s, j, LCC_ERR_CUDA, e.what());
+      }
+    }
+  }
+}
+
+static void server_loop(lcc_server *s) {
+  cudaSetDevice(s->dev);
+  Engine &E = *s->eng;
+  while (true) {
+    std::vector<SJob *> admit;
+    std::vector<SJob *> cancelled;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop) break;
+      while (!s->loaded.empty()) {
+        SJob *j = s->loaded.front();
+        s->loaded.pop_front();
+        if (j->cancel)
+          cancelled.push_back(j);
+        else
+          admit.push_back(j);
+      }
+      for (SJob *j : s->running)
+        if (j->cancel && j->job.g && std::find(cancelled.begin(), cancelled.end(), j) == cancelled.end())
+          cancelled.push_back(j);
       if (admit.empty() && cancelled.empty() && E.idle()) {
         s->cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
@@ -736,10 +829,9 @@ static void server_loop(lcc_server *s) {
       E.drop_job(&j->job);
       finish_job(s, j, LCC_ERR_CANCELLED, "cancelled");
     }
-    for (SJob *j : admit) {
-      try {
-        j->g = load_graph(j->off.data(), j->nbr.data(), j->weighted ? j->w.data() : nullptr, j->n,
-                          j->nnz, nullptr, LCC_MEM_HOST, s->st);
+    if (!admit.empty()) {
+      std::vector<Job *> jobs;
+      for (SJob *j : admit) {
         j->labels.resize((size_t)j->n);
         Job &J = j->job;
         J.g = j->g;
@@ -750,13 +842,20 @@ static void server_loop(lcc_server *s) {
         J.labels_out = j->labels.data();
         J.labels_space = LCC_MEM_HOST;
         J.inject_fault_tick = j->inject_fault_tick;
-        E.add_job(&J);
-      } catch (const Error &e) {
-        E.drop_job(&j->job);
-        finish_job(s, j, e.st, e.what());
+        jobs.push_back(&J);
+      }
+      try {
+        // one statistics pass for every newly admitted job; a job whose own
+        // input fails a check comes back alone
+        for (auto &f : E.add_jobs(jobs))
+          for (SJob *j : admit)
+            if (&j->job == f.first) finish_job(s, j, f.second.st, f.second.what());
       } catch (const std::exception &e) {
-        E.drop_job(&j->job);
-        finish_job(s, j, LCC_ERR_CUDA, e.what());
+        const Error *le = dynamic_cast<const Error *>(&e);
+        for (SJob *j : admit) {
+          E.drop_job(&j->job);
+          finish_job(s, j, le ? le->st : LCC_ERR_CUDA, e.what());
+        }
       }
     }
     if (!E.idle()) {
@@ -798,6 +897,7 @@ static void server_loop(lcc_server *s) {
         } else {
           // otherwise the tick's state is unknown: every job in it fails
           for (SJob *j : run) {
+            if (!j->job.g) continue;  // still being loaded: not in the tick
             E.drop_job(&j->job);
             finish_job(s, j, le ? le->st : LCC_ERR_CUDA, e.what());
           }
@@ -820,9 +920,11 @@ lcc_status lcc_server_create(const lcc_server_cfg *cfg, lcc_server **out) {
   s->cfg = *cfg;
   CK(cudaGetDevice(&s->dev));
   CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&s->st_adm, cudaStreamNonBlocking));
   s->eng.reset(new Engine(s->dev, s->st));
   lcc_server *raw = s.get();
   s->worker = std::thread(server_loop, raw);
+  s->admitter = std::thread(admit_loop, raw);
   *out = s.release();
   API_END
 }
@@ -861,7 +963,7 @@ lcc_status lcc_submit(lcc_server *s, const lcc_job *job, uint64_t *ticket) {
     s->queue.push_back(j.release());
     s->pending += 1;
   }
-  s->cv.notify_all();
+  s->cv_adm.notify_all();
   API_END
 }
 
@@ -898,6 +1000,7 @@ lcc_status lcc_cancel(lcc_server *s, uint64_t ticket) {
   if (it == s->all.end()) fail(LCC_ERR_INVALID, "unknown ticket");
   it->second->cancel = true;
   s->cv.notify_all();
+  s->cv_adm.notify_all();
   API_END
 }
 
@@ -931,15 +1034,19 @@ lcc_status lcc_server_destroy(lcc_server *s) {
     s->stop = true;
   }
   s->cv.notify_all();
+  s->cv_adm.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->admitter.joinable()) s->admitter.join();
   cudaSetDevice(s->dev);
   for (SJob *j : s->running) {
     s->eng->drop_job(&j->job);
-    if (j->g) lcc_free_graph(j->g);
+    release_graph(j);
   }
   for (auto &kv : s->all) delete kv.second;
   s->eng.reset();
+  cudaStreamSynchronize(s->st_adm);
   cudaStreamDestroy(s->st);
+  cudaStreamDestroy(s->st_adm);
   delete s;
   API_END
 }

@@ -38,6 +38,18 @@ static int64_t hub_window() {
   return (int64_t)1 << 27;
 }
 
+// Table slots of the longest coarse rows processed per pass of Compress; the
+// LCC_ROW_WINDOW_SLOTS environment variable overrides it (tests use a small
+// window to exercise many passes).
+static int64_t row_window() {
+  const char *e = getenv("LCC_ROW_WINDOW_SLOTS");
+  if (e) {
+    const long long v = atoll(e);
+    if (v >= 1024) return (int64_t)v;
+  }
+  return (int64_t)1 << 27;
+}
+
 // Packed-word bytes above which a level gets a gather layout; the
 // LCC_LAYOUT_MIN_BYTES environment variable overrides it (tests use 0 so that
 // small graphs run through the layout too).
@@ -60,6 +72,7 @@ lcc_tuning tuning_for(int dev) {
   lcc_tuning t;
   memset(&t, 0, sizeof(t));
   t.warp_max = T_WARP;
+  t.fuse_small = 1;
   return t;
 }
 
@@ -305,8 +318,9 @@ void Engine::init_levels(std::vector<Level *> &lvs) {
 
 // ------------------------------------------------------------ add job ----
 
-void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *frontier_host,
-                     bool activate) {
+// Level 0 of a job: its arrays and node weights.  Degree-mode weights are
+// left to the caller (deg collects the job's table entry).
+void Engine::prepare_level0(Job *j, std::vector<LJob> &deg) {
   const lcc_graph *g = j->g;
   j->base = std::make_shared<Store>(st_);
   Level L0;
@@ -319,26 +333,20 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
   const int64_t n = g->n;
   int64_t *k = nullptr;
   if (j->mode == LCC_NODEW_CUSTOM) {
-    if (!g->kc) throw Error(LCC_ERR_INVALID, "LCC_NODEW_CUSTOM needs node weights at load time");
+    if (!g->kc) throw Error(LCC_ERR_INVALID, "LCC_NODEW_CUSTOM needs node weights at load time", j);
     k = g->kc;
-  } else {
+  } else if (j->mode == LCC_NODEW_UNIT || j->mode == LCC_NODEW_DEGREE) {
     k = j->base->alloc<int64_t>(n);
     if (j->mode == LCC_NODEW_UNIT) {
       launch_fill_k_unit(k, n, st_, d_);
       note_launches(1);
-    } else if (j->mode == LCC_NODEW_DEGREE) {
+    } else {
       LJob t = ljob_of(L0);
       t.K = k;  // output of the degree kernel
-      std::vector<LJob> tab(1, t);
-      std::vector<int64_t> vs = {0, n};
-      LJob *dt = s_ljobs_.get<LJob>(1, st_);
-      int64_t *dv = s_vstart_.get<int64_t>(2, st_);
-      upload_table(tab, vs, dt, dv, stage(sizeof(LJob) + 16), st_);
-      launch_degree_k(dt, dv, 1, n, nullptr, st_, d_);
-      note_launches(1);
-    } else {
-      throw Error(LCC_ERR_INVALID, "unknown node-weight mode");
+      deg.push_back(t);
     }
+  } else {
+    throw Error(LCC_ERR_INVALID, "unknown node-weight mode", j);
   }
   L0.k = k;
   L0.L = j->base->alloc<int32_t>(n);
@@ -352,38 +360,66 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
   j->lv.clear();
   j->lv.push_back(L0);
   j->depth = 0;
+}
+
+// Node weights of the degree-mode jobs collected by prepare_level0.
+void Engine::degree_weights(const std::vector<LJob> &deg) {
+  const int nj = (int)deg.size();
+  if (nj == 0) return;
+  std::vector<int64_t> vs(nj + 1, 0);
+  for (int i = 0; i < nj; ++i) vs[i + 1] = vs[i] + deg[i].n;
+  LJob *dt = s_ljobs_.get<LJob>(nj, st_);
+  int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
+  upload_table(deg, vs, dt, dv, stage(nj * (sizeof(LJob) + 8) + 8), st_);
+  launch_degree_k(dt, dv, nj, vs[nj], nullptr, st_, d_);
+  note_launches(1);
+}
+
+// Checks on level 0's statistics: node-weight signs, the modularity scaling
+// of lambda, the range of the exact arithmetic and the integer widths.
+void Engine::check_level0(Job *j) {
+  LevelInfo &I = j->lv[0].info;
+  if (I.pad > 0) throw Error(LCC_ERR_INVALID, "negative node weight (degree) in the input", j);
+  j->ktot = I.ksum;
+  if (j->mode == LCC_NODEW_DEGREE) {
+    if (I.ksum <= 0)
+      throw Error(LCC_ERR_INVALID, "modularity mode needs a positive total weight", j);
+    const i128 qq = (i128)j->q * (i128)I.ksum;
+    if (qq > (i128)INT64_MAX) throw Error(LCC_ERR_OVERFLOW, "q * 2m exceeds int64", j);
+    j->q = (int64_t)qq;
+  }
+  // Range of the exact arithmetic.  A q-scaled gain is q w(v,C) - p k_v K_C
+  // and q CC is q S_in - p (sum K^2 - sum k^2); with k >= 0 the first terms
+  // are at most q * sum|w| and the second at most p * (sum k)^2.  Both
+  // below 2^125 keep every gain, every comparison of two gains and the
+  // objective inside a signed 128-bit integer on every level (coarse levels
+  // keep sum k and never raise sum|w|).
+  const i128 lim = (i128)1 << 125;
+  const i128 kt = (i128)I.ksum, wa = (i128)I.wabs;
+  if (I.ksat || kt >= ((i128)1 << 62) || wa >= ((i128)1 << 62) || (i128)j->q * wa >= lim ||
+      (kt > 0 && (i128)j->p > (lim - 1) / (kt * kt)))
+    throw Error(LCC_ERR_OVERFLOW,
+                "q * sum|w| or p * (sum k)^2 reaches 2^125: outside the exact integer range", j);
+  j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
+  // cluster weights fit the 32-bit half of the packed label word
+  if (j->ktot >= (int64_t)KNONE) j->lv[0].lk = nullptr;
+}
+
+void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *frontier_host,
+                     bool activate) {
+  const int64_t n = j->g->n;
+  {
+    std::vector<LJob> deg;
+    prepare_level0(j, deg);
+    degree_weights(deg);
+  }
   // statistics of level 0 (also gives sum k for the modularity scaling)
   {
     std::vector<Job *> js = {j};
     std::vector<Level *> lvs = {&j->lv[0]};
     j->ktot = 0;
     level_stats(js, lvs);
-    LevelInfo &I = j->lv[0].info;
-    if (I.pad > 0) throw Error(LCC_ERR_INVALID, "negative node weight (degree) in the input");
-    j->ktot = I.ksum;
-    if (j->mode == LCC_NODEW_DEGREE) {
-      if (I.ksum <= 0) throw Error(LCC_ERR_INVALID, "modularity mode needs a positive total weight");
-      const i128 qq = (i128)j->q * (i128)I.ksum;
-      if (qq > (i128)INT64_MAX) throw Error(LCC_ERR_OVERFLOW, "q * 2m exceeds int64");
-      j->q = (int64_t)qq;
-    }
-    // Range of the exact arithmetic.  A q-scaled gain is q w(v,C) - p k_v K_C
-    // and q CC is q S_in - p (sum K^2 - sum k^2); with k >= 0 the first terms
-    // are at most q * sum|w| and the second at most p * (sum k)^2.  Both
-    // below 2^125 keep every gain, every comparison of two gains and the
-    // objective inside a signed 128-bit integer on every level (coarse levels
-    // keep sum k and never raise sum|w|).
-    {
-      const i128 lim = (i128)1 << 125;
-      const i128 kt = (i128)I.ksum, wa = (i128)I.wabs;
-      if (I.ksat || kt >= ((i128)1 << 62) || wa >= ((i128)1 << 62) || (i128)j->q * wa >= lim ||
-          (kt > 0 && (i128)j->p > (lim - 1) / (kt * kt)))
-        throw Error(LCC_ERR_OVERFLOW,
-                    "q * sum|w| or p * (sum k)^2 reaches 2^125: outside the exact integer range");
-    }
-    j->lv[0].wide = needs_wide(j->lv[0], j->p, j->q, j->ktot);
-    // cluster weights fit the 32-bit half of the packed label word
-    if (j->ktot >= (int64_t)KNONE) j->lv[0].lk = nullptr;
+    check_level0(j);
     std::vector<Store *> stores = {j->base.get()};
     build_layout(lvs, stores);
   }
@@ -411,6 +447,55 @@ void Engine::add_job(Job *j, const int32_t *init_labels_host, const uint8_t *fro
   j->round = 0;
   j->moved_level = false;
   if (activate) active_.push_back(j);
+}
+
+std::vector<std::pair<Job *, Error>> Engine::add_jobs(const std::vector<Job *> &in) {
+  std::vector<std::pair<Job *, Error>> failed;
+  auto drop = [&](Job *J, const Error &e) {
+    failed.emplace_back(J, e);
+    J->lv.clear();
+    J->base.reset();
+  };
+  std::vector<Job *> js;
+  std::vector<LJob> deg;
+  for (Job *J : in) {
+    try {
+      prepare_level0(J, deg);
+      js.push_back(J);
+    } catch (const Error &e) {
+      if (!e.job) throw;
+      drop(J, e);
+    }
+  }
+  degree_weights(deg);
+  std::vector<Level *> lvs;
+  for (Job *J : js) {
+    J->ktot = 0;
+    lvs.push_back(&J->lv[0]);
+  }
+  level_stats(js, lvs);
+  std::vector<Job *> ok;
+  std::vector<Level *> oklv;
+  std::vector<Store *> stores;
+  for (Job *J : js) {
+    try {
+      check_level0(J);
+      ok.push_back(J);
+      oklv.push_back(&J->lv[0]);
+      stores.push_back(J->base.get());
+    } catch (const Error &e) {
+      drop(J, e);
+    }
+  }
+  build_layout(oklv, stores);
+  init_levels(oklv);
+  for (Job *J : ok) {
+    J->phase = P_BM;
+    J->round = 0;
+    J->moved_level = false;
+    active_.push_back(J);
+  }
+  return failed;
 }
 
 void Engine::drop_job(Job *j) {
@@ -567,7 +652,8 @@ void Engine::round(std::vector<Job *> &js) {
   launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
   ++launches;
   if (timing) CK(cudaEventRecord(ev_[1], st_));
-  launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr);
+  launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr,
+                  tuning_for(dev_).fuse_small != 0);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_coin) {
     launch_coin(dt, dcoin, b, dheld, st_, d_);
@@ -618,13 +704,30 @@ void Engine::round(std::vector<Job *> &js) {
       end_bm(J);
       continue;
     }
+    if (J->trace && nj == 1) {
+      lcc_round rr;
+      memset(&rr, 0, sizeof(rr));
+      rr.level = J->depth;
+      rr.phase = J->kind == BM_REFINE ? 1 : 0;
+      rr.round = J->round - 1;
+      rr.vprime = hbuf[C_VERTS];
+      rr.entries = hbuf[C_EDGES];
+      rr.moved = mv;
+      rr.held = held;
+      J->trace->push_back(rr);
+    }
     if (mv > 0) {
       J->moved_level = true;
       J->moved_any = true;
     }
     // the call ends when no vertex wants to move: none moved and the coin
-    // held none back
-    if ((mv == 0 && held == 0) || J->round >= J->sc.num_iter) end_bm(J);
+    // held none back (converged), or after num_iter rounds
+    const bool converged = mv == 0 && held == 0;
+    if (converged || J->round >= J->sc.num_iter) {
+      J->calls += 1;
+      if (!converged) J->calls_capped += 1;
+      end_bm(J);
+    }
   }
 }
 
@@ -640,11 +743,10 @@ void Engine::contract(std::vector<Job *> &js) {
   const int nj = (int)js.size();
   if (timing) CK(cudaEventRecord(ev_[4], st_));
   std::vector<CJob> tab(nj);
-  std::vector<int64_t> vs(nj + 1), es(nj + 1);
+  std::vector<int64_t> vs(nj + 1);
   int64_t vt = 0, et = 0, read_min = 0;
   for (int i = 0; i < nj; ++i) {
     Level &L = js[i]->lv[js[i]->depth];
-    es[i] = et;
     et += L.info.nnz;
     // least reads: offsets, neighbours, weights and labels, once each
     const int64_t wb = L.wtype == W_I32 ? 4 : (L.wtype == W_I64 ? 8 : 0);
@@ -664,23 +766,19 @@ void Engine::contract(std::vector<Job *> &js) {
     vt += L.n;
   }
   vs[nj] = vt;
-  es[nj] = et;
   auto store = std::make_shared<Store>(st_);
   int32_t *map_u = store->alloc<int32_t>(vt);
   for (int i = 0; i < nj; ++i) tab[i].map = map_u + vs[i];
 
   Store tmp(st_);
   CJob *dt = tmp.alloc<CJob>(nj);
-  int64_t *dv = tmp.alloc<int64_t>(2 * (nj + 1));
-  int64_t *de = dv + (nj + 1);  // first flat entry of each job
+  int64_t *dv = tmp.alloc<int64_t>(nj + 1);
   {
-    char *h = (char *)stage(nj * sizeof(CJob) + 2 * (nj + 1) * 8);
+    char *h = (char *)stage(nj * sizeof(CJob) + (nj + 1) * 8);
     memcpy(h, tab.data(), nj * sizeof(CJob));
     memcpy(h + nj * sizeof(CJob), vs.data(), (nj + 1) * 8);
-    memcpy(h + nj * sizeof(CJob) + (nj + 1) * 8, es.data(), (nj + 1) * 8);
     CK(cudaMemcpyAsync(dt, h, nj * sizeof(CJob), cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(dv, h + nj * sizeof(CJob), 2 * (nj + 1) * 8, cudaMemcpyHostToDevice,
-                       st_));
+    CK(cudaMemcpyAsync(dv, h + nj * sizeof(CJob), (nj + 1) * 8, cudaMemcpyHostToDevice, st_));
   }
   int64_t *rank = tmp.alloc<int64_t>(vt + 1);
   int32_t *gmap = tmp.alloc<int32_t>(vt);
@@ -704,64 +802,135 @@ void Engine::contract(std::vector<Job *> &js) {
   sync_checked(st_);
   if ((int32_t)hb[2]) throw Error(LCC_ERR_INVALID, "label out of range in Compress");
   const int64_t ntot = hb[0];
-  const int64_t P = et;  // every entry is emitted; those inside clusters sort last
   std::vector<int64_t> nprime(nj), cbase(nj);
-  int64_t nmax = 1;
   for (int i = 0; i < nj; ++i) {
     nprime[i] = hb[3 + 2 * i];
     cbase[i] = hb[3 + 2 * i + 1];
-    nmax = std::max(nmax, nprime[i]);
   }
   if (ntot >= ((int64_t)1 << 31) - 1) throw Error(LCC_ERR_OVERFLOW, "too many coarse vertices");
-
-  // the buffer the sort leaves free is reused for the unique keys (<= P)
-  uint64_t *keys = tmp.alloc<uint64_t>(P);
-  int64_t *vals = tmp.alloc<int64_t>(P);
-  uint64_t *keys2 = tmp.alloc<uint64_t>(P);
-  int64_t *vals2 = tmp.alloc<int64_t>(P);
-  launch_emit_all(dt, dv, de, nj, vt, gmap, gmapp, rank, keys, vals, intra, st_, d_);
   int64_t *knew = store->alloc<int64_t>(ntot);
   launch_knew(dt, dv, nj, vt, rank, knew, st_, d_);
-  note_launches(2);
-  int shifts[16], np = 0;
-  // the high half on bits_for(ntot + 1) bits: no coarse id is all ones there,
-  // so the intra-cluster key (all ones) sorts after every real pair
-  const int lb = bits_for(nmax), hbits = bits_for(ntot + 1);
-  for (int s = 0; s < lb; s += 8) shifts[np++] = s;
-  for (int s = 32; s < 32 + hbits; s += 8) shifts[np++] = s;
-  int64_t *rtmp = tmp.alloc<int64_t>(radix_tmp_elems(P));
-  bool in_alt = false;
-  int lcount = 0;
-  radix_sort_pairs(keys, vals, keys2, vals2, P, shifts, np, rtmp, st_, d_, &in_alt, &lcount);
-  note_launches(lcount);
-  uint64_t *sk = in_alt ? keys2 : keys;
-  int64_t *sv = in_alt ? vals2 : vals;
-  uint64_t *ukeys = (uint64_t *)(in_alt ? vals : vals2);
-  // reduce by key: heads per tile, their scan (first run of each tile; the
-  // total is the number of coarse entries), then keys and sums
-  const int64_t nt = rb_tiles(P);
-  int64_t *toff = tmp.alloc<int64_t>(nt + 1);
-  CK(cudaMemsetAsync(toff + nt, 0, 8, st_));
-  launch_rb_count(sk, P, toff, st_);
-  scan_exclusive_i64(toff, nt, stmp = tmp.alloc<int64_t>(scan_tmp_elems(nt + 1)), st_, d_);
-  note_launches(3);
-  CK(cudaMemcpyAsync(hb, toff + nt, 8, cudaMemcpyDeviceToHost, st_));
-  CK(cudaMemcpyAsync(hb + 1, intra, 8, cudaMemcpyDeviceToHost, st_));
+  note_launches(1);
+
+  // Every coarse row gets a region of the flat entry space as large as the
+  // sum of its members' degrees; each fine vertex appends its entries that
+  // leave its cluster to its coarse row's region.
+  int64_t *boff = tmp.alloc<int64_t>(ntot + 1);
+  int64_t *rcnt = tmp.alloc<int64_t>(ntot);
+  int64_t *stmp2 = tmp.alloc<int64_t>(scan_tmp_elems(ntot + 1));
+  int32_t *tnbr = tmp.alloc<int32_t>(et);
+  int64_t *tw = tmp.alloc<int64_t>(et);
+  int64_t *offg = store->alloc<int64_t>(ntot + 1);
+  CK(cudaMemsetAsync(boff, 0, (ntot + 1) * 8, st_));
+  CK(cudaMemsetAsync(rcnt, 0, ntot * 8, st_));
+  CK(cudaMemsetAsync(offg, 0, (ntot + 1) * 8, st_));
+  launch_rbound(dt, dv, nj, vt, gmap, boff, st_, d_);
+  scan_exclusive_i64(boff, ntot, stmp2, st_, d_);
+  RowSpace R;
+  memset(&R, 0, sizeof(R));
+  R.jobs = dt;
+  R.vstart = dv;
+  R.njobs = nj;
+  R.gmap = gmap;
+  R.gmapp = gmapp;
+  R.rank = rank;
+  R.boff = boff;
+  R.rcnt = rcnt;
+  R.tnbr = tnbr;
+  R.tw = tw;
+  R.ucnt = offg;  // unique entries per row, scanned into the offsets below
+  R.intra = intra;
+  launch_emit_rows(R, vt, st_, d_);
+  // rows by their number of entries
+  unsigned long long *ccnt = tmp.alloc<unsigned long long>(RC_N);
+  int64_t *dseg = tmp.alloc<int64_t>(RC_N);
+  CK(cudaMemsetAsync(ccnt, 0, RC_N * 8, st_));
+  launch_rows_classify(R, ntot, false, ccnt, nullptr, nullptr, st_, d_);
+  note_launches(6);
+  int64_t *hc = (int64_t *)stage2(RC_N * 8);
+  CK(cudaMemcpyAsync(hc, ccnt, RC_N * 8, cudaMemcpyDeviceToHost, st_));
   sync_checked(st_);
-  // the last run holds the intra-cluster entries, if there are any
-  const int64_t Uall = hb[0];
-  const int64_t nintra = hb[1];
-  const int64_t U = Uall - (nintra > 0 ? 1 : 0);
-  stats.pairs += P - nintra;
+  int64_t cnt[RC_N], seg[RC_N], nrows = 0;
+  for (int c = 0; c < RC_N; ++c) {
+    cnt[c] = hc[c];
+    seg[c] = nrows;
+    nrows += cnt[c];
+  }
+  int32_t *items = tmp.alloc<int32_t>(nrows);
+  {
+    int64_t *hs = (int64_t *)stage(RC_N * 8);
+    memcpy(hs, seg, sizeof(seg));
+    CK(cudaMemcpyAsync(dseg, hs, RC_N * 8, cudaMemcpyHostToDevice, st_));
+  }
+  CK(cudaMemsetAsync(ccnt, 0, RC_N * 8, st_));
+  launch_rows_classify(R, ntot, true, ccnt, dseg, items, st_, d_);
+  // each row merges its region in place: unique entries at its start,
+  // their number in offg[C] (rows of one entry were counted by the classes)
+  int launches = 1;
+  launch_rows_small(R, items, seg, cnt, st_, d_, &launches);
+  const int64_t H = cnt[RC_BIG];
+  if (H > 0) {
+    // rows longer than a block's table: global tables, in windows of slots
+    const int32_t *bitems = items + seg[RC_BIG];
+    int64_t *bb = tmp.alloc<int64_t>(H);
+    launch_big_bounds(R, bitems, H, bb, st_, d_);
+    ++launches;
+    int64_t *hbb = (int64_t *)stage2(H * 8);
+    CK(cudaMemcpyAsync(hbb, bb, H * 8, cudaMemcpyDeviceToHost, st_));
+    sync_checked(st_);
+    const std::vector<int64_t> bnd(hbb, hbb + H);
+    std::vector<int64_t> offs(3 * (H + 1));
+    int64_t *to = offs.data(), *uo = to + (H + 1), *so = uo + (H + 1);
+    int64_t maxcap = 0;
+    to[0] = uo[0] = so[0] = 0;
+    for (int64_t h = 0; h < H; ++h) {
+      const int64_t cap = next_pow2(2 * bnd[h]);
+      maxcap = std::max(maxcap, cap);
+      to[h + 1] = to[h] + cap;
+      uo[h + 1] = uo[h] + (bnd[h] + RC_CHUNK - 1) / RC_CHUNK;
+      so[h + 1] = so[h] + (cap + RC_SCHUNK - 1) / RC_SCHUNK;
+    }
+    int64_t *doffs = tmp.alloc<int64_t>(3 * (H + 1));
+    {
+      int64_t *hs = (int64_t *)stage(offs.size() * 8);
+      memcpy(hs, offs.data(), offs.size() * 8);
+      CK(cudaMemcpyAsync(doffs, hs, offs.size() * 8, cudaMemcpyHostToDevice, st_));
+    }
+    const int64_t win = std::min(to[H], row_window());
+    BigRows B;
+    B.keys = tmp.alloc<int32_t>(win + maxcap);
+    B.vals = tmp.alloc<unsigned long long>(win + maxcap);
+    B.tbl_off = doffs;
+    B.unit_off = doffs + (H + 1);
+    B.sunit_off = doffs + 2 * (H + 1);
+    B.H = H;
+    for (int64_t h0 = 0; h0 < H;) {
+      const int64_t lo = to[h0];
+      int64_t h1 = h0 + 1;
+      while (h1 < H && to[h1] < lo + win) ++h1;
+      const int64_t slots = to[h1] - lo;
+      CK(cudaMemsetAsync(B.keys, 0xFF, slots * 4, st_));
+      CK(cudaMemsetAsync(B.vals, 0, slots * 8, st_));
+      launch_big_window(R, bitems, B, h0, h1, lo, uo[h1] - uo[h0], so[h1] - so[h0], st_, d_,
+                        &launches);
+      h0 = h1;
+    }
+  }
+  scan_exclusive_i64(offg, ntot, stmp2, st_, d_);
+  note_launches(launches + 2);
+  int64_t *hu = (int64_t *)stage2(16);
+  CK(cudaMemcpyAsync(hu, offg + ntot, 8, cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(hu + 1, intra, 8, cudaMemcpyDeviceToHost, st_));
+  sync_checked(st_);
+  const int64_t U = hu[0];
+  const int64_t nintra = hu[1];
+  stats.pairs += et - nintra;
   // least writes: coarse offsets, neighbours, int64 weights and node weights
   stats.contract_min_bytes += read_min + (ntot + nj) * 8 + U * (4 + 8) + ntot * 8;
-  int64_t *uvals = store->alloc<int64_t>(Uall);
+  int64_t *uvals = store->alloc<int64_t>(U);
   int32_t *unbr = store->alloc<int32_t>(U);
-  int64_t *offg = store->alloc<int64_t>(ntot + 1);
-  CK(cudaMemsetAsync(uvals, 0, (Uall > 0 ? Uall : 1) * 8, st_));
-  launch_rb_write(sk, sv, P, toff, ukeys, uvals, st_);
-  launch_csr_rows(ukeys, U, ntot, offg, unbr, st_, d_);
-  note_launches(2);
+  launch_rows_copy(R, ntot, offg, unbr, uvals, st_, d_);
+  note_launches(1);
   int32_t *Lu = store->alloc<int32_t>(ntot);
   int64_t *Ku = store->alloc<int64_t>(ntot);
   int32_t *Du = store->alloc<int32_t>(ntot);
@@ -1004,6 +1173,26 @@ void Engine::compress_to_graph(Job *J, int32_t *map_host, lcc_graph **out) {
   if (first != 0) {
     // offsets of a single-job level start at 0; keep the invariant explicit
     throw Error(LCC_ERR_CUDA, "internal: coarse offsets do not start at 0");
+  }
+  if (nnz2 > 1) {
+    // Compress leaves a row's entries in table order; the exported graph has
+    // every row ascending by neighbour: sort (row << 32 | neighbour, w)
+    Store srt(st_);
+    uint64_t *k1 = srt.alloc<uint64_t>(nnz2), *k2 = srt.alloc<uint64_t>(nnz2);
+    int64_t *w2 = srt.alloc<int64_t>(nnz2);
+    int64_t *rt = srt.alloc<int64_t>(radix_tmp_elems(nnz2));
+    launch_row_keys(g->off, n2, g->nbr, k1, st_, d_);
+    int shifts[16], np = 0;
+    const int b = bits_for(n2);
+    for (int sh = 0; sh < b; sh += 8) shifts[np++] = sh;
+    for (int sh = 32; sh < 32 + b; sh += 8) shifts[np++] = sh;
+    bool in_alt = false;
+    int lc = 0;
+    radix_sort_pairs(k1, w, k2, w2, nnz2, shifts, np, rt, st_, d_, &in_alt, &lc);
+    launch_row_unkey(in_alt ? k2 : k1, nnz2, g->nbr, st_, d_);
+    if (in_alt) CK(cudaMemcpyAsync(w, w2, nnz2 * 8, cudaMemcpyDeviceToDevice, st_));
+    note_launches(lc + 2);
+    sync_checked(st_);
   }
   // |w| total of the coarse graph never exceeds the input's
   g->wabs = J->g->wabs;

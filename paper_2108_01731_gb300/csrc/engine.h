@@ -156,6 +156,7 @@ struct Job {
   int64_t den = 1;
   int32_t rounds_total = 0;
   int32_t levels = 1;
+  int64_t calls = 0, calls_capped = 0;  // Best-Moves calls; those ended by num_iter
   // final labels copied here (host or device pointer) when done
   int32_t *labels_out = nullptr;
   int32_t labels_space = LCC_MEM_HOST;
@@ -166,6 +167,8 @@ struct Job {
   // error for this job alone
   int64_t ticks = 0;
   int64_t inject_fault_tick = 0;
+  // per-round record of a job that runs alone (lcc_cluster_trace)
+  std::vector<lcc_round> *trace = nullptr;
 };
 
 struct EngineStats {
@@ -186,6 +189,10 @@ class Engine {
   // adds it to the active set.
   void add_job(Job *j, const int32_t *init_labels_host = nullptr,
                const uint8_t *frontier_host = nullptr, bool activate = true);
+  // Level 0 of several jobs at once (singletons, every job activated), with
+  // one statistics pass for all; a job whose own input fails a check is
+  // returned with its error and not added, the others are.
+  std::vector<std::pair<Job *, Error>> add_jobs(const std::vector<Job *> &js);
   // One step of every active job; returns the jobs that finished.
   std::vector<Job *> tick();
   bool idle() const { return active_.empty(); }
@@ -206,6 +213,9 @@ class Engine {
   void up(std::vector<Job *> &js);
   void finalize(std::vector<Job *> &js);
   void level_stats(std::vector<Job *> &js, std::vector<Level *> &lvs);
+  void prepare_level0(Job *j, std::vector<LJob> &deg);
+  void degree_weights(const std::vector<LJob> &deg);
+  void check_level0(Job *j);
   // Gather layout for the levels (with packed words) that are large enough;
   // its arrays come from stores[i].
   void build_layout(std::vector<Level *> &lvs, std::vector<Store *> &stores);

@@ -1,18 +1,18 @@
-// Compress (Sec. 3.1, Appendix B) as relabel -> emit -> radix sort ->
-// reduce by key -> CSR, over a table of jobs laid out in one flat vertex
-// space (vstart[j] = first flat index of job j).
+// The first steps of Compress (Sec. 3.1, Appendix B) over a table of jobs
+// laid out in one flat vertex space (vstart[j] = first flat index of job j),
+// plus the scan and the radix sort they and the exported graphs use:
 //
 //   occ/rank   occupied cluster ids, exclusive scan -> dense coarse ids in
 //              increasing cluster-id order; rank[vstart_j + c] is the global
 //              coarse id of cluster c of job j;
-//   emit       every entry (u, v) whose ends lie in different clusters gives
-//              key = (global coarse id of u) << 32 | (local coarse id of v)
-//              and value w, at its own entry position; entries inside a
-//              cluster get a key that sorts last and are dropped there;
-//   sort       LSD radix sort, 8-bit digits, only on the bits in use;
-//   reduce     equal keys are summed (parallel edges merged): heads per tile,
-//              a scan of the tile counts, then keys and sums per tile;
-//   CSR        row r starts at the first unique key >= r << 32.
+//   relabel    the global coarse id of every vertex (gmap, and gmapp at the
+//              positions of the gather layout) and its job-local one (map);
+//   knew       the coarse node weights k' = K;
+//   scan       exclusive scan of int64;
+//   sort       LSD radix sort of (key, value) pairs, 8-bit digits, only on
+//              the bits in use (the rows of an exported coarse graph).
+//
+// The aggregation of the coarse rows is in k_rows.cu.
 #include "lcc_internal.cuh"
 
 namespace lcc {
@@ -111,59 +111,6 @@ void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, in
                        cudaStream_t st) {
   if (njobs <= 0) return;
   k_job_counts<<<(njobs + 255) / 256, 256, 0, st>>>(vstart, njobs, rank, out);
-}
-
-// ------------------------------------------------------------- emission --
-
-// Every entry (u, v) of every job is written at its flat entry position
-// estart[j] + (e - off[0]) (a coarse level of a contraction batch indexes a
-// shared entry array, so its offsets need not start at 0):
-// key = (global coarse id of u) << 32 | (local coarse id of v)
-// and value w; an entry inside a cluster gets the key EMIT_INTRA instead,
-// which sorts after every real pair (the sort covers the high half on
-// bits_for(ntot + 1) bits, on which no coarse id is all ones), so the sorted
-// array ends with the intra entries and the reduction stops before them.
-// `intra` counts them.
-__global__ void __launch_bounds__(256) k_emit_all(const CJob *__restrict__ jobs,
-                                                  const int64_t *__restrict__ vstart,
-                                                  const int64_t *__restrict__ estart, int njobs,
-                                                  int64_t vtot, const int32_t *__restrict__ gmap,
-                                                  const int32_t *__restrict__ gmapp,
-                                                  const int64_t *__restrict__ rank, uint64_t *keys,
-                                                  int64_t *vals, unsigned long long *intra) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  long long my_intra = 0;
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
-       i += warps_total) {
-    const int j = find_job(vstart, njobs, i);
-    const CJob *J = jobs + j;
-    const int64_t v = i - vstart[j];
-    const int64_t vs = vstart[j];
-    const int64_t es = estart[j] - J->off[0];
-    const int64_t cbase = rank[vs];
-    const uint64_t cu = (uint64_t)(uint32_t)gmap[i];
-    const int64_t beg = J->off[v], end = J->off[v + 1];
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      const int32_t cv = gmapp[vs + __ldg(J->gnbr + e)];
-      const bool in = (uint32_t)cv == (uint32_t)cu;
-      keys[es + e] = in ? EMIT_INTRA : ((cu << 32) | (uint64_t)(uint32_t)(cv - cbase));
-      vals[es + e] = load_w(J->w, J->wtype, e);
-      my_intra += in ? 1 : 0;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_intra += __shfl_xor_sync(FULL, my_intra, o);
-  if (lane == 0 && my_intra) atomicAdd(intra, (unsigned long long)my_intra);
-}
-
-void launch_emit_all(const CJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
-                     int64_t vtot, const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
-                     uint64_t *keys, int64_t *vals, unsigned long long *intra, cudaStream_t st,
-                     const Dev &d) {
-  if (vtot <= 0) return;
-  k_emit_all<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, estart, njobs, vtot, gmap,
-                                                          gmapp, rank, keys, vals, intra);
 }
 
 // ----------------------------------------------------------------- scan --
@@ -406,159 +353,6 @@ void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t
     int64_t *tv = vi; vi = vo; vo = tv;
   }
   *result_in_alt = (npasses & 1) != 0;
-}
-
-// ---------------------------------------------------- reduce by key ----
-
-// Sorted keys in tiles of RB_TILE (16 rounds of 256 consecutive elements).  A
-// head is the first element of a run of equal keys; run r of the whole array
-// goes to ukeys[r] / uvals[r].
-constexpr int RB_T = 256, RB_I = 16, RB_TILE = RB_T * RB_I, RB_W = RB_T / 32;
-
-__device__ __forceinline__ bool is_head(const uint64_t *__restrict__ keys, int64_t i) {
-  return i == 0 || keys[i] != keys[i - 1];
-}
-
-// Heads per tile (the scan of these gives each tile's first run).
-__global__ void __launch_bounds__(RB_T) k_rb_count(const uint64_t *__restrict__ keys, int64_t n,
-                                                   int64_t *tile_heads) {
-  __shared__ int wsum[RB_W];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t t0 = (int64_t)blockIdx.x * RB_TILE;
-  int c = 0;
-#pragma unroll 4
-  for (int r = 0; r < RB_I; ++r) {
-    const int64_t i = t0 + r * RB_T + tid;
-    c += (i < n && is_head(keys, i)) ? 1 : 0;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-  if (lane == 0) wsum[w] = c;
-  __syncthreads();
-  if (tid == 0) {
-    int t = 0;
-    for (int k = 0; k < RB_W; ++k) t += wsum[k];
-    tile_heads[blockIdx.x] = t;
-  }
-}
-
-// Unique keys and sums.  Heads are ranked in index order from per-(round,
-// warp) ballot counts; values are summed per run inside each 32-element chunk
-// by a segmented warp scan.  A run wholly inside one chunk is stored; parts of
-// runs that cross a chunk are added atomically (uvals is zeroed beforehand).
-__global__ void __launch_bounds__(RB_T) k_rb_write(const uint64_t *__restrict__ keys,
-                                                   const int64_t *__restrict__ vals, int64_t n,
-                                                   const int64_t *__restrict__ tile_off,
-                                                   uint64_t *ukeys, int64_t *uvals) {
-  __shared__ int cnt[RB_I * RB_W];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t t0 = (int64_t)blockIdx.x * RB_TILE;
-  unsigned hmask = 0;
-#pragma unroll
-  for (int r = 0; r < RB_I; ++r) {
-    const int64_t i = t0 + r * RB_T + tid;
-    const bool h = i < n && is_head(keys, i);
-    hmask |= (h ? 1u : 0u) << r;
-    const unsigned b = __ballot_sync(FULL, h);
-    if (lane == 0) cnt[r * RB_W + w] = __popc(b);
-  }
-  __syncthreads();
-  if (w == 0) {  // exclusive prefix of the 128 counts in index order (round, warp)
-    int v[RB_I * RB_W / 32];
-    int tot = 0;
-#pragma unroll
-    for (int k = 0; k < RB_I * RB_W / 32; ++k) {
-      v[k] = cnt[lane * (RB_I * RB_W / 32) + k];
-      tot += v[k];
-    }
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += y;
-    }
-    int run = incl - tot;
-#pragma unroll
-    for (int k = 0; k < RB_I * RB_W / 32; ++k) {
-      cnt[lane * (RB_I * RB_W / 32) + k] = run;
-      run += v[k];
-    }
-  }
-  __syncthreads();
-  const int64_t base = tile_off[blockIdx.x];
-#pragma unroll 2
-  for (int r = 0; r < RB_I; ++r) {
-    const int64_t i = t0 + r * RB_T + tid;
-    const bool valid = i < n;
-    const bool h = (hmask >> r) & 1u;
-    const unsigned b = __ballot_sync(FULL, h);
-    const int64_t before = base + cnt[r * RB_W + w] + __popc(b & lanemask_lt());
-    // run of element i (the previous tile's last run before this tile's first head)
-    const int64_t run = valid ? before + (h ? 1 : 0) - 1 : INT64_MAX;
-    uint64_t key = 0;
-    long long v = 0;
-    if (valid) {
-      key = keys[i];
-      v = vals[i];
-      if (h) ukeys[before] = key;
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(FULL, v, o);
-      const int64_t ry = __shfl_up_sync(FULL, run, o);
-      if (lane >= o && ry == run) v += y;
-    }
-    const int64_t nrun = __shfl_down_sync(FULL, run, 1);
-    const unsigned same = __match_any_sync(FULL, run);
-    if (valid && (lane == 31 || nrun != run)) {  // last element of the run in this chunk
-      const bool starts = (b >> (__ffs(same) - 1)) & 1u;
-      bool ends;
-      if (lane < 31)
-        ends = true;  // the next lane starts another run or lies past the end
-      else
-        ends = i + 1 >= n || keys[i + 1] != key;
-      if (starts && ends)
-        uvals[run] = v;
-      else
-        atomic_add_i64(uvals + run, v);
-    }
-  }
-}
-
-int64_t rb_tiles(int64_t n) { return (n + RB_TILE - 1) / RB_TILE; }
-
-void launch_rb_count(const uint64_t *keys, int64_t n, int64_t *tile_heads, cudaStream_t st) {
-  if (n <= 0) return;
-  k_rb_count<<<(unsigned)rb_tiles(n), RB_T, 0, st>>>(keys, n, tile_heads);
-}
-
-void launch_rb_write(const uint64_t *keys, const int64_t *vals, int64_t n, const int64_t *tile_off,
-                     uint64_t *ukeys, int64_t *uvals, cudaStream_t st) {
-  if (n <= 0) return;
-  k_rb_write<<<(unsigned)rb_tiles(n), RB_T, 0, st>>>(keys, vals, n, tile_off, ukeys, uvals);
-}
-
-
-__global__ void k_csr_rows(const uint64_t *__restrict__ ukeys, int64_t nu, int64_t nrows,
-                           int64_t *offg, int32_t *nbr_out) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows; r += stride) {
-    const uint64_t target = (uint64_t)r << 32;
-    int64_t lo = 0, hi = nu;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (ukeys[mid] < target) lo = mid + 1; else hi = mid;
-    }
-    offg[r] = lo;
-  }
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += stride)
-    nbr_out[u] = (int32_t)(uint32_t)(ukeys[u] & 0xffffffffull);
-}
-
-void launch_csr_rows(const uint64_t *ukeys, int64_t nu, int64_t nrows, int64_t *offg,
-                     int32_t *nbr_out, cudaStream_t st, const Dev &d) {
-  const int64_t work = (nu > nrows + 1) ? nu : nrows + 1;
-  k_csr_rows<<<grid_for(work, 256, d), 256, 0, st>>>(ukeys, nu, nrows, offg, nbr_out);
 }
 
 }  // namespace lcc

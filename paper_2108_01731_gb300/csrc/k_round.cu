@@ -132,12 +132,44 @@ __device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
   return x;
 }
 
+// L2 policies of the best-move loads.  A round streams every CSR entry of
+// V' once (the neighbour ids and weights: read once, evicted first, not kept
+// in L1), while the packed label words are gathered at data-dependent
+// positions over and over; they are kept in L2 in preference to the streams.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *a) {
+  int32_t x;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+      : "=r"(x) : "l"(a), "l"(l2_evict_first()));
+  return x;
+}
+__device__ __forceinline__ int64_t ld_stream(const int64_t *a) {
+  int64_t x;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b64 %0, [%1], %2;"
+      : "=l"(x) : "l"(a), "l"(l2_evict_first()));
+  return x;
+}
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long *a) {
+  unsigned long long x;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(x) : "l"(a), "l"(l2_evict_last()));
+  return x;
+}
+
 // Cluster of neighbour u and, when packed, its weight; `moved` collects the
 // LK_MOVED bit.
 __device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c, uint32_t &k32,
                                          uint32_t &moved) {
   if (J.lk) {
-    const unsigned long long x = __ldg(J.lk + u);
+    const unsigned long long x = ld_keep(J.lk + u);
     moved |= (uint32_t)x & LK_MOVED;
     c = (int32_t)((uint32_t)x & ~LK_MOVED);
     k32 = (uint32_t)(x >> 32);
@@ -148,8 +180,8 @@ __device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c
 }
 
 __device__ __forceinline__ long long weight_at(const JobView &J, int64_t e) {
-  if (J.wtype == W_I32) return (long long)__ldg((const int32_t *)J.w + e);
-  if (J.wtype == W_I64) return (long long)__ldg((const int64_t *)J.w + e);
+  if (J.wtype == W_I32) return (long long)ld_stream((const int32_t *)J.w + e);
+  if (J.wtype == W_I64) return (long long)ld_stream((const int64_t *)J.w + e);
   return 1;
 }
 
@@ -339,6 +371,9 @@ __global__ void __launch_bounds__(FR_T) k_frontier(const JobDev *__restrict__ jo
             my_wb += deg * (J->wtype == W_I32 ? 4 : (J->wtype == W_I64 ? 8 : 0));
           }
         } else {
+          // in V' = V but alone with no neighbour: it keeps its cluster
+          // without an evaluation, and still counts as a member of V'
+          if (J->flags & JF_ALL) my_cnt += 1;
           deg = 0;
         }
       }
@@ -400,86 +435,142 @@ void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64
 
 // ------------------------------------------------ deg <= G: G lanes/vertex --
 
-// Each group of G lanes takes one vertex; lane t reads entry t.  Equal
+// One step of a warp over items [wbase, wbase + 32 / G) of a bucket's list:
+// each group of G lanes takes one vertex and lane t reads entry t.  Equal
 // clusters are found with __match_any_sync on (group, cluster) and summed
-// into the group leader's shared slot; the leaders' scores are then reduced
-// inside the group with xor-shuffles of width G.
+// into the group leader's shared slot (accw: this warp's 32 words); the
+// leaders' scores are then reduced inside the group with xor-shuffles of
+// width G.
+template <int G, typename S>
+__device__ __forceinline__ void group_step(const JobDev *__restrict__ jobs,
+                                           const uint64_t *__restrict__ items, int64_t count,
+                                           int64_t wbase, unsigned long long *accw,
+                                           long long &ncand) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int gsub = lane / G;
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (gsub * G));
+  const int64_t it = wbase + gsub;
+  const bool valid = it < count;
+  const uint64_t item = valid ? items[it] : 0ull;
+  const JobView J = view_of(jobs + (int)(item >> 32));
+  const int32_t v = (int32_t)(uint32_t)item;
+  int64_t beg = 0;
+  int deg = 0;
+  int32_t Lv = 0;
+  int64_t kv = 0;
+  if (valid) {
+    beg = J.off[v];
+    deg = (int)(J.off[v + 1] - beg);
+    Lv = J.L[v];
+    kv = J.k[v];
+  }
+  const bool has = valid && gl < deg;
+  int32_t c = -1;
+  uint32_t k32 = KNONE, mbit = 0;
+  long long wt = 0;
+  if (has) {
+    const int32_t u = ld_stream(J.nbr + beg + gl);
+    wt = weight_at(J, beg + gl);
+    label_of(J, u, c, k32, mbit);
+  }
+  const bool row_moved = (__ballot_sync(FULL, mbit != 0) & gmask) != 0;
+  const unsigned long long key = ((unsigned long long)gsub << 32) | (uint32_t)c;
+  const unsigned peers = __match_any_sync(FULL, key);
+  const int leader = __ffs(peers) - 1;
+  long long wsum = wt;
+  if (!__all_sync(FULL, !has || __popc(peers) == 1)) {
+    accw[lane] = 0;
+    __syncwarp();
+    if (has) atomicAdd(&accw[leader], (unsigned long long)wt);
+    __syncwarp();
+    wsum = (long long)accw[lane];
+    __syncwarp();
+  }
+  const bool lead = has && lane == leader;
+  const bool is_stay = lead && c == Lv;
+  const unsigned sb = __ballot_sync(FULL, is_stay) & gmask;
+  long long w_stay = __shfl_sync(FULL, wsum, sb ? (__ffs(sb) - 1) : lane);
+  if (!sb) w_stay = 0;
+  const bool v_seen = (__ballot_sync(FULL, lead && c == v) & gmask) != 0;
+  const bool cand = lead && !is_stay;
+  S score = ScoreOps<S>::lowest();
+  int32_t cid = INT32_MAX;
+  if (cand) {
+    score = score_of<S>(J, kv, wsum, c, k32);
+    cid = c;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const S os = ScoreOps<S>::shfl_xor(score, o, G);
+    const int32_t oc = __shfl_xor_sync(FULL, cid, o, G);
+    if (better<S>(os, oc, score, cid)) { score = os; cid = oc; }
+  }
+  if (valid && gl == 0)
+    write_desired<S>(J, v, deg, Lv, kv, own_weight(J, v, Lv), score, cid, w_stay, v_seen,
+                     row_moved);
+  ncand += __popc(__ballot_sync(FULL, cand));
+}
+
 template <int G, typename S>
 __global__ void __launch_bounds__(256) k_bm_group(const JobDev *__restrict__ jobs, Buckets b,
                                                   int bk, int64_t *ctr) {
   __shared__ unsigned long long acc[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gl = lane & (G - 1);
-  const int gsub = lane / G;
   constexpr int GPW = 32 / G;
-  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (gsub * G));
   const int64_t count = seg_count(b, bk);
   const uint64_t *items = b.items + b.seg_start[bk];
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   long long ncand = 0;
   PullCount::init();
-  for (int64_t wbase = gw * GPW; wbase < count; wbase += warps_total * GPW) {
-    const int64_t it = wbase + gsub;
-    const bool valid = it < count;
-    const uint64_t item = valid ? items[it] : 0ull;
-    const JobView J = view_of(jobs + (int)(item >> 32));
-    const int32_t v = (int32_t)(uint32_t)item;
-    int64_t beg = 0;
-    int deg = 0;
-    int32_t Lv = 0;
-    int64_t kv = 0;
-    if (valid) {
-      beg = J.off[v];
-      deg = (int)(J.off[v + 1] - beg);
-      Lv = J.L[v];
-      kv = J.k[v];
-    }
-    const bool has = valid && gl < deg;
-    int32_t c = -1;
-    uint32_t k32 = KNONE, mbit = 0;
-    long long wt = 0;
-    if (has) {
-      const int32_t u = __ldg(J.nbr + beg + gl);
-      wt = weight_at(J, beg + gl);
-      label_of(J, u, c, k32, mbit);
-    }
-    const bool row_moved = (__ballot_sync(FULL, mbit != 0) & gmask) != 0;
-    const unsigned long long key = ((unsigned long long)gsub << 32) | (uint32_t)c;
-    const unsigned peers = __match_any_sync(FULL, key);
-    const int leader = __ffs(peers) - 1;
-    long long wsum = wt;
-    if (!__all_sync(FULL, !has || __popc(peers) == 1)) {
-      acc[wib][lane] = 0;
-      __syncwarp();
-      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)wt);
-      __syncwarp();
-      wsum = (long long)acc[wib][lane];
-      __syncwarp();
-    }
-    const bool lead = has && lane == leader;
-    const bool is_stay = lead && c == Lv;
-    const unsigned sb = __ballot_sync(FULL, is_stay) & gmask;
-    long long w_stay = __shfl_sync(FULL, wsum, sb ? (__ffs(sb) - 1) : lane);
-    if (!sb) w_stay = 0;
-    const bool v_seen = (__ballot_sync(FULL, lead && c == v) & gmask) != 0;
-    const bool cand = lead && !is_stay;
-    S score = ScoreOps<S>::lowest();
-    int32_t cid = INT32_MAX;
-    if (cand) {
-      score = score_of<S>(J, kv, wsum, c, k32);
-      cid = c;
-    }
+  for (int64_t wbase = gw * GPW; wbase < count; wbase += warps_total * GPW)
+    group_step<G, S>(jobs, items, count, wbase, acc[wib], ncand);
+  if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
+  PullCount::flush(ctr);
+}
+
+// Every row of at most 32 entries of every job in one resident launch: the
+// four lane-group buckets (<= 4, 8, 16, 32 entries) are cut into warp-sized
+// units (32 / G vertices each), and each warp takes the next unit from a
+// device counter until all are done.  Units are handed out in bucket order,
+// so warps that finish early move on to the next bucket's rows instead of
+// waiting for a launch boundary, and the number of warps does not depend on
+// the size of any one bucket or graph.
+template <typename S>
+__global__ void __launch_bounds__(256) k_bm_small(const JobDev *__restrict__ jobs, Buckets b,
+                                                  int64_t *ctr) {
+  __shared__ unsigned long long acc[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int64_t cnt[4], ends[4];
+  int64_t tot = 0;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const S os = ScoreOps<S>::shfl_xor(score, o, G);
-      const int32_t oc = __shfl_xor_sync(FULL, cid, o, G);
-      if (better<S>(os, oc, score, cid)) { score = os; cid = oc; }
+  for (int i = 0; i < 4; ++i) {
+    cnt[i] = seg_count(b, B_G4 + i);
+    const int gpw = 8 >> i;  // 32 / G for G = 4, 8, 16, 32
+    tot += (cnt[i] + gpw - 1) / gpw;
+    ends[i] = tot;
+  }
+  long long ncand = 0;
+  PullCount::init();
+  while (true) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd((unsigned long long *)&ctr[C_WORK], 1ull);
+    u = __shfl_sync(FULL, u, 0);
+    if ((int64_t)u >= tot) break;
+    const int64_t x = (int64_t)u;
+    if (x < ends[0]) {
+      group_step<4, S>(jobs, b.items + b.seg_start[B_G4], cnt[0], x * 8, acc[wib], ncand);
+    } else if (x < ends[1]) {
+      group_step<8, S>(jobs, b.items + b.seg_start[B_G8], cnt[1], (x - ends[0]) * 4, acc[wib],
+                       ncand);
+    } else if (x < ends[2]) {
+      group_step<16, S>(jobs, b.items + b.seg_start[B_G16], cnt[2], (x - ends[1]) * 2,
+                        acc[wib], ncand);
+    } else {
+      group_step<32, S>(jobs, b.items + b.seg_start[B_G32], cnt[3], x - ends[2], acc[wib],
+                        ncand);
     }
-    if (valid && gl == 0)
-      write_desired<S>(J, v, deg, Lv, kv, own_weight(J, v, Lv), score, cid, w_stay, v_seen,
-                       row_moved);
-    ncand += __popc(__ballot_sync(FULL, cand));
   }
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
   PullCount::flush(ctr);
@@ -508,7 +599,7 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
     u[i] = -1;
     x.w[i] = 0;
     if (e < hi) {
-      u[i] = __ldg(J.nbr + beg + e);
+      u[i] = ld_stream(J.nbr + beg + e);
       x.w[i] = weight_at(J, beg + e);
     }
   }
@@ -1164,8 +1255,9 @@ void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream
 }
 
 template <typename S>
-void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d, int *launches,
-                   cudaEvent_t *ev) {
+void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes,
+                   int64_t *ctr, cudaStream_t st, const Dev &d, int *launches, cudaEvent_t *ev,
+                   bool fuse_small) {
   auto mark = [&](int bk) {
     if (ev) cudaEventRecord(ev[bk], st);
   };
@@ -1177,6 +1269,7 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
     occ[2] = occ_blocks(k_bm_group<16, S>, 256, 0);
     occ[3] = occ_blocks(k_bm_group<32, S>, 256, 0);
+    occ[9] = occ_blocks(k_bm_small<S>, 256, 0);
     occ[7] = occ_blocks(k_bm_warp<S, 2, B_W64>, 128, 0);
     occ[8] = occ_blocks(k_bm_warp<S, 4, B_W128>, 128, 0);
     occ[5] = occ_blocks(k_hub_insert, 256, 0);
@@ -1189,26 +1282,41 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     if (need < g) g = need;
     return (int)(g > 0 ? g : 1);
   };
-  if (b.seg_cap[B_G4] > 0) {
-    k_bm_group<4, S><<<grid(B_G4, occ[0], 64), 256, 0, st>>>(jobs, b, B_G4, ctr);
-    ++*launches;
+  if (fuse_small) {
+    // one resident launch for the four lane-group buckets, timed as <= 32
+    const int64_t small = b.seg_cap[B_G4] + b.seg_cap[B_G8] + b.seg_cap[B_G16] + b.seg_cap[B_G32];
+    mark(B_G4);
+    mark(B_G8);
+    mark(B_G16);
+    if (small > 0) {
+      int64_t g = (small + 63) / 64;
+      if (g > (int64_t)d.sms * occ[9]) g = (int64_t)d.sms * occ[9];
+      k_bm_small<S><<<(int)g, 256, 0, st>>>(jobs, b, ctr);
+      ++*launches;
+    }
+    mark(B_G32);
+  } else {
+    if (b.seg_cap[B_G4] > 0) {
+      k_bm_group<4, S><<<grid(B_G4, occ[0], 64), 256, 0, st>>>(jobs, b, B_G4, ctr);
+      ++*launches;
+    }
+    mark(B_G4);
+    if (b.seg_cap[B_G8] > 0) {
+      k_bm_group<8, S><<<grid(B_G8, occ[1], 32), 256, 0, st>>>(jobs, b, B_G8, ctr);
+      ++*launches;
+    }
+    mark(B_G8);
+    if (b.seg_cap[B_G16] > 0) {
+      k_bm_group<16, S><<<grid(B_G16, occ[2], 16), 256, 0, st>>>(jobs, b, B_G16, ctr);
+      ++*launches;
+    }
+    mark(B_G16);
+    if (b.seg_cap[B_G32] > 0) {
+      k_bm_group<32, S><<<grid(B_G32, occ[3], 8), 256, 0, st>>>(jobs, b, B_G32, ctr);
+      ++*launches;
+    }
+    mark(B_G32);
   }
-  mark(B_G4);
-  if (b.seg_cap[B_G8] > 0) {
-    k_bm_group<8, S><<<grid(B_G8, occ[1], 32), 256, 0, st>>>(jobs, b, B_G8, ctr);
-    ++*launches;
-  }
-  mark(B_G8);
-  if (b.seg_cap[B_G16] > 0) {
-    k_bm_group<16, S><<<grid(B_G16, occ[2], 16), 256, 0, st>>>(jobs, b, B_G16, ctr);
-    ++*launches;
-  }
-  mark(B_G16);
-  if (b.seg_cap[B_G32] > 0) {
-    k_bm_group<32, S><<<grid(B_G32, occ[3], 8), 256, 0, st>>>(jobs, b, B_G32, ctr);
-    ++*launches;
-  }
-  mark(B_G32);
   if (b.seg_cap[B_W64] > 0) {
     k_bm_warp<S, 2, B_W64><<<grid(B_W64, occ[7], 4), 128, 0, st>>>(jobs, b, ctr);
     ++*launches;
@@ -1263,11 +1371,11 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev) {
+                     int *launches, cudaEvent_t *ev, bool fuse_small) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev);
+    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small);
   else
-    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev);
+    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small);
 }
 
 // --------------------------------------------------------------- apply ----

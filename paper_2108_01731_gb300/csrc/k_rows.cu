@@ -1,0 +1,632 @@
+// Compress (Sec. 3.1, Appendix B) by rows: the entries of every coarse
+// vertex C are gathered into one region, the entries that stay inside C are
+// dropped, and parallel edges (equal coarse neighbour) are merged by summing
+// their weights in a hash table.  This is the paper's parallel aggregation of
+// edges by endpoint clusters, done per coarse row, with no global sort.
+//
+//   bound    rbound[C] = sum of the degrees of C's members; its scan gives
+//            each coarse row a region [boff[C], boff[C+1]) of the flat entry
+//            space, large enough for all of its entries;
+//   emit     one warp per fine vertex u reads its row (coalesced), looks up
+//            every neighbour's coarse id and appends the entries that leave
+//            C = coarse(u) to C's region (one atomic per 32 entries on the
+//            row's fill count rcnt[C]);
+//   classes  rows by rcnt: a single entry is already final; G lanes per row
+//            (<= 4 .. 32 entries), a warp with a shared table (<= 256), a
+//            block with a shared table (<= 4096), global tables in bounded
+//            windows (more);
+//   reduce   every row merges its region in place: its unique entries are
+//            written back to the start of the region, their number to
+//            ucnt[C]; a scan of ucnt gives the coarse offsets and the rows
+//            are copied into place.
+//
+// The order of a coarse row's entries is not fixed (arrival and table
+// order): no result depends on it, because every sum is an exact integer and
+// ties between clusters go to the smallest id.  The exported graph of
+// lcc_compress sorts its rows.
+#include "lcc_internal.cuh"
+
+namespace lcc {
+
+namespace {
+constexpr unsigned FULL = 0xffffffffu;
+
+int grid_of(int64_t work, int threads, const Dev &d, int per_sm = 8) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t mx = (int64_t)d.sms * per_sm;
+  if (g > mx) g = mx;
+  return (int)(g > 0 ? g : 1);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Home slot of a coarse id in a power-of-two table of 2^lg slots.
+__device__ __forceinline__ uint32_t row_home(int32_t c, int lg) {
+  return (uint32_t)(((uint64_t)(uint32_t)c * 0x9E3779B97F4A7C15ull) >> (64 - lg));
+}
+
+__device__ __forceinline__ int lg_of(int64_t pow2) { return 63 - __clzll((long long)pow2); }
+
+// One coarse row: its region and its number of entries there.
+struct Row {
+  int64_t rb;    // first entry of the region (and of its unique entries)
+  int64_t cnt;   // entries in the region
+  int32_t C;     // global coarse id
+};
+
+__device__ __forceinline__ Row row_of(const RowSpace &R, int32_t C) {
+  Row r;
+  r.C = C;
+  r.rb = R.boff[C];
+  r.cnt = R.rcnt[C];
+  return r;
+}
+
+__device__ __forceinline__ long long warp_sum(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+}  // namespace
+
+// ------------------------------------------------------- bound, emit ----
+
+__global__ void k_rbound(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
+                         int njobs, int64_t vt, const int32_t *__restrict__ gmap,
+                         int64_t *rbound) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = find_job(vstart, njobs, i);
+    const CJob *J = jobs + j;
+    const int64_t v = i - vstart[j];
+    const int64_t deg = J->off[v + 1] - J->off[v];
+    if (deg) atomicAdd((unsigned long long *)&rbound[gmap[i]], (unsigned long long)deg);
+  }
+}
+
+void launch_rbound(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vt,
+                   const int32_t *gmap, int64_t *rbound, cudaStream_t st, const Dev &d) {
+  if (vt <= 0) return;
+  k_rbound<<<grid_of(vt, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vt, gmap, rbound);
+}
+
+// One warp per fine vertex u of coarse row C: every entry whose far end lies
+// in another coarse vertex is appended to C's region as (local coarse id of
+// the far end, w).  32 entries at a time, with one atomic on rcnt[C].
+__global__ void __launch_bounds__(256) k_emit_rows(RowSpace R, int64_t vt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  long long nintra = 0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < vt;
+       i += warps_total) {
+    const int j = find_job(R.vstart, R.njobs, i);
+    const CJob *J = R.jobs + j;
+    const int64_t v = i - R.vstart[j];
+    const int64_t vs = R.vstart[j];
+    const int32_t C = R.gmap[i];
+    const int32_t cbase = (int32_t)R.rank[vs];
+    const int64_t beg = J->off[v], end = J->off[v + 1];
+    if (beg == end) continue;
+    const int64_t rb = R.boff[C];
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      int32_t cv = -1;
+      long long w = 0;
+      if (e < end) {
+        cv = R.gmapp[vs + __ldg(J->gnbr + e)];
+        w = load_w(J->w, J->wtype, e);
+      }
+      const bool inter = e < end && cv != C;
+      nintra += (e < end && !inter) ? 1 : 0;
+      const unsigned b = __ballot_sync(FULL, inter);
+      if (!b) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd((unsigned long long *)&R.rcnt[C], (unsigned long long)__popc(b));
+      base = __shfl_sync(FULL, base, 0);
+      if (inter) {
+        const int64_t pos = rb + (int64_t)base + __popc(b & lanemask_lt());
+        R.tnbr[pos] = cv - cbase;
+        R.tw[pos] = w;
+      }
+    }
+  }
+  nintra = warp_sum(nintra);
+  if (lane == 0 && nintra) atomicAdd(R.intra, (unsigned long long)nintra);
+}
+
+void launch_emit_rows(const RowSpace &R, int64_t vt, cudaStream_t st, const Dev &d) {
+  if (vt <= 0) return;
+  k_emit_rows<<<grid_of(vt * 32, 256, d), 256, 0, st>>>(R, vt);
+}
+
+// ------------------------------------------------------------ classes ----
+
+__device__ __forceinline__ int row_class(int64_t cnt) {
+  if (cnt <= 1) return -1;  // nothing to merge
+  if (cnt <= 4) return RC_G4;
+  if (cnt <= 8) return RC_G8;
+  if (cnt <= 16) return RC_G16;
+  if (cnt <= 32) return RC_G32;
+  if (cnt <= RC_WARP_MAX) return RC_WARP;
+  if (cnt <= RC_BLOCK_MAX) return RC_BLOCK;
+  return RC_BIG;
+}
+
+// fill = false: rows per class into cnt[]; fill = true: the rows of class c
+// into items[seg[c] ..] (cnt[] then serves as the cursors, zeroed first), and
+// a row of one entry gets ucnt = 1 (it is already in place).
+__global__ void __launch_bounds__(256) k_rows_classify(RowSpace R, int64_t ntot, bool fill,
+                                                       unsigned long long *cnt,
+                                                       const int64_t *__restrict__ seg,
+                                                       int32_t *items) {
+  __shared__ unsigned long long s_cnt[RC_N];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < RC_N) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ntot;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t C = base + threadIdx.x;
+    const int64_t rc = C < ntot ? R.rcnt[C] : 0;
+    const int cls = row_class(rc);
+    if (fill && rc == 1) R.ucnt[C] = 1;
+    const unsigned peers = __match_any_sync(FULL, cls);
+    const int leader = __ffs(peers) - 1;
+    if (cls >= 0) {
+      if (!fill) {
+        if (lane == leader) atomicAdd(&s_cnt[cls], (unsigned long long)__popc(peers));
+      } else {
+        unsigned long long p0 = 0;
+        if (lane == leader) p0 = atomicAdd(&cnt[cls], (unsigned long long)__popc(peers));
+        p0 = __shfl_sync(peers, p0, leader);
+        items[seg[cls] + (int64_t)p0 + __popc(peers & lanemask_lt())] = (int32_t)C;
+      }
+    }
+  }
+  if (!fill) {
+    __syncthreads();
+    if (threadIdx.x < RC_N && s_cnt[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], s_cnt[threadIdx.x]);
+  }
+}
+
+void launch_rows_classify(const RowSpace &R, int64_t ntot, bool fill, unsigned long long *cnt,
+                          const int64_t *seg, int32_t *items, cudaStream_t st, const Dev &d) {
+  if (ntot <= 0) return;
+  k_rows_classify<<<grid_of(ntot, 256, d), 256, 0, st>>>(R, ntot, fill, cnt, seg, items);
+}
+
+// -------------------------------------------- rows of <= 32: G lanes each --
+
+// G lanes per row, lane t reads entry t.  Equal coarse neighbours are found
+// with __match_any_sync on (group, id) and summed into the first lane's
+// shared slot; the first lane of each id writes it.
+template <int G>
+__global__ void __launch_bounds__(256) k_rows_group(RowSpace R, const int32_t *__restrict__ items,
+                                                    int64_t count) {
+  __shared__ unsigned long long acc[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gl = lane & (G - 1), gsub = lane / G;
+  constexpr int GPW = 32 / G;
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (gsub * G));
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW; wbase < count;
+       wbase += warps_total * GPW) {
+    const int64_t it = wbase + gsub;
+    const bool valid = it < count;
+    Row r;
+    r.cnt = 0;
+    r.rb = 0;
+    r.C = 0;
+    if (valid) r = row_of(R, items[it]);
+    const bool has = valid && gl < r.cnt;
+    int32_t cv = -1;
+    long long w = 0;
+    if (has) {
+      cv = R.tnbr[r.rb + gl];
+      w = R.tw[r.rb + gl];
+    }
+    // every lane holds its entry before any lane writes the row back
+    const unsigned long long key =
+        ((unsigned long long)gsub << 32) | (uint32_t)(has ? cv : -1 - gl);
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int leader = __ffs(peers) - 1;
+    long long wsum = w;
+    if (!__all_sync(FULL, !has || __popc(peers) == 1)) {
+      acc[wib][lane] = 0;
+      __syncwarp();
+      if (has) atomicAdd(&acc[wib][leader], (unsigned long long)w);
+      __syncwarp();
+      wsum = (long long)acc[wib][lane];
+      __syncwarp();
+    }
+    const bool lead = has && lane == leader;
+    const unsigned lb = __ballot_sync(FULL, lead) & gmask;
+    if (lead) {
+      const int pos = __popc(lb & lanemask_lt());
+      R.tnbr[r.rb + pos] = cv;
+      R.tw[r.rb + pos] = wsum;
+    }
+    if (valid && gl == 0) R.ucnt[r.C] = __popc(lb);
+  }
+}
+
+// ------------------------------------ rows of <= 256: warp + shared table --
+
+// Inserts (cv, w) into a power-of-two table of cap slots (keys -1 = empty).
+// The table has at least two slots per entry, so a slot is always found.
+__device__ __forceinline__ void table_add(int32_t *keys, unsigned long long *vals, int lg,
+                                          int32_t cv, long long w) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t s = row_home(cv, lg);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    const int32_t prev = atomicCAS(keys + s, -1, cv);
+    if (prev == -1 || prev == cv) {
+      atomicAdd(vals + s, (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(128) k_rows_warp(RowSpace R, const int32_t *__restrict__ items,
+                                                   int64_t count) {
+  constexpr int WPB = 4, CAP = 64 * E;
+  __shared__ int32_t tkey[WPB][CAP];
+  __shared__ unsigned long long tval[WPB][CAP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t *K0 = tkey[wib];
+  unsigned long long *V0 = tval[wib];
+  for (int s = lane; s < CAP; s += 32) {
+    K0[s] = -1;
+    V0[s] = 0;
+  }
+  __syncwarp();
+  for (int64_t it = (int64_t)blockIdx.x * WPB + wib; it < count; it += (int64_t)gridDim.x * WPB) {
+    const Row r = row_of(R, items[it]);
+    const int64_t cap = next_pow2(2 * r.cnt);
+    const int lg = lg_of(cap);
+    int32_t cv[E];
+    long long w[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {  // every load first, then the inserts
+      cv[i] = -1;
+      w[i] = 0;
+      const int64_t t = lane + 32 * i;
+      if (t < r.cnt) {
+        cv[i] = R.tnbr[r.rb + t];
+        w[i] = R.tw[r.rb + t];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (cv[i] >= 0) table_add(K0, V0, lg, cv[i], w[i]);
+    __syncwarp();
+    int base = 0;
+    for (int s0 = 0; s0 < (int)cap; s0 += 32) {
+      const int s = s0 + lane;
+      const int32_t key = K0[s];
+      const bool occ = key >= 0;
+      const unsigned b = __ballot_sync(FULL, occ);
+      if (occ) {
+        const int64_t pos = r.rb + base + __popc(b & lanemask_lt());
+        R.tnbr[pos] = key;
+        R.tw[pos] = (int64_t)V0[s];
+        K0[s] = -1;
+        V0[s] = 0;
+      }
+      base += __popc(b);
+    }
+    if (lane == 0) R.ucnt[r.C] = base;
+    __syncwarp();
+  }
+}
+
+// ----------------------------------- rows of <= 4096: block + shared table --
+
+constexpr int RB_THREADS = 512, RB_E = RC_BLOCK_MAX / RB_THREADS;
+constexpr int RB_CAP = 2 * RC_BLOCK_MAX;
+
+__global__ void __launch_bounds__(RB_THREADS) k_rows_block(RowSpace R,
+                                                           const int32_t *__restrict__ items,
+                                                           int64_t count) {
+  extern __shared__ __align__(16) unsigned char rb_smem[];
+  unsigned long long *tval = (unsigned long long *)rb_smem;
+  int32_t *tkey = (int32_t *)(tval + RB_CAP);
+  __shared__ int s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int s = tid; s < RB_CAP; s += RB_THREADS) {
+    tkey[s] = -1;
+    tval[s] = 0;
+  }
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+    const Row r = row_of(R, items[it]);
+    const int64_t cap = next_pow2(2 * r.cnt);
+    const int lg = lg_of(cap);
+    int32_t cv[RB_E];
+    long long w[RB_E];
+#pragma unroll
+    for (int i = 0; i < RB_E; ++i) {
+      cv[i] = -1;
+      w[i] = 0;
+      const int64_t t = tid + (int64_t)RB_THREADS * i;
+      if (t < r.cnt) {
+        cv[i] = R.tnbr[r.rb + t];
+        w[i] = R.tw[r.rb + t];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RB_E; ++i)
+      if (cv[i] >= 0) table_add(tkey, tval, lg, cv[i], w[i]);
+    __syncthreads();  // every entry is read and inserted before the row is rewritten
+    for (int s0 = 0; s0 < (int)cap; s0 += RB_THREADS) {
+      const int s = s0 + tid;
+      const bool occ = s < (int)cap && tkey[s] >= 0;
+      const unsigned b = __ballot_sync(FULL, occ);
+      int wbase = 0;
+      if (lane == 0 && b) wbase = atomicAdd(&s_cnt, __popc(b));
+      wbase = __shfl_sync(FULL, wbase, 0);
+      if (occ) {
+        const int64_t pos = r.rb + wbase + __popc(b & lanemask_lt());
+        R.tnbr[pos] = tkey[s];
+        R.tw[pos] = (int64_t)tval[s];
+        tkey[s] = -1;
+        tval[s] = 0;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      R.ucnt[r.C] = s_cnt;
+      s_cnt = 0;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_rows_small(const RowSpace &R, const int32_t *items, const int64_t *seg,
+                       const int64_t *cnt, cudaStream_t st, const Dev &d, int *launches) {
+  static int occ_b = 0;
+  if (!occ_b) {
+    const int smem = RB_CAP * 12;
+    cudaFuncSetAttribute(k_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rows_block, RB_THREADS, smem);
+    occ_b = nb > 0 ? nb : 1;
+  }
+  auto groups = [&](int c, int G, auto kern) {
+    if (cnt[c] <= 0) return;
+    const int64_t warps = (cnt[c] * G + 31) / 32;
+    int64_t blocks = (warps + 7) / 8;
+    if (blocks > (int64_t)d.sms * 8) blocks = (int64_t)d.sms * 8;
+    kern<<<(int)blocks, 256, 0, st>>>(R, items + seg[c], cnt[c]);
+    ++*launches;
+  };
+  groups(RC_G4, 4, k_rows_group<4>);
+  groups(RC_G8, 8, k_rows_group<8>);
+  groups(RC_G16, 16, k_rows_group<16>);
+  groups(RC_G32, 32, k_rows_group<32>);
+  if (cnt[RC_WARP] > 0) {
+    int64_t blocks = (cnt[RC_WARP] + 3) / 4;
+    if (blocks > (int64_t)d.sms * 10) blocks = (int64_t)d.sms * 10;
+    k_rows_warp<RC_WARP_MAX / 32><<<(int)blocks, 128, 0, st>>>(R, items + seg[RC_WARP],
+                                                                 cnt[RC_WARP]);
+    ++*launches;
+  }
+  if (cnt[RC_BLOCK] > 0) {
+    int64_t blocks = cnt[RC_BLOCK];
+    if (blocks > (int64_t)d.sms * occ_b) blocks = (int64_t)d.sms * occ_b;
+    k_rows_block<<<(int)blocks, RB_THREADS, RB_CAP * 12, st>>>(R, items + seg[RC_BLOCK],
+                                                               cnt[RC_BLOCK]);
+    ++*launches;
+  }
+}
+
+// ----------------------------------------- longer rows: global tables ----
+
+// The rows of the big class get tables of next_pow2(2 * bound) slots at
+// tbl_off[h] (prefix over the class); insertion units of RC_CHUNK entries
+// (unit_off) and compaction units of RC_SCHUNK slots (sunit_off).  A window
+// covers the rows whose tables lie in [lo, lo + window) of that prefix.
+
+__global__ void k_big_bounds(const RowSpace R, const int32_t *__restrict__ items, int64_t H,
+                             int64_t *bound) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    bound[h] = R.rcnt[items[h]];
+  }
+}
+
+void launch_big_bounds(const RowSpace &R, const int32_t *items, int64_t H, int64_t *bound,
+                       cudaStream_t st, const Dev &d) {
+  if (H <= 0) return;
+  k_big_bounds<<<grid_of(H, 256, d), 256, 0, st>>>(R, items, H, bound);
+}
+
+__device__ __forceinline__ int64_t seg_of(const int64_t *__restrict__ off, int64_t n, int64_t x) {
+  // largest h in [0, n) with off[h] <= x
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_big_insert(RowSpace R, const int32_t *__restrict__ items,
+                                                    BigRows B, int64_t h0, int64_t h1,
+                                                    int64_t lo) {
+  const int64_t U0 = B.unit_off[h0], U1 = B.unit_off[h1];
+  for (int64_t u = U0 + blockIdx.x; u < U1; u += gridDim.x) {
+    const int64_t h = seg_of(B.unit_off, B.H, u);
+    const Row r = row_of(R, items[h]);
+    const int64_t cap = next_pow2(2 * r.cnt);
+    const int lg = lg_of(cap);
+    int32_t *keys = B.keys + (B.tbl_off[h] - lo);
+    unsigned long long *vals = B.vals + (B.tbl_off[h] - lo);
+    const int64_t t0 = (u - B.unit_off[h]) * RC_CHUNK;
+    const int64_t t1 = t0 + RC_CHUNK < r.cnt ? t0 + RC_CHUNK : r.cnt;
+    constexpr int E = RC_CHUNK / 256;
+    int32_t cv[E];
+    long long w[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      cv[i] = -1;
+      w[i] = 0;
+      const int64_t t = t0 + threadIdx.x + 256 * i;
+      if (t < t1) {
+        cv[i] = R.tnbr[r.rb + t];
+        w[i] = R.tw[r.rb + t];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if (cv[i] < 0) continue;
+      // the table (>= 2 slots per entry) always has room: this loop ends
+      const uint64_t mask = (uint64_t)cap - 1;
+      uint64_t s = row_home(cv[i], lg);
+      for (uint64_t t = 0; t <= mask; ++t) {
+        const int32_t prev = atomicCAS(keys + s, -1, cv[i]);
+        if (prev == -1 || prev == cv[i]) {
+          atomicAdd(vals + s, (unsigned long long)w[i]);
+          break;
+        }
+        s = (s + 1) & mask;
+      }
+    }
+  }
+}
+
+// Compaction: a block takes RC_SCHUNK slots of one row's table, counts the
+// occupied ones, claims their places with one atomic on ucnt and writes them.
+__global__ void __launch_bounds__(256) k_big_compact(RowSpace R, const int32_t *__restrict__ items,
+                                                     BigRows B, int64_t h0, int64_t h1,
+                                                     int64_t lo) {
+  __shared__ int s_wcnt[8];
+  __shared__ long long s_base;
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const int64_t S0 = B.sunit_off[h0], S1 = B.sunit_off[h1];
+  constexpr int PER = RC_SCHUNK / 256;
+  for (int64_t su = S0 + blockIdx.x; su < S1; su += gridDim.x) {
+    const int64_t h = seg_of(B.sunit_off, B.H, su);
+    const Row r = row_of(R, items[h]);
+    const int64_t cap = next_pow2(2 * r.cnt);
+    const int32_t *keys = B.keys + (B.tbl_off[h] - lo);
+    const unsigned long long *vals = B.vals + (B.tbl_off[h] - lo);
+    const int64_t s0 = (su - B.sunit_off[h]) * RC_SCHUNK;
+    // thread tid owns slots s0 + tid * PER .. + PER (in order)
+    int mine = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int64_t s = s0 + (int64_t)tid * PER + i;
+      if (s < cap && keys[s] >= 0) ++mine;
+    }
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wcnt[wib] = incl;
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int k = 0; k < 8; ++k) {
+        const int c = s_wcnt[k];
+        s_wcnt[k] = tot;
+        tot += c;
+      }
+      s_base = tot ? (long long)atomicAdd((unsigned long long *)&R.ucnt[r.C],
+                                          (unsigned long long)tot)
+                   : 0;
+    }
+    __syncthreads();
+    int64_t pos = r.rb + s_base + s_wcnt[wib] + (incl - mine);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int64_t s = s0 + (int64_t)tid * PER + i;
+      if (s < cap && keys[s] >= 0) {
+        R.tnbr[pos] = keys[s];
+        R.tw[pos] = (int64_t)vals[s];
+        ++pos;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_big_window(const RowSpace &R, const int32_t *items, const BigRows &B, int64_t h0,
+                       int64_t h1, int64_t lo, int64_t units, int64_t sunits, cudaStream_t st,
+                       const Dev &d, int *launches) {
+  if (h1 <= h0) return;
+  int64_t g = units < (int64_t)d.sms * 8 ? units : (int64_t)d.sms * 8;
+  k_big_insert<<<(int)(g > 0 ? g : 1), 256, 0, st>>>(R, items, B, h0, h1, lo);
+  g = sunits < (int64_t)d.sms * 8 ? sunits : (int64_t)d.sms * 8;
+  k_big_compact<<<(int)(g > 0 ? g : 1), 256, 0, st>>>(R, items, B, h0, h1, lo);
+  *launches += 2;
+}
+
+// ------------------------------------------------------------- copy ------
+
+// Row C's unique entries from the start of its flat range to offg[C].
+template <int G>
+__global__ void __launch_bounds__(256) k_rows_copy(const RowSpace R, int64_t ntot,
+                                                   const int64_t *__restrict__ offg,
+                                                   int32_t *nbr_out, int64_t *w_out) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t C = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; C < ntot; C += groups) {
+    const int64_t dst = offg[C], nu = offg[C + 1] - dst;
+    if (nu == 0) continue;
+    const int64_t src = R.boff[C];
+    for (int64_t t = gl; t < nu; t += G) {
+      nbr_out[dst + t] = R.tnbr[src + t];
+      w_out[dst + t] = R.tw[src + t];
+    }
+  }
+}
+
+void launch_rows_copy(const RowSpace &R, int64_t ntot, const int64_t *offg, int32_t *nbr_out,
+                      int64_t *w_out, cudaStream_t st, const Dev &d) {
+  if (ntot <= 0) return;
+  k_rows_copy<4><<<grid_of(ntot * 4, 256, d), 256, 0, st>>>(R, ntot, offg, nbr_out, w_out);
+}
+
+// ------------------------------------------------ sorted rows (export) ----
+
+// key = row << 32 | neighbour for every entry of a CSR whose offsets start
+// at 0; after a sort of (key, w) the rows keep their ranges and come out
+// ascending by neighbour.
+__global__ void k_row_keys(const int64_t *__restrict__ off, int64_t n,
+                           const int32_t *__restrict__ nbr, uint64_t *keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps)
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32)
+      keys[e] = ((uint64_t)v << 32) | (uint32_t)nbr[e];
+}
+
+__global__ void k_row_unkey(const uint64_t *__restrict__ keys, int64_t nnz, int32_t *nbr) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    nbr[e] = (int32_t)(uint32_t)keys[e];
+}
+
+void launch_row_keys(const int64_t *off, int64_t n, const int32_t *nbr, uint64_t *keys,
+                     cudaStream_t st, const Dev &d) {
+  if (n <= 0) return;
+  k_row_keys<<<grid_of(n * 32, 256, d), 256, 0, st>>>(off, n, nbr, keys);
+}
+
+void launch_row_unkey(const uint64_t *keys, int64_t nnz, int32_t *nbr, cudaStream_t st,
+                      const Dev &d) {
+  if (nnz <= 0) return;
+  k_row_unkey<<<grid_of(nnz, 256, d), 256, 0, st>>>(keys, nnz, nbr);
+}
+
+}  // namespace lcc

@@ -145,7 +145,8 @@ enum Ctr : int {
   C_WB = 7,       // sum of deg * (bytes per stored weight) over evaluated vertices
   C_BE = 8,       // [NB] entries per degree bucket
   C_BV = 8 + NB,  // [NB] vertices per degree bucket
-  NCTR = 8 + 2 * NB
+  C_WORK = 8 + 2 * NB,  // work-unit counter of the fused small-row kernel
+  NCTR = 9 + 2 * NB
 };
 enum Err : int64_t {
   E_BUCKET_OVERFLOW = 1,
@@ -313,9 +314,10 @@ struct Dev {
 void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
 // ev (nullable, NB events): ev[b] is recorded after degree bucket b's kernels.
+// fuse_small: the <= 4 .. <= 32 buckets in one resident launch (k_bm_small).
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev);
+                     int *launches, cudaEvent_t *ev, bool fuse_small);
 // jmoves[2j] = moves of job j, jmoves[2j + 1] = entries of its movers' rows.
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
@@ -371,14 +373,6 @@ void launch_occ(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot
 void launch_relabel(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                     const int64_t *rank, int32_t *gmap, int32_t *gmapp, cudaStream_t st,
                     const Dev &d);
-// Key of an entry inside a cluster (sorts after every real pair).
-constexpr uint64_t EMIT_INTRA = ~0ull;
-// Every entry of every job at flat position estart[j] + e (see k_contract.cu);
-// intra (zeroed) receives the number of entries inside clusters.
-void launch_emit_all(const CJob *jobs, const int64_t *vstart, const int64_t *estart, int njobs,
-                     int64_t vtot, const int32_t *gmap, const int32_t *gmapp, const int64_t *rank,
-                     uint64_t *keys, int64_t *vals, unsigned long long *intra, cudaStream_t st,
-                     const Dev &d);
 void launch_knew(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                  const int64_t *rank, int64_t *knew, cudaStream_t st, const Dev &d);
 void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, int64_t *out,
@@ -388,19 +382,69 @@ void launch_job_counts(const int64_t *vstart, int njobs, const int64_t *rank, in
 int64_t scan_tmp_elems(int64_t n);
 void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, const Dev &d);
 
+// Compress by rows (k_rows.cu).  Classes of coarse rows by the number of
+// entries of their members.
+enum RowClass : int { RC_G4 = 0, RC_G8, RC_G16, RC_G32, RC_WARP, RC_BLOCK, RC_BIG, RC_N };
+constexpr int RC_WARP_MAX = 256;    // warp + shared table of 2 slots per entry
+constexpr int RC_BLOCK_MAX = 4096;  // block + shared table of 2 slots per entry
+constexpr int RC_CHUNK = 4096;      // entries per insertion unit of a big row
+constexpr int RC_SCHUNK = 4096;     // table slots per compaction unit of a big row
+
+struct RowSpace {
+  const CJob *jobs;
+  const int64_t *vstart;    // [njobs + 1] first flat vertex of each job
+  const int32_t *gmap;      // [vt] global coarse id of each flat vertex
+  const int32_t *gmapp;     // global coarse id at the flat gather positions
+  const int64_t *rank;      // rank[vstart_j] = first global coarse id of job j
+  const int64_t *boff;      // [ntot + 1] region of coarse row C: [boff[C], boff[C+1])
+  int64_t *rcnt;            // [ntot] entries appended to each region (zeroed)
+  int32_t *tnbr;            // [entries] job-local coarse id of the far end
+  int64_t *tw;              // [entries] weight
+  int64_t *ucnt;            // [ntot + 1] unique entries per row (zeroed)
+  unsigned long long *intra;  // entries inside a cluster (counted)
+  int32_t njobs;
+  int32_t pad;
+};
+
+// Global tables of the rows of class RC_BIG (prefix arrays over those rows).
+struct BigRows {
+  int32_t *keys;            // window of tables, -1 = empty
+  unsigned long long *vals;
+  const int64_t *tbl_off;   // [H + 1] next_pow2(2 * bound) slots per row
+  const int64_t *unit_off;  // [H + 1] ceil(bound / RC_CHUNK)
+  const int64_t *sunit_off; // [H + 1] ceil(slots / RC_SCHUNK)
+  int64_t H;
+};
+
+// rbound[gmap[i]] += deg(i) for every flat vertex (rbound zeroed).
+void launch_rbound(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vt,
+                   const int32_t *gmap, int64_t *rbound, cudaStream_t st, const Dev &d);
+// Appends every inter-cluster entry to its coarse row's region.
+void launch_emit_rows(const RowSpace &R, int64_t vt, cudaStream_t st, const Dev &d);
+void launch_rows_classify(const RowSpace &R, int64_t ntot, bool fill, unsigned long long *cnt,
+                          const int64_t *seg, int32_t *items, cudaStream_t st, const Dev &d);
+// seg and cnt: host arrays [RC_N]; items of class c at items + seg[c].
+void launch_rows_small(const RowSpace &R, const int32_t *items, const int64_t *seg,
+                       const int64_t *cnt, cudaStream_t st, const Dev &d, int *launches);
+void launch_big_bounds(const RowSpace &R, const int32_t *items, int64_t H, int64_t *bound,
+                       cudaStream_t st, const Dev &d);
+// Rows [h0, h1) of the big class, whose tables start at or after slot lo
+// (B.keys / B.vals hold that window, cleared).
+void launch_big_window(const RowSpace &R, const int32_t *items, const BigRows &B, int64_t h0,
+                       int64_t h1, int64_t lo, int64_t units, int64_t sunits, cudaStream_t st,
+                       const Dev &d, int *launches);
+void launch_rows_copy(const RowSpace &R, int64_t ntot, const int64_t *offg, int32_t *nbr_out,
+                      int64_t *w_out, cudaStream_t st, const Dev &d);
+// Sorting the rows of a CSR (offsets from 0) by neighbour: keys row << 32 |
+// neighbour, then back.
+void launch_row_keys(const int64_t *off, int64_t n, const int32_t *nbr, uint64_t *keys,
+                     cudaStream_t st, const Dev &d);
+void launch_row_unkey(const uint64_t *keys, int64_t nnz, int32_t *nbr, cudaStream_t st,
+                      const Dev &d);
+
 // LSD radix sort of (key, val) pairs on the given 8-bit digit positions.
 int64_t radix_tmp_elems(int64_t n);
 void radix_sort_pairs(uint64_t *keys, int64_t *vals, uint64_t *keys_alt, int64_t *vals_alt,
                       int64_t n, const int *shifts, int npasses, int64_t *tmp,
                       cudaStream_t st, const Dev &d, bool *result_in_alt, int *launches);
-// Reduce by key over sorted keys (k_contract.cu): rb_tiles(n) tiles;
-// tile_heads[t] = heads of tile t (scanned in place by the caller into each
-// tile's first run); ukeys/uvals receive one entry per run (uvals zeroed).
-int64_t rb_tiles(int64_t n);
-void launch_rb_count(const uint64_t *keys, int64_t n, int64_t *tile_heads, cudaStream_t st);
-void launch_rb_write(const uint64_t *keys, const int64_t *vals, int64_t n, const int64_t *tile_off,
-                     uint64_t *ukeys, int64_t *uvals, cudaStream_t st);
-void launch_csr_rows(const uint64_t *ukeys, int64_t nu, int64_t nrows, int64_t *offg,
-                     int32_t *nbr_out, cudaStream_t st, const Dev &d);
-
 }  // namespace lcc

@@ -39,7 +39,7 @@ class lcc_schedule(C.Structure):
 
 
 class lcc_tuning(C.Structure):
-    _fields_ = [("warp_max", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("warp_max", C.c_int32), ("fuse_small", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class lcc_stats(C.Structure):
@@ -53,7 +53,17 @@ class lcc_stats(C.Structure):
                 ("ms_total", C.c_double), ("bytes_bestmove", C.c_int64),
                 ("pairs_sorted", C.c_int64), ("kernel_launches", C.c_int64),
                 ("ms_bucket", C.c_double * 16), ("bucket_entries", C.c_int64 * 16),
-                ("bucket_vertices", C.c_int64 * 16), ("bytes_contract_min", C.c_int64)]
+                ("bucket_vertices", C.c_int64 * 16), ("bytes_contract_min", C.c_int64),
+                ("calls", C.c_int64), ("calls_capped", C.c_int64)]
+
+
+class lcc_round(C.Structure):
+    _fields_ = [("level", C.c_int32), ("phase", C.c_int32), ("round", C.c_int32),
+                ("pad", C.c_int32), ("vprime", C.c_int64), ("entries", C.c_int64),
+                ("moved", C.c_int64), ("held", C.c_int64)]
+
+
+ROUND_COLUMNS = ("level", "phase", "round", "vprime", "entries", "moved", "held")
 
 
 class lcc_server_cfg(C.Structure):
@@ -81,6 +91,7 @@ _SIGS = {
     "lcc_graph_info": [P, P, P],
     "lcc_free_graph": [P],
     "lcc_cluster": [P, I64, I64, I32, P, P, I32, P, P],
+    "lcc_cluster_trace": [P, I64, I64, I32, P, P, I32, P, P, P, I64, P],
     "lcc_desired": [P, I64, I64, I32, P, P, P],
     "lcc_best_moves": [P, I64, I64, I32, I32, I32, P, P, P],
     "lcc_compress": [P, I32, P, P, P],
@@ -242,6 +253,29 @@ def lcc_cluster(g, lambda_p, lambda_q, mode=LCC_NODEW_UNIT, sched=None, labels_o
     return labels_out, obj.value, _stats_dict(st)
 
 
+def lcc_cluster_trace(g, lambda_p, lambda_q, mode=LCC_NODEW_UNIT, sched=None, max_rounds=100000):
+    """lcc_cluster plus its per-round record.  Returns (labels, objective,
+    stats dict, rows) with one row per Best-Moves round (ROUND_COLUMNS):
+    depth, phase (1 = refinement), round of the call, |V'|, entries scanned,
+    vertices moved, vertices held back by the coin."""
+    lib = load()
+    sched = sched or schedule()
+    labels = np.empty(g.n, np.int32)
+    obj = C.c_double()
+    st = lcc_stats()
+    buf = (lcc_round * max_rounds)()
+    tl = C.c_int64()
+    _check(lib.lcc_cluster_trace(g.handle, int(lambda_p), int(lambda_q), int(mode),
+                                 C.byref(sched), labels.ctypes.data_as(C.c_void_p),
+                                 LCC_MEM_HOST, C.byref(obj), C.byref(st), buf, max_rounds,
+                                 C.byref(tl)))
+    if tl.value > max_rounds:
+        raise ValueError("more than %d rounds; raise max_rounds" % max_rounds)
+    rows = np.array([[getattr(buf[i], f) for f in ROUND_COLUMNS] for i in range(tl.value)],
+                    np.int64).reshape(-1, len(ROUND_COLUMNS))
+    return labels, obj.value, _stats_dict(st), rows
+
+
 def lcc_desired(g, lambda_p, lambda_q, mode, labels, frontier=None):
     lib = load()
     labels = np.ascontiguousarray(labels, np.int32)
@@ -304,26 +338,28 @@ def lcc_objective(g, lambda_p, lambda_q, mode, labels):
 
 
 def lcc_get_tuning(device=0):
-    """The degree routing used on `device`: returns warp_max."""
+    """The kernel tuning used on `device`: {"warp_max", "fuse_small"}."""
     t = lcc_tuning()
     _check(load().lcc_get_tuning(int(device), C.byref(t)))
-    return t.warp_max
+    return {"warp_max": t.warp_max, "fuse_small": t.fuse_small}
 
 
-def lcc_set_tuning(device, warp_max):
+def lcc_set_tuning(device, warp_max, fuse_small=1):
     t = lcc_tuning()
     t.warp_max = int(warp_max)
+    t.fuse_small = int(fuse_small)
     _check(load().lcc_set_tuning(int(device), C.byref(t)))
 
 
 def lcc_autotune(g, lambda_p, lambda_q, mode, cache_path=None):
-    """Times each routing on three best-move rounds of g (or reads the cache
-    file's line for this device) and applies the fastest; returns warp_max."""
+    """Times every tuning (warp_max x fuse_small) on three best-move rounds of
+    g (or reads the cache file's line for this device) and applies the
+    fastest; returns it as {"warp_max", "fuse_small"}."""
     t = lcc_tuning()
     path = cache_path.encode() if cache_path else None
     _check(load().lcc_autotune(g.handle, int(lambda_p), int(lambda_q), int(mode), path,
                                C.byref(t)))
-    return t.warp_max
+    return {"warp_max": t.warp_max, "fuse_small": t.fuse_small}
 
 
 def lcc_desired_noalloc(off, nbr, w, k, lambda_p, lambda_q, labels, K, out, stream=None):

@@ -41,7 +41,8 @@ def test_struct_layouts_match_header_sizes(tmp_path):
     the size of every struct and the offset of every field."""
     import subprocess
     from paper_2108_01731_gb300 import lcc
-    structs = [lcc.lcc_schedule, lcc.lcc_stats, lcc.lcc_tuning, lcc.lcc_server_cfg, lcc.lcc_job]
+    structs = [lcc.lcc_schedule, lcc.lcc_stats, lcc.lcc_tuning, lcc.lcc_server_cfg, lcc.lcc_job,
+               lcc.lcc_round]
     lines = []
     for st in structs:
         lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (st.__name__, st.__name__))

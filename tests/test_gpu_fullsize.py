@@ -164,6 +164,37 @@ def test_knn_1e6_signed_weights(L):
     G.free()
 
 
+@pytest.mark.parametrize("name", ["sbm1e4", "chunglu16"])
+def test_run_to_convergence_against_sequential_cc(L, name):
+    """The paper's run-to-convergence variant (^CON, Sec. 4): Best-Moves
+    calls that run until no vertex wants to move, here with a round cap that
+    is never reached.  With the symmetry-breaking coin every call converges,
+    and the run equals the oracle's; the plain synchronous rounds keep
+    swapping and every call stops at its cap (200 rounds), also equal to the
+    oracle.  The objective of the converged run is printed beside the
+    paper's sequential method (Sequential-CC, Sec. 3.1 / Algorithm 2) and must
+    reach at least 90% of it."""
+    if name == "sbm1e4":
+        g = I.to_numpy(I.sbm([100] * 100, 0.05, 0.0005, seed=I.BASE_SEED + 1))
+        mode, p, q = L.LCC_NODEW_UNIT, 1, 100
+    else:
+        g = I.to_numpy(I.chung_lu(1 << 16, 2.1, 32, seed=I.BASE_SEED + 2))
+        mode, p, q = L.LCC_NODEW_DEGREE, 1, 1
+    G = L.lcc_load_csr(g["off"], g["nbr"])
+    con = same_run(L, G, g, p, q, mode, L.schedule(num_iter=10000, coin=True, seed=0),
+                   coin=True, seed=0)
+    assert con["calls"] > 0 and con["calls_capped"] == 0
+    plain = same_run(L, G, g, p, q, mode, L.schedule(num_iter=200))
+    assert plain["calls_capped"] == plain["calls"] > 0
+    _, snum, sden, _ = O.sequential_cc(g["off"], g["nbr"], None, p, q, mode=mode, seed=0)
+    seq = snum / sden
+    print("%s: run to convergence with the coin %.6g (%d rounds), plain synchronous capped at "
+          "200 rounds %.6g, Sequential-CC %.6g" % (name, con["objective"], con["rounds_total"],
+                                                   plain["objective"], seq))
+    assert con["objective"] >= 0.9 * seq
+    G.free()
+
+
 @pytest.mark.skipif(os.environ.get("LCC_TEST_RMAT26_WHOLE") != "1",
                     reason="about ten minutes of host time: set LCC_TEST_RMAT26_WHOLE=1")
 def test_rmat_2e26_whole_run_equals_cpu_twin(L):

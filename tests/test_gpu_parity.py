@@ -202,6 +202,34 @@ def test_cluster_matches_oracle(L, case):
     check_cluster_case(L, case)
 
 
+TRACE_CASES = [("sbm", O.NODEW_UNIT, 1, 50, O.VSET_NBR_VERTICES, False),
+               ("hubs", O.NODEW_DEGREE, 1, 1, O.VSET_NBR_VERTICES, False),
+               ("rmat", O.NODEW_DEGREE, 1, 1, O.VSET_NBR_CLUSTERS, False),
+               ("cl", O.NODEW_DEGREE, 1, 1, O.VSET_ALL, False),
+               ("signed", O.NODEW_UNIT, 1, 9, O.VSET_NBR_VERTICES, False),
+               ("rmat", O.NODEW_DEGREE, 1, 1, O.VSET_NBR_VERTICES, True),
+               ("hubs_w", O.NODEW_UNIT, 1, 9, O.VSET_NBR_CLUSTERS, True)]
+
+
+@pytest.mark.parametrize("case", TRACE_CASES, ids=lambda c: "%s-%d-%s" % (c[0], c[4], c[5]))
+def test_round_trace_matches_oracle(L, case):
+    """Per-round |V'|, scanned entries, moves and held-back vertices (the
+    paper's plot of |V'| per round) equal the oracle's record, round by round
+    over the whole multi-level run; the pull rounds of the neighbour rule
+    report the same V' as marking."""
+    name, mode, p, q, vset, coin = case
+    g = GRAPHS[name]
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    sched = L.schedule(vset=vset, coin=coin, seed=3)
+    labels, obj, st, rows = L.lcc_cluster_trace(G, p, q, mode, sched)
+    wl, num, den, ws, wtr = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, vset=vset,
+                                      coin=coin, seed=3, trace=True)
+    assert np.array_equal(labels, wl) and st["obj_num"] == num
+    assert np.array_equal(rows, wtr)
+    assert rows[:, 4].sum() == st["edges_scanned"] and len(rows) == st["rounds_total"]
+    G.free()
+
+
 def test_gather_layout_matches_oracle(L, monkeypatch):
     """The degree-ordered storage of the packed label words (forced here on
     graphs far below the size that gets it by default) moves words only:
@@ -220,10 +248,12 @@ def test_gather_layout_matches_oracle(L, monkeypatch):
 
 
 def test_tuning_routes_without_changing_results(L, tmp_path):
-    """Every degree routing (rows of 33..warp_max entries in the warp kernels,
-    longer rows up to 1024 in the block kernel) gives the oracle's labels and
-    scanned entries; the autotuner picks one of the routings, and its cache
-    file is read back on the next call."""
+    """Every tuning -- the degree routing (rows of 33..warp_max entries in the
+    warp kernels, longer rows up to 1024 in the block kernel) crossed with the
+    small rows in one resident launch or in one launch per bucket -- gives
+    the oracle's labels, objective and scanned entries, alone and in a batch;
+    the autotuner picks one of them, and its cache file is read back on the
+    next call."""
     before = L.lcc_get_tuning(0)
     try:
         for name, mode, p, q in [("hubs", O.NODEW_DEGREE, 1, 1), ("rmat", O.NODEW_DEGREE, 1, 1),
@@ -231,27 +261,39 @@ def test_tuning_routes_without_changing_results(L, tmp_path):
             g = GRAPHS[name]
             G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
             wl, num, _, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode)
-            for wm in (32, 64, 128, 256):
-                L.lcc_set_tuning(0, wm)
-                labels, _, st = L.lcc_cluster(G, p, q, mode, None)
-                assert np.array_equal(labels, wl), (name, wm)
-                assert st["obj_num"] == num and st["edges_scanned"] == wst[2]
+            for fs in (0, 1):
+                for wm in (32, 64, 128, 256):
+                    L.lcc_set_tuning(0, wm, fs)
+                    labels, _, st = L.lcc_cluster(G, p, q, mode, None)
+                    assert np.array_equal(labels, wl), (name, wm, fs)
+                    assert st["obj_num"] == num and st["edges_scanned"] == wst[2]
+            G.free()
+        graphs = [GRAPHS[x] for x in ("sbm", "rmat", "cl")]
+        Gs = [L.lcc_load_csr(g["off"], g["nbr"], g["w"]) for g in graphs]
+        for fs in (0, 1):
+            L.lcc_set_tuning(0, 256, fs)
+            labs, _ = L.lcc_cluster_batch(Gs, [1] * 3, [1] * 3, [O.NODEW_DEGREE] * 3)
+            for g, lab in zip(graphs, labs):
+                wl, *_ = O.cluster(g["off"], g["nbr"], g["w"], 1, 1, mode=O.NODEW_DEGREE)
+                assert np.array_equal(lab, wl), fs
+        for G in Gs:
             G.free()
         g = GRAPHS["rmat"]
         G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
         path = tmp_path / "tuning.txt"
-        wm = L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path))
-        assert wm in (32, 64, 128, 256) and L.lcc_get_tuning(0) == wm
-        assert path.read_text().strip().endswith(" %d" % wm)
-        L.lcc_set_tuning(0, 32 if wm != 32 else 256)
-        assert L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path)) == wm
-        assert L.lcc_get_tuning(0) == wm
+        t = L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path))
+        assert t["warp_max"] in (32, 64, 128, 256) and t["fuse_small"] in (0, 1)
+        assert L.lcc_get_tuning(0) == t
+        assert path.read_text().strip().endswith(" %d %d" % (t["warp_max"], t["fuse_small"]))
+        L.lcc_set_tuning(0, 32 if t["warp_max"] != 32 else 256, 1 - t["fuse_small"])
+        assert L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path)) == t
+        assert L.lcc_get_tuning(0) == t
         G.free()
-        for bad in (0, 48, 512):
+        for bad in ((0, 1), (48, 1), (512, 1), (256, 2)):
             with pytest.raises(L.LccError):
-                L.lcc_set_tuning(0, bad)
+                L.lcc_set_tuning(0, *bad)
     finally:
-        L.lcc_set_tuning(0, before)
+        L.lcc_set_tuning(0, before["warp_max"], before["fuse_small"])
 
 
 def check_cluster_case(L, case):
@@ -634,9 +676,23 @@ def test_server_rejects_oversize_and_cancels(L):
 
 
 def test_hub_tables_in_many_windows(L, monkeypatch):
-    """Hub hash tables processed in small windows (many passes per round)
-    give the same desired clusters and the same clustering."""
+    """Hub hash tables processed in small windows (many passes per round),
+    and the tables of long coarse rows in Compress likewise, give the same
+    desired clusters, the same coarse graph and the same clustering."""
     monkeypatch.setenv("LCC_HUB_WINDOW_SLOTS", "4096")
+    monkeypatch.setenv("LCC_ROW_WINDOW_SLOTS", "4096")
+    g = GRAPHS["giant"]
+    G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
+    k = np.ones(g["n"], np.int64)
+    Lb = I.random_labels(g["n"], g["n"] // 3, seed=78).numpy()
+    mp, C = L.lcc_compress(G, O.NODEW_UNIT, Lb)
+    got = L.lcc_graph_export(C)
+    want = O.compress(g["off"], g["nbr"], g["w"], k, Lb)
+    assert np.array_equal(mp, want[0])
+    for a, b in zip(got, want[1:]):
+        assert np.array_equal(a, b)
+    C.free()
+    G.free()
     g = GRAPHS["hubs_w"]
     n = g["n"]
     G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])

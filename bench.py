@@ -44,6 +44,10 @@ WORKLOADS = {
     "chunglu20": dict(kind="chunglu", n=1 << 20, beta=2.1, deg=32, mode=1, p=1, q=1,
                       num_iter=10, desc="Chung-Lu beta=2.1, 2^20 vertices, ~16M edges, "
                                         "modularity (gamma=1)"),
+    "rmat24": dict(kind="rmat", scale=24, m=1 << 28, mode=1, p=1, q=1, num_iter=10,
+                   desc="R-MAT a=0.57 b=c=0.19 d=0.05, 2^24 vertices, 2^28 undirected edges "
+                        "(2^29 CSR entries), modularity (gamma=1): the benchmark graph at a "
+                        "quarter of its size, for kernel profiles"),
     "rmat22": dict(kind="rmat", scale=22, m=1 << 26, mode=1, p=1, q=1, num_iter=10,
                    desc="R-MAT a=0.57 b=c=0.19 d=0.05, 2^22 vertices, 2^26 undirected edges, "
                         "modularity (gamma=1)"),
@@ -75,6 +79,9 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--serving", type=int, default=160,
                     help="graphs of the serving stream to run (0 = skip)")
+    ap.add_argument("--serving-large", type=int, default=3000,
+                    help="graphs of the stream for one more saturation run in which the "
+                         "HBM admission budget binds (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-twin", action="store_true",
                     help="skip the OpenMP CPU twin's timed first round")
@@ -354,34 +361,42 @@ def host_copy(g):
 
 # ---------------------------------------------------------------- serving --
 
-def serving_bench(L, count, device):
-    """Config-5 stream sample: plain one-graph-per-call path vs the continuous
-    batching server; graphs/s at saturation and p50/p99 under Poisson arrivals."""
+def serving_bench(L, count, device, large=0):
+    """Config-5 stream: the plain one-graph-per-call path against the
+    continuous-batching server, on the first `count` graphs of the stream:
+    graphs/s at saturation (every graph submitted at once) with its p50/p99,
+    and p50/p99 under Poisson arrivals at 0.25 ... 8 times the plain path's
+    rate.  With large > 0, the first `large` graphs of the stream also run
+    through the server at saturation, which is long enough for the 120 GB
+    admission budget to bind."""
     import numpy as np
     from paper_2108_01731_gb300 import inputs as I
-    graphs = []
-    for i in range(count):
-        g = I.serving_graph(i, device=device)
-        graphs.append({k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in g.items()
-                       if k in ("off", "nbr", "n", "nnz")})
+
+    def make(k):
+        out = []
+        for i in range(k):
+            g = I.serving_graph(i, device=device)
+            out.append({x: (v.cpu().numpy() if hasattr(v, "cpu") else v) for x, v in g.items()
+                        if x in ("off", "nbr", "n", "nnz")})
+        return out
+
     mode = L.LCC_NODEW_DEGREE
-    # plain: one graph per call (load + cluster + labels to host)
-    t0 = time.perf_counter()
-    plain = []
-    for g in graphs:
-        G = L.lcc_load_csr(g["off"], g["nbr"])
-        lab, _, _ = L.lcc_cluster(G, 1, 1, mode)
-        plain.append(lab)
-        G.free()
-    t_plain = time.perf_counter() - t0
-    gps_plain = count / t_plain
-    tot_bytes = sum(g["nnz"] for g in graphs) * 40
     budget = 120 << 30
 
-    def run_server(rate):
+    def plain_run(graphs):
+        t0 = time.perf_counter()
+        labs = []
+        for g in graphs:
+            G = L.lcc_load_csr(g["off"], g["nbr"])
+            lab, _, _ = L.lcc_cluster(G, 1, 1, mode)
+            labs.append(lab)
+            G.free()
+        return labs, time.perf_counter() - t0
+
+    def run_server(graphs, ref, rate):
         srv = L.Server(budget, 1 << 14)
         rs = np.random.default_rng(12345)
-        gaps = rs.exponential(1.0 / rate, count) if rate else np.zeros(count)
+        gaps = rs.exponential(1.0 / rate, len(graphs)) if rate else np.zeros(len(graphs))
         t_start = time.perf_counter()
         tickets = []
         t_next = t_start
@@ -393,30 +408,52 @@ def serving_bench(L, count, device):
         srv.wait_idle(3600 * 1000)
         t_end = time.perf_counter()
         lats, same = [], True
-        for t, ref in zip(tickets, plain):
+        for t, r in zip(tickets, ref):
             lab, obj, lat = srv.poll(t)
             lats.append(lat)
-            same &= bool(np.array_equal(lab, ref))
+            same &= bool(np.array_equal(lab, r))
         c = srv.counters()
         srv.close()
-        return count / (t_end - t_start), lats, same, c
+        return len(graphs) / (t_end - t_start), lats, same, c
 
-    gps_batched, lats_sat, same_sat, c_sat = run_server(0)
+    def pct(lats):
+        return (round(float(np.percentile(lats, 50)), 3), round(float(np.percentile(lats, 99)), 3))
+
+    graphs = make(count)
+    plain, t_plain = plain_run(graphs)
+    gps_plain = count / t_plain
+    gps_batched, lats_sat, same_sat, c_sat = run_server(graphs, plain, 0)
+    p50, p99 = pct(lats_sat)
     out = {"graphs": count, "config": "planted-partition stream, n log-uniform [100, 200000], "
                                       "5-500 communities, mean degree 8-64, modularity",
+           "sample": "the first %d graphs of the 20,000-graph stream" % count,
            "plain_graphs_per_s": round(gps_plain, 3),
            "batched_graphs_per_s": round(gps_batched, 3),
            "batched_over_plain": round(gps_batched / gps_plain, 3),
            "labels_identical": same_sat,
+           "saturation_p50_ms": p50, "saturation_p99_ms": p99,
            "peak_concurrent_jobs": c_sat["peak_jobs"], "budget_bytes": budget, "rates": []}
-    for frac in (0.5, 1.0, 2.0):
+    for frac in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0):
         rate = frac * gps_plain
-        gps, lats, same, c = run_server(rate)
+        gps, lats, same, c = run_server(graphs, plain, rate)
+        p50, p99 = pct(lats)
         out["rates"].append({"arrival_per_s": round(rate, 3), "x_plain": frac,
-                             "graphs_per_s": round(gps, 3),
-                             "p50_ms": round(float(np.percentile(lats, 50)), 3),
-                             "p99_ms": round(float(np.percentile(lats, 99)), 3),
+                             "graphs_per_s": round(gps, 3), "p50_ms": p50, "p99_ms": p99,
                              "labels_identical": same, "peak_concurrent_jobs": c["peak_jobs"]})
+    if large > count:
+        graphs = make(large)
+        plain, t_plain = plain_run(graphs)
+        gps, lats, same, c = run_server(graphs, plain, 0)
+        p50, p99 = pct(lats)
+        out["large_stream"] = {"graphs": large,
+                               "sample": "the first %d graphs of the 20,000-graph stream" % large,
+                               "plain_graphs_per_s": round(large / t_plain, 3),
+                               "batched_graphs_per_s": round(gps, 3),
+                               "batched_over_plain": round(gps / (large / t_plain), 3),
+                               "saturation_p50_ms": p50, "saturation_p99_ms": p99,
+                               "labels_identical": same, "peak_concurrent_jobs": c["peak_jobs"],
+                               "peak_resident_bytes": c["peak_bytes"],
+                               "total_entries": int(sum(g["nnz"] for g in graphs))}
     return out
 
 
@@ -638,7 +675,7 @@ def run_ours(args, rank, world, local):
             twin = twin_round(host, wl, lambda lab: L.lcc_desired(G, wl["p"], wl["q"],
                                                                   wl["mode"], lab))
         if args.serving > 0:
-            serving = serving_bench(L, args.serving, dev)
+            serving = serving_bench(L, args.serving, dev, args.serving_large)
     line = {"metric": "best-move GEdges/s", "value": round(value, 4), "unit": "GEdges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak",
@@ -657,6 +694,8 @@ def run_ours(args, rank, world, local):
                        "generation_s": round(t_gen, 2),
                        "tuning": {"warp_max": tuning["warp_max"],
                                   "fuse_small": tuning["fuse_small"],
+                                  "prefetch": tuning["prefetch"],
+                                  "pregather": tuning["pregather"],
                                   "autotune_s": round(t_tune, 2),
                                   "chosen_by": ("lcc_autotune on this graph before timing "
                                                 "(3 best-move rounds per routing)"

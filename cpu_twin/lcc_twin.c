@@ -266,8 +266,9 @@ static int64_t max_degree(const tw_level *g) {
 }
 
 /* Every gain fits __int128 and every per-cluster sum fits int64 when the
- * total absolute edge weight W < 2^62, q W < 2^125 and p Ktot^2 < 2^125
- * (k_v <= Ktot and K_C <= Ktot at every level, as Compress keeps both). */
+ * total absolute edge weight W < 2^62, Ktot < 2^62, q W < 2^125 and
+ * p Ktot^2 < 2^125 (k_v <= Ktot and K_C <= Ktot at every level, as Compress
+ * keeps both). */
 static int check_bounds(const tw_level *g, int64_t p, int64_t q) {
   const int T = omp_get_max_threads();
   i128 wpart[T], kpart[T];
@@ -292,10 +293,12 @@ static int check_bounds(const tw_level *g, int64_t p, int64_t q) {
   if (bad) return TW_ERR_INVALID;
   i128 W = 0, Kt = 0;
   for (int i = 0; i < T; ++i) { W += wpart[i]; Kt += kpart[i]; }
+  /* refused when q W or p Ktot^2 reaches 2^125 (the bound the oracle and the
+   * library apply): q > (lim - 1) / W  <=>  q W >= lim for positive integers */
   const i128 lim = (i128)1 << 125;
-  if (W >= ((i128)1 << 62)) return TW_ERR_OVERFLOW;
-  if (W > 0 && (i128)q > lim / W) return TW_ERR_OVERFLOW;
-  if (Kt > 0 && (Kt >= ((i128)1 << 100) || (i128)p > lim / Kt / Kt)) return TW_ERR_OVERFLOW;
+  if (W >= ((i128)1 << 62) || Kt >= ((i128)1 << 62)) return TW_ERR_OVERFLOW;
+  if (W > 0 && (i128)q > (lim - 1) / W) return TW_ERR_OVERFLOW;
+  if (Kt > 0 && (i128)p > (lim - 1) / (Kt * Kt)) return TW_ERR_OVERFLOW;
   return TW_OK;
 }
 

@@ -369,7 +369,18 @@ typedef struct lcc_tuning {
                           graph in one resident launch whose warps take work
                           units from a device counter; 0: one launch per
                           bucket of <= 4, 8, 16 and 32 entries */
-  int32_t reserved[6]; /* zero */
+  int32_t prefetch;    /* 1: the block kernels for rows of 129..4096 entries
+                          load the next vertex's neighbour positions while
+                          they merge the current vertex and ask L2 for its
+                          label words; 0 (the default): no pipeline (fewer
+                          registers per thread) */
+  int32_t pregather;   /* 1 (the default): a round that reads every row (V' =
+                          V, or V' tested inside the best-move kernels) first
+                          gathers the label word of every entry in one flat
+                          pass (8 bytes per entry of extra device memory), and
+                          the best-move kernels read those words as a stream;
+                          0: every entry gathers its own word */
+  int32_t reserved[4]; /* zero */
 } lcc_tuning;
 
 /* lcc_get_tuning / lcc_set_tuning -- the tuning used by later calls on CUDA

@@ -399,7 +399,9 @@ static void check_tuning(const lcc_tuning *t) {
   if (w != 32 && w != 64 && w != 128 && w != 256)
     fail(LCC_ERR_INVALID, "warp_max must be 32, 64, 128 or 256");
   if (t->fuse_small != 0 && t->fuse_small != 1) fail(LCC_ERR_INVALID, "fuse_small must be 0 or 1");
-  for (int i = 0; i < 6; ++i)
+  if (t->prefetch != 0 && t->prefetch != 1) fail(LCC_ERR_INVALID, "prefetch must be 0 or 1");
+  if (t->pregather != 0 && t->pregather != 1) fail(LCC_ERR_INVALID, "pregather must be 0 or 1");
+  for (int i = 0; i < 4; ++i)
     if (t->reserved[i]) fail(LCC_ERR_INVALID, "reserved tuning fields must be zero");
 }
 
@@ -482,11 +484,13 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
         std::string l(line);
         if (l.size() <= key.size() || l.compare(0, key.size(), key) != 0 || l[key.size()] != ' ')
           continue;
-        int wm = 0, fs = 1;
-        const int nread = sscanf(l.c_str() + key.size() + 1, "%d %d", &wm, &fs);
+        int wm = 0, fs = 1, pf = 0, pg = 1;
+        const int nread = sscanf(l.c_str() + key.size() + 1, "%d %d %d %d", &wm, &fs, &pf, &pg);
         if (nread < 1) fail(LCC_ERR_INVALID, "malformed tuning line for this device");
         t.warp_max = wm;
         t.fuse_small = nread >= 2 ? fs : 1;
+        t.prefetch = nread >= 3 ? pf : 0;
+        t.pregather = nread >= 4 ? pg : 1;
         found = true;
       }
       fclose(f);
@@ -499,24 +503,38 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
     }
   }
   const lcc_tuning before = tuning_for(g->dev);
-  const int cand[4] = {32, 64, 128, 256};
   double best_ms = 0;
   lcc_tuning best = before;
   bool first = true;
+  auto trial = [&](const lcc_tuning &c) {
+    set_tuning(g->dev, c);
+    const double ms = time_rounds(g, lambda_p, lambda_q, mode, 3);
+    if (first || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+      first = false;
+    }
+  };
   try {
     time_rounds(g, lambda_p, lambda_q, mode, 1);  // first-use costs outside the comparison
-    for (int fs = 0; fs <= 1; ++fs)
-      for (int c : cand) {
-        t.warp_max = c;
-        t.fuse_small = fs;
-        set_tuning(g->dev, t);
-        const double ms = time_rounds(g, lambda_p, lambda_q, mode, 3);
-        if (first || ms < best_ms) {
-          best_ms = ms;
-          best = t;
-          first = false;
-        }
-      }
+    // one field at a time, each from the best so far: warp_max, then
+    // fuse_small, then prefetch
+    memset(&t, 0, sizeof(t));
+    t.fuse_small = 1;
+    t.pregather = 1;
+    for (int c : {32, 64, 128, 256}) {
+      t.warp_max = c;
+      trial(t);
+    }
+    t = best;
+    t.fuse_small = 1 - t.fuse_small;
+    trial(t);
+    t = best;
+    t.prefetch = 1 - t.prefetch;
+    trial(t);
+    t = best;
+    t.pregather = 1 - t.pregather;
+    trial(t);
   } catch (...) {
     set_tuning(g->dev, before);
     throw;
@@ -526,7 +544,8 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
   if (cache_path) {
     FILE *f = fopen(cache_path, "a");
     if (!f) fail(LCC_ERR_INVALID, std::string("cannot write the tuning file ") + cache_path);
-    fprintf(f, "%s %d %d\n", key.c_str(), t.warp_max, t.fuse_small);
+    fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.warp_max, t.fuse_small, t.prefetch,
+            t.pregather);
     fclose(f);
   }
   if (out) *out = t;

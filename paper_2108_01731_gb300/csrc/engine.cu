@@ -73,6 +73,7 @@ lcc_tuning tuning_for(int dev) {
   memset(&t, 0, sizeof(t));
   t.warp_max = T_WARP;
   t.fuse_small = 1;
+  t.pregather = 1;
   return t;
 }
 
@@ -150,7 +151,8 @@ Engine::~Engine() {
   for (auto &e : bev_) cudaEventDestroy(e);
   Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                     &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
-                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,    &s_layout_};
+                    &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,    &s_layout_,
+                    &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_};
   for (Scratch *s : all) s->release(st_);
   cudaStreamSynchronize(st_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -161,7 +163,7 @@ size_t Engine::scratch_bytes() const {
   const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                           &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
                           &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
-                          &s_layout_};
+                          &s_layout_, &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_};
   size_t t = 0;
   for (const Scratch *s : all) t += s->bytes;
   return t;
@@ -524,6 +526,10 @@ void Engine::end_bm(Job *j) {
 
 void Engine::round(std::vector<Job *> &js) {
   const int nj = (int)js.size();
+  const lcc_tuning tun = tuning_for(dev_);
+  const bool pregather = tun.pregather != 0;
+  std::vector<int64_t> gw_start(nj + 1, 0);
+  int64_t gw_tot = 0;
   std::vector<JobDev> tab(nj);
   std::vector<CoinJob> coins(nj);
   std::vector<int64_t> vs(nj + 1);
@@ -581,6 +587,13 @@ void Engine::round(std::vector<Job *> &js) {
       any_apply = true;
     }
     x.flags = f;
+    // a round that reads every row (V' = V, or V' tested in the kernels)
+    // gathers its label words in one flat pass first
+    if (pregather && L.lk && !J->eval_only && (f & (JF_ALL | JF_PULL))) {
+      gw_start[i] = gw_tot;
+      gw_tot += L.info.nnz;
+    }
+    gw_start[i + 1] = gw_tot;
     any_cl |= (f & JF_MARK_CL) != 0;
     any_mark |= (f & (JF_MARK_NBR | JF_MARK_CL)) != 0;
     vs[i] = vt;
@@ -629,11 +642,25 @@ void Engine::round(std::vector<Job *> &js) {
     h.max_hubs = hubs;
     h.max_sunits = hub_su;
   }
+  unsigned long long *gwbuf = nullptr;
+  int64_t *dgw = nullptr;
+  if (gw_tot > 0) {
+    gwbuf = s_gw_.get<unsigned long long>(gw_tot, st_);
+    dgw = s_gwoff_.get<int64_t>(nj + 1, st_);
+    for (int i = 0; i < nj; ++i)
+      if (gw_start[i + 1] > gw_start[i]) tab[i].gw = gwbuf + gw_start[i];
+  }
   JobDev *dt = s_jobs_.get<JobDev>(nj, st_);
   int64_t *dv = s_vstart_.get<int64_t>(nj + 1, st_);
   const size_t tab_bytes = nj * (sizeof(JobDev) + 8) + 8;
-  char *hs = (char *)stage(tab_bytes + (any_coin ? nj * sizeof(CoinJob) : 0));
+  const size_t gw_bytes = gw_tot > 0 ? (nj + 1) * sizeof(int64_t) : 0;
+  char *hs = (char *)stage(tab_bytes + (any_coin ? nj * sizeof(CoinJob) : 0) + gw_bytes);
   upload_table(tab, vs, dt, dv, hs, st_);
+  if (gw_tot > 0) {
+    char *hg = hs + tab_bytes + (any_coin ? nj * sizeof(CoinJob) : 0);
+    memcpy(hg, gw_start.data(), gw_bytes);
+    CK(cudaMemcpyAsync(dgw, hg, gw_bytes, cudaMemcpyHostToDevice, st_));
+  }
   CoinJob *dcoin = nullptr;
   int64_t *dheld = nullptr;
   if (any_coin) {
@@ -651,9 +678,13 @@ void Engine::round(std::vector<Job *> &js) {
   if (timing) CK(cudaEventRecord(ev_[0], st_));
   launch_frontier(dt, dv, nj, vt, b, ctr, st_, d_);
   ++launches;
+  if (gw_tot > 0) {  // after the frontier kernel wrote this round's label words
+    launch_gather_words(dt, dgw, nj, gw_tot, st_, d_);
+    ++launches;
+  }
   if (timing) CK(cudaEventRecord(ev_[1], st_));
   launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr,
-                  tuning_for(dev_).fuse_small != 0);
+                  tun.fuse_small != 0, tun.prefetch != 0);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_coin) {
     launch_coin(dt, dcoin, b, dheld, st_, d_);
@@ -816,15 +847,14 @@ void Engine::contract(std::vector<Job *> &js) {
   // sum of its members' degrees; each fine vertex appends its entries that
   // leave its cluster to its coarse row's region.
   int64_t *boff = tmp.alloc<int64_t>(ntot + 1);
-  int64_t *rcnt = tmp.alloc<int64_t>(ntot);
+  int64_t *rpos = tmp.alloc<int64_t>(vt);
   int64_t *stmp2 = tmp.alloc<int64_t>(scan_tmp_elems(ntot + 1));
   int32_t *tnbr = tmp.alloc<int32_t>(et);
   int64_t *tw = tmp.alloc<int64_t>(et);
   int64_t *offg = store->alloc<int64_t>(ntot + 1);
   CK(cudaMemsetAsync(boff, 0, (ntot + 1) * 8, st_));
-  CK(cudaMemsetAsync(rcnt, 0, ntot * 8, st_));
   CK(cudaMemsetAsync(offg, 0, (ntot + 1) * 8, st_));
-  launch_rbound(dt, dv, nj, vt, gmap, boff, st_, d_);
+  launch_rbound(dt, dv, nj, vt, gmap, boff, rpos, st_, d_);
   scan_exclusive_i64(boff, ntot, stmp2, st_, d_);
   RowSpace R;
   memset(&R, 0, sizeof(R));
@@ -835,7 +865,7 @@ void Engine::contract(std::vector<Job *> &js) {
   R.gmapp = gmapp;
   R.rank = rank;
   R.boff = boff;
-  R.rcnt = rcnt;
+  R.rpos = rpos;
   R.tnbr = tnbr;
   R.tw = tw;
   R.ucnt = offg;  // unique entries per row, scanned into the offsets below

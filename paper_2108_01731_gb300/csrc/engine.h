@@ -231,7 +231,7 @@ class Engine {
   Scratch s_jobs_, s_vstart_, s_items_, s_cnt_, s_ctr_, s_jmoves_, s_moved_;
   Scratch s_hkeys_, s_hvals_, s_hmeta_, s_hpart_s_, s_hpart_c_, s_hstay_, s_hiso_;
   Scratch s_ljobs_, s_info_, s_obj_, s_layout_;
-  Scratch s_coin_, s_jheld_;
+  Scratch s_coin_, s_jheld_, s_gw_, s_gwoff_;
   // pinned host staging
   void *h_stage_ = nullptr;
   size_t h_stage_bytes_ = 0;

@@ -104,6 +104,8 @@ __device__ __forceinline__ unsigned long long slot_word(int32_t c, uint32_t k32)
 struct JobView {
   const int64_t *off;
   const int32_t *nbr;
+  const unsigned long long *gw;  // pre-gathered words from entry gw0 on (null: gather)
+  int64_t gw0;
   const void *w;
   const int64_t *k;
   const int32_t *L;
@@ -119,6 +121,8 @@ __device__ __forceinline__ JobView view_of(const JobDev *__restrict__ J) {
   JobView x;
   x.off = J->off;
   x.nbr = J->gnbr;  // neighbour positions in the gather layout
+  x.gw = J->gw;
+  x.gw0 = J->gw ? J->off[0] : 0;
   x.w = J->w;
   x.k = J->k;
   x.L = J->L;
@@ -177,6 +181,16 @@ __device__ __forceinline__ void label_of(const JobView &J, int32_t u, int32_t &c
     c = J.L[u];
     k32 = KNONE;
   }
+}
+
+// The same from the word gathered for entry e by k_gather_words (a
+// coalesced stream instead of a dependent random gather).
+__device__ __forceinline__ void label_at(const JobView &J, int64_t e, int32_t &c, uint32_t &k32,
+                                         uint32_t &moved) {
+  const unsigned long long x = (unsigned long long)ld_stream((const int64_t *)(J.gw + (e - J.gw0)));
+  moved |= (uint32_t)x & LK_MOVED;
+  c = (int32_t)((uint32_t)x & ~LK_MOVED);
+  k32 = (uint32_t)(x >> 32);
 }
 
 __device__ __forceinline__ long long weight_at(const JobView &J, int64_t e) {
@@ -299,6 +313,56 @@ __device__ __forceinline__ bool probe_insert(At at, Cap g, int32_t c, uint32_t k
   return false;
 }
 }  // namespace
+
+// ------------------------------------------------------- gathered words ----
+
+// The label word of every entry of the jobs that have a gw buffer, in one
+// flat pass: each warp takes 256 consecutive entries, loads their neighbour
+// positions (a coalesced stream) and then gathers all eight words a lane
+// owns before storing them, so that every thread keeps eight gathers in
+// flight and no gather waits on a table operation.
+__global__ void __launch_bounds__(256) k_gather_words(const JobDev *__restrict__ jobs,
+                                                      const int64_t *__restrict__ estart,
+                                                      int njobs, int64_t etot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 256;
+       c0 < etot; c0 += warps * 256) {
+    const int j0 = find_job(estart, njobs, c0);
+    const int64_t jend = estart[j0 + 1];
+    int32_t u[8];
+    const JobDev *Js[8];
+    int64_t dst[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t f = c0 + k * 32 + lane;
+      u[k] = -1;
+      Js[k] = nullptr;
+      dst[k] = 0;
+      if (f < etot) {
+        const int jj = f < jend ? j0 : find_job(estart, njobs, f);
+        const JobDev *J = jobs + jj;
+        dst[k] = f - estart[jj];
+        u[k] = ld_stream(J->gnbr + J->off[0] + dst[k]);
+        Js[k] = J;
+      }
+    }
+    unsigned long long x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = u[k] >= 0 ? ld_keep(Js[k]->lk + u[k]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (u[k] >= 0) Js[k]->gw[dst[k]] = x[k];
+  }
+}
+
+void launch_gather_words(const JobDev *jobs, const int64_t *estart, int njobs, int64_t etot,
+                         cudaStream_t st, const Dev &d) {
+  if (etot <= 0) return;
+  int64_t g = (etot + 2047) / 2048;
+  if (g > (int64_t)d.sms * 8) g = (int64_t)d.sms * 8;
+  k_gather_words<<<(int)g, 256, 0, st>>>(jobs, estart, njobs, etot);
+}
 
 // ---------------------------------------------------------------- V' -----
 
@@ -470,9 +534,13 @@ __device__ __forceinline__ void group_step(const JobDev *__restrict__ jobs,
   uint32_t k32 = KNONE, mbit = 0;
   long long wt = 0;
   if (has) {
-    const int32_t u = ld_stream(J.nbr + beg + gl);
     wt = weight_at(J, beg + gl);
-    label_of(J, u, c, k32, mbit);
+    if (J.gw) {
+      label_at(J, beg + gl, c, k32, mbit);
+    } else {
+      const int32_t u = ld_stream(J.nbr + beg + gl);
+      label_of(J, u, c, k32, mbit);
+    }
   }
   const bool row_moved = (__ballot_sync(FULL, mbit != 0) & gmask) != 0;
   const unsigned long long key = ((unsigned long long)gsub << 32) | (uint32_t)c;
@@ -592,6 +660,21 @@ struct Chunk {
 template <int E>
 __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_t lo, int64_t hi,
                                            int stride, int t, Chunk<E> &x) {
+  if (J.gw) {
+    x.mv = 0;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int64_t e = lo + (int64_t)i * stride + t;
+      x.c[i] = -1;
+      x.k[i] = KNONE;
+      x.w[i] = 0;
+      if (e < hi) {
+        x.w[i] = weight_at(J, beg + e);
+        label_at(J, beg + e, x.c[i], x.k[i], x.mv);
+      }
+    }
+    return;
+  }
   int32_t u[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) {
@@ -609,6 +692,54 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
     x.c[i] = -1;
     x.k[i] = KNONE;
     if (u[i] >= 0) label_of(J, u[i], x.c[i], x.k[i], x.mv);
+  }
+}
+
+// The same chunk in two steps, for a pipeline over vertices: the neighbour
+// positions first (load_pos), then, later, the weights and label words
+// gathered through those positions (load_chunk_at).
+template <int E>
+__device__ __forceinline__ void load_pos(const JobView &J, int64_t beg, int64_t lo, int64_t hi,
+                                         int stride, int t, int32_t (&u)[E]) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int64_t e = lo + (int64_t)i * stride + t;
+    u[i] = (e < hi && !J.gw) ? ld_stream(J.nbr + beg + e) : -1;
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void load_chunk_at(const JobView &J, int64_t beg, int64_t lo,
+                                              int64_t hi, int stride, int t,
+                                              const int32_t (&u)[E], Chunk<E> &x) {
+  if (J.gw) {  // words already gathered: no positions were loaded
+    load_chunk(J, beg, lo, hi, stride, t, x);
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int64_t e = lo + (int64_t)i * stride + t;
+    x.w[i] = e < hi ? weight_at(J, beg + e) : 0;
+  }
+  x.mv = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    x.c[i] = -1;
+    x.k[i] = KNONE;
+    if (u[i] >= 0) label_of(J, u[i], x.c[i], x.k[i], x.mv);
+  }
+}
+
+// Asks L2 for the label words the positions u will gather (no registers are
+// held for the results): issued for the next vertex while the current one is
+// merged, so that its gathers find the words in L2.
+template <int E>
+__device__ __forceinline__ void prefetch_words(const JobView &J, const int32_t (&u)[E]) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (u[i] < 0) continue;
+    const void *a = J.lk ? (const void *)(J.lk + u[i]) : (const void *)(J.L + u[i]);
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
   }
 }
 
@@ -826,7 +957,7 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
 // cluster scores it and empties its slot (one chunk and CS <= 2: a vertex
 // costs one step per distinct cluster), or each block scans and empties its
 // own share, so no clearing pass is needed.  Block 0 combines the results.
-template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK>
+template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK, bool PF = false>
 __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
                                                       int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -862,18 +993,49 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
   }
   PullCount::init();
   if (CS > 1) cluster.sync();  // every block's table is empty before any remote insert
+  // This block's share [lo, hi) of the row of the vertex in item it.
+  auto share = [&](const JobView &Jx, int32_t vx, int64_t &bx, int64_t &dx, int64_t &lx,
+                   int64_t &hx) {
+    bx = Jx.off[vx];
+    dx = Jx.off[vx + 1] - bx;
+    const int64_t px = (dx + CS - 1) / CS;
+    lx = (int64_t)rank * px;
+    hx = lx + px < dx ? lx + px : dx;
+  };
+  // One-chunk kernels pipeline the vertices: the next vertex's neighbour
+  // positions are loaded while this one is merged, and its label words are
+  // prefetched into L2 before the closing barriers.
+  constexpr bool PIPE = PF && CH == 1;
+  int32_t un[E];
+  if (PIPE && cid < count) {
+    const uint64_t item0 = items[cid];
+    const JobView J0 = view_of(jobs + (int)(item0 >> 32));
+    int64_t b0, d0, l0, h0;
+    share(J0, (int32_t)(uint32_t)item0, b0, d0, l0, h0);
+    load_pos<E>(J0, b0, l0, h0, THREADS, tid, un);
+  }
   for (int64_t it = cid; it < count; it += ncl) {
     const uint64_t item = items[it];
     const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
-    const int64_t beg = J.off[v];
-    const int64_t deg = J.off[v + 1] - beg;
-    const int64_t per = (deg + CS - 1) / CS;
-    const int64_t lo = (int64_t)rank * per;
-    const int64_t hi = lo + per < deg ? lo + per : deg;
+    int64_t beg, deg, lo, hi;
+    share(J, v, beg, deg, lo, hi);
     if (hi - lo > (int64_t)THREADS * E * CH) fail = true;  // excluded by the degree buckets
     Chunk<E> x;
-    load_chunk(J, beg, lo, hi, THREADS, tid, x);
+    JobView Jn = J;
+    const bool next = PIPE && it + ncl < count;
+    if (PIPE) {
+      load_chunk_at<E>(J, beg, lo, hi, THREADS, tid, un, x);
+      if (next) {
+        const uint64_t itemn = items[it + ncl];
+        Jn = view_of(jobs + (int)(itemn >> 32));
+        int64_t bn, dn, ln, hn;
+        share(Jn, (int32_t)(uint32_t)itemn, bn, dn, ln, hn);
+        load_pos<E>(Jn, bn, ln, hn, THREADS, tid, un);
+      }
+    } else {
+      load_chunk(J, beg, lo, hi, THREADS, tid, x);
+    }
     const Own o = own_of(J, v);
     // P slots per block: POW2, next_pow2(2 deg) / CS (at least 32); else 1.6
     // per entry of the row, a multiple of 32
@@ -907,6 +1069,7 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
     if (CH == 1) {
       fail |= !insert_chunk_won(x, at, geo, won);
       if (x.mv) s_rowmv = 1;
+      if (next) prefetch_words<E>(Jn, un);
     } else {
       Chunk<E> y;  // the second chunk's gathers overlap the first chunk's inserts
       load_chunk(J, beg, lo + (int64_t)THREADS * E, hi, THREADS, tid, y);
@@ -1222,10 +1385,10 @@ struct TableLaunch {
   bool init = false;
 };
 
-template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK>
+template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK, bool PF = false>
 void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream_t st,
                   TableLaunch &tl, int *launches) {
-  auto kern = k_bm_table<S, CS, THREADS, TP, E, CH, POW2, BK>;
+  auto kern = k_bm_table<S, CS, THREADS, TP, E, CH, POW2, BK, PF>;
   const size_t smem = (size_t)TP * 16;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -1257,13 +1420,13 @@ void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream
 template <typename S>
 void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes,
                    int64_t *ctr, cudaStream_t st, const Dev &d, int *launches, cudaEvent_t *ev,
-                   bool fuse_small) {
+                   bool fuse_small, bool prefetch) {
   auto mark = [&](int bk) {
     if (ev) cudaEventRecord(ev[bk], st);
   };
   static int occ[10] = {0};
   static bool init = false;
-  static TableLaunch tl[8];
+  static TableLaunch tl[8], tlp[3];
   if (!init) {
     occ[0] = occ_blocks(k_bm_group<4, S>, 256, 0);
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
@@ -1327,14 +1490,29 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
     ++*launches;
   }
   mark(B_W128);
-  if (b.seg_cap[B_WARP] > 0)
-    launch_table<S, 1, 128, WARP_CAP, 2, 1, true, B_WARP>(jobs, b, ctr, st, tl[7], launches);
+  if (b.seg_cap[B_WARP] > 0) {
+    if (prefetch)
+      launch_table<S, 1, 128, WARP_CAP, 2, 1, true, B_WARP, true>(jobs, b, ctr, st, tlp[0],
+                                                                   launches);
+    else
+      launch_table<S, 1, 128, WARP_CAP, 2, 1, true, B_WARP>(jobs, b, ctr, st, tl[7], launches);
+  }
   mark(B_WARP);
-  if (b.seg_cap[B_BLK] > 0)
-    launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK>(jobs, b, ctr, st, tl[0], launches);
+  if (b.seg_cap[B_BLK] > 0) {
+    if (prefetch)
+      launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK, true>(jobs, b, ctr, st, tlp[1],
+                                                                launches);
+    else
+      launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK>(jobs, b, ctr, st, tl[0], launches);
+  }
   mark(B_BLK);
-  if (b.seg_cap[B_T4K] > 0)
-    launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K>(jobs, b, ctr, st, tl[1], launches);
+  if (b.seg_cap[B_T4K] > 0) {
+    if (prefetch)
+      launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K, true>(jobs, b, ctr, st, tlp[2],
+                                                                launches);
+    else
+      launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K>(jobs, b, ctr, st, tl[1], launches);
+  }
   mark(B_T4K);
   if (b.seg_cap[B_T8K] > 0)
     launch_table<S, 1, 1024, TP_8K, 4, 2, false, B_T8K>(jobs, b, ctr, st, tl[2], launches);
@@ -1371,11 +1549,12 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev, bool fuse_small) {
+                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small);
+    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small, prefetch);
   else
-    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small);
+    bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small,
+                           prefetch);
 }
 
 // --------------------------------------------------------------- apply ----

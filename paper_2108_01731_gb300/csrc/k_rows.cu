@@ -4,17 +4,20 @@
 // their weights in a hash table.  This is the paper's parallel aggregation of
 // edges by endpoint clusters, done per coarse row, with no global sort.
 //
-//   bound    rbound[C] = sum of the degrees of C's members; its scan gives
-//            each coarse row a region [boff[C], boff[C+1]) of the flat entry
-//            space, large enough for all of its entries;
-//   emit     one warp per fine vertex u reads its row (coalesced), looks up
-//            every neighbour's coarse id and appends the entries that leave
-//            C = coarse(u) to C's region (one atomic per 32 entries on the
-//            row's fill count rcnt[C]);
-//   classes  rows by rcnt: a single entry is already final; G lanes per row
+//   bound    one atomic per fine vertex u adds deg(u) to rbound[C] for its
+//            coarse vertex C and keeps the old value as u's place rpos[u]
+//            in C's region; the scan of rbound gives each coarse row a region
+//            [boff[C], boff[C+1]) of the flat entry space;
+//   emit     a warp takes 32 consecutive fine vertices, whose rows are one
+//            contiguous run of entries, reads them coalesced, looks up every
+//            neighbour's coarse id and writes (local coarse id of the far
+//            end, w) at boff[C] + rpos[u] + j; an entry inside C becomes a
+//            hole (-1) that the merges skip;
+//   classes  rows by region length: a single entry is already final (or a
+//            hole); G lanes per row
 //            (<= 4 .. 32 entries), a warp with a shared table (<= 256), a
-//            block with a shared table (<= 4096), global tables in bounded
-//            windows (more);
+//            block with a shared table (<= 4096, and <= 8192 with 1024
+//            threads and 192 KB), global tables in bounded windows (more);
 //   reduce   every row merges its region in place: its unique entries are
 //            written back to the start of the region, their number to
 //            ucnt[C]; a scan of ucnt gives the coarse offsets and the rows
@@ -62,7 +65,7 @@ __device__ __forceinline__ Row row_of(const RowSpace &R, int32_t C) {
   Row r;
   r.C = C;
   r.rb = R.boff[C];
-  r.cnt = R.rcnt[C];
+  r.cnt = R.boff[C + 1] - r.rb;
   return r;
 }
 
@@ -77,61 +80,97 @@ __device__ __forceinline__ long long warp_sum(long long x) {
 
 __global__ void k_rbound(const CJob *__restrict__ jobs, const int64_t *__restrict__ vstart,
                          int njobs, int64_t vt, const int32_t *__restrict__ gmap,
-                         int64_t *rbound) {
+                         int64_t *rbound, int64_t *rpos) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vt;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int j = find_job(vstart, njobs, i);
     const CJob *J = jobs + j;
     const int64_t v = i - vstart[j];
     const int64_t deg = J->off[v + 1] - J->off[v];
-    if (deg) atomicAdd((unsigned long long *)&rbound[gmap[i]], (unsigned long long)deg);
+    rpos[i] = deg ? (int64_t)atomicAdd((unsigned long long *)&rbound[gmap[i]],
+                                       (unsigned long long)deg)
+                  : 0;
   }
 }
 
 void launch_rbound(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vt,
-                   const int32_t *gmap, int64_t *rbound, cudaStream_t st, const Dev &d) {
+                   const int32_t *gmap, int64_t *rbound, int64_t *rpos, cudaStream_t st,
+                   const Dev &d) {
   if (vt <= 0) return;
-  k_rbound<<<grid_of(vt, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vt, gmap, rbound);
+  k_rbound<<<grid_of(vt, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vt, gmap, rbound, rpos);
 }
 
-// One warp per fine vertex u of coarse row C: every entry whose far end lies
-// in another coarse vertex is appended to C's region as (local coarse id of
-// the far end, w).  32 entries at a time, with one atomic on rcnt[C].
+// One entry of fine vertex u (flat index i) of coarse row C, written at its
+// place pos of C's region: the far end's job-local coarse id, or a hole.
+__device__ __forceinline__ void emit_one(const RowSpace &R, const CJob *J, int64_t vs,
+                                         int32_t cbase, int32_t C, int64_t e, int64_t pos,
+                                         long long &nintra) {
+  const int32_t cv = R.gmapp[vs + __ldg(J->gnbr + e)];
+  const bool intra = cv == C;
+  R.tnbr[pos] = intra ? -1 : cv - cbase;
+  R.tw[pos] = load_w(J->w, J->wtype, e);
+  nintra += intra ? 1 : 0;
+}
+
+// A warp takes 32 consecutive fine vertices.  Inside one job their rows are
+// one contiguous run of entries [off[v0], off[v0 + 32]): the lanes stream it,
+// each entry finding its vertex by a binary search over the 33 row starts in
+// shared memory, and write it at its vertex's place in its coarse row's
+// region.  A window that crosses into another job (at most one per job)
+// walks each lane's own vertex instead.
 __global__ void __launch_bounds__(256) k_emit_rows(RowSpace R, int64_t vt) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int64_t s_e[8][33];
+  __shared__ int64_t s_dst[8][32];
+  __shared__ int32_t s_c[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   long long nintra = 0;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < vt;
-       i += warps_total) {
-    const int j = find_job(R.vstart, R.njobs, i);
-    const CJob *J = R.jobs + j;
-    const int64_t v = i - R.vstart[j];
-    const int64_t vs = R.vstart[j];
-    const int32_t C = R.gmap[i];
-    const int32_t cbase = (int32_t)R.rank[vs];
-    const int64_t beg = J->off[v], end = J->off[v + 1];
-    if (beg == end) continue;
-    const int64_t rb = R.boff[C];
-    for (int64_t e0 = beg; e0 < end; e0 += 32) {
-      const int64_t e = e0 + lane;
-      int32_t cv = -1;
-      long long w = 0;
-      if (e < end) {
-        cv = R.gmapp[vs + __ldg(J->gnbr + e)];
-        w = load_w(J->w, J->wtype, e);
+  for (int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; i0 < vt;
+       i0 += warps_total * 32) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < vt;
+    int j = 0;
+    int64_t eb = 0, ee = 0, dst = 0;
+    int32_t C = 0;
+    if (valid) {
+      j = find_job(R.vstart, R.njobs, i);
+      const CJob *J = R.jobs + j;
+      const int64_t v = i - R.vstart[j];
+      eb = J->off[v];
+      ee = J->off[v + 1];
+      C = R.gmap[i];
+      if (ee > eb) dst = R.boff[C] + R.rpos[i];
+    }
+    const int j0 = __shfl_sync(FULL, j, 0);
+    if (__all_sync(FULL, !valid || j == j0)) {
+      // lanes past the end take the last vertex's end as an empty row
+      const int last = vt - 1 - i0 < 31 ? (int)(vt - 1 - i0) : 31;
+      const int64_t e_end = __shfl_sync(FULL, ee, last);
+      if (!valid) eb = ee = e_end;
+      s_e[wib][lane] = eb;
+      if (lane == 31) s_e[wib][32] = ee;
+      s_dst[wib][lane] = dst;
+      s_c[wib][lane] = C;
+      __syncwarp();
+      const CJob *J = R.jobs + j0;
+      const int64_t vs = R.vstart[j0];
+      const int32_t cbase = (int32_t)R.rank[vs];
+      const int64_t e1 = s_e[wib][32];
+      for (int64_t e = s_e[wib][0] + lane; e < e1; e += 32) {
+        int lo = 0, hi = 32;  // the last vertex whose row starts at or before e
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_e[wib][mid] <= e) lo = mid; else hi = mid;
+        }
+        emit_one(R, J, vs, cbase, s_c[wib][lo], e, s_dst[wib][lo] + (e - s_e[wib][lo]),
+                 nintra);
       }
-      const bool inter = e < end && cv != C;
-      nintra += (e < end && !inter) ? 1 : 0;
-      const unsigned b = __ballot_sync(FULL, inter);
-      if (!b) continue;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd((unsigned long long *)&R.rcnt[C], (unsigned long long)__popc(b));
-      base = __shfl_sync(FULL, base, 0);
-      if (inter) {
-        const int64_t pos = rb + (int64_t)base + __popc(b & lanemask_lt());
-        R.tnbr[pos] = cv - cbase;
-        R.tw[pos] = w;
-      }
+      __syncwarp();
+    } else if (valid) {
+      const CJob *J = R.jobs + j;
+      const int64_t vs = R.vstart[j];
+      const int32_t cbase = (int32_t)R.rank[vs];
+      for (int64_t e = eb; e < ee; ++e) emit_one(R, J, vs, cbase, C, e, dst + (e - eb), nintra);
     }
   }
   nintra = warp_sum(nintra);
@@ -140,7 +179,7 @@ __global__ void __launch_bounds__(256) k_emit_rows(RowSpace R, int64_t vt) {
 
 void launch_emit_rows(const RowSpace &R, int64_t vt, cudaStream_t st, const Dev &d) {
   if (vt <= 0) return;
-  k_emit_rows<<<grid_of(vt * 32, 256, d), 256, 0, st>>>(R, vt);
+  k_emit_rows<<<grid_of((vt + 31) / 32 * 32, 256, d), 256, 0, st>>>(R, vt);
 }
 
 // ------------------------------------------------------------ classes ----
@@ -153,12 +192,14 @@ __device__ __forceinline__ int row_class(int64_t cnt) {
   if (cnt <= 32) return RC_G32;
   if (cnt <= RC_WARP_MAX) return RC_WARP;
   if (cnt <= RC_BLOCK_MAX) return RC_BLOCK;
+  if (cnt <= RC_BLOCK8K_MAX) return RC_BLOCK8K;
   return RC_BIG;
 }
 
 // fill = false: rows per class into cnt[]; fill = true: the rows of class c
 // into items[seg[c] ..] (cnt[] then serves as the cursors, zeroed first), and
-// a row of one entry gets ucnt = 1 (it is already in place).
+// a row of one entry that is not a hole gets ucnt = 1 (it is already in
+// place).
 __global__ void __launch_bounds__(256) k_rows_classify(RowSpace R, int64_t ntot, bool fill,
                                                        unsigned long long *cnt,
                                                        const int64_t *__restrict__ seg,
@@ -170,9 +211,9 @@ __global__ void __launch_bounds__(256) k_rows_classify(RowSpace R, int64_t ntot,
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ntot;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t C = base + threadIdx.x;
-    const int64_t rc = C < ntot ? R.rcnt[C] : 0;
+    const int64_t rc = C < ntot ? R.boff[C + 1] - R.boff[C] : 0;
     const int cls = row_class(rc);
-    if (fill && rc == 1) R.ucnt[C] = 1;
+    if (fill && rc == 1 && R.tnbr[R.boff[C]] >= 0) R.ucnt[C] = 1;  // one entry, not a hole
     const unsigned peers = __match_any_sync(FULL, cls);
     const int leader = __ffs(peers) - 1;
     if (cls >= 0) {
@@ -221,13 +262,13 @@ __global__ void __launch_bounds__(256) k_rows_group(RowSpace R, const int32_t *_
     r.rb = 0;
     r.C = 0;
     if (valid) r = row_of(R, items[it]);
-    const bool has = valid && gl < r.cnt;
     int32_t cv = -1;
     long long w = 0;
-    if (has) {
+    if (valid && gl < r.cnt) {
       cv = R.tnbr[r.rb + gl];
       w = R.tw[r.rb + gl];
     }
+    const bool has = cv >= 0;  // holes (entries inside the cluster) are skipped
     // every lane holds its entry before any lane writes the row back
     const unsigned long long key =
         ((unsigned long long)gsub << 32) | (uint32_t)(has ? cv : -1 - gl);
@@ -327,18 +368,19 @@ __global__ void __launch_bounds__(128) k_rows_warp(RowSpace R, const int32_t *__
 
 // ----------------------------------- rows of <= 4096: block + shared table --
 
-constexpr int RB_THREADS = 512, RB_E = RC_BLOCK_MAX / RB_THREADS;
-constexpr int RB_CAP = 2 * RC_BLOCK_MAX;
-
-__global__ void __launch_bounds__(RB_THREADS) k_rows_block(RowSpace R,
-                                                           const int32_t *__restrict__ items,
-                                                           int64_t count) {
+// One block per row, THREADS x E entries, a table of 2 slots per entry in
+// shared memory (int32 keys and int64 sums: 12 bytes a slot).
+template <int THREADS, int E>
+__global__ void __launch_bounds__(THREADS) k_rows_block(RowSpace R,
+                                                        const int32_t *__restrict__ items,
+                                                        int64_t count) {
+  constexpr int CAP = 2 * THREADS * E;
   extern __shared__ __align__(16) unsigned char rb_smem[];
   unsigned long long *tval = (unsigned long long *)rb_smem;
-  int32_t *tkey = (int32_t *)(tval + RB_CAP);
+  int32_t *tkey = (int32_t *)(tval + CAP);
   __shared__ int s_cnt;
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int s = tid; s < RB_CAP; s += RB_THREADS) {
+  for (int s = tid; s < CAP; s += THREADS) {
     tkey[s] = -1;
     tval[s] = 0;
   }
@@ -348,23 +390,23 @@ __global__ void __launch_bounds__(RB_THREADS) k_rows_block(RowSpace R,
     const Row r = row_of(R, items[it]);
     const int64_t cap = next_pow2(2 * r.cnt);
     const int lg = lg_of(cap);
-    int32_t cv[RB_E];
-    long long w[RB_E];
+    int32_t cv[E];
+    long long w[E];
 #pragma unroll
-    for (int i = 0; i < RB_E; ++i) {
+    for (int i = 0; i < E; ++i) {
       cv[i] = -1;
       w[i] = 0;
-      const int64_t t = tid + (int64_t)RB_THREADS * i;
+      const int64_t t = tid + (int64_t)THREADS * i;
       if (t < r.cnt) {
         cv[i] = R.tnbr[r.rb + t];
         w[i] = R.tw[r.rb + t];
       }
     }
 #pragma unroll
-    for (int i = 0; i < RB_E; ++i)
+    for (int i = 0; i < E; ++i)
       if (cv[i] >= 0) table_add(tkey, tval, lg, cv[i], w[i]);
     __syncthreads();  // every entry is read and inserted before the row is rewritten
-    for (int s0 = 0; s0 < (int)cap; s0 += RB_THREADS) {
+    for (int s0 = 0; s0 < (int)cap; s0 += THREADS) {
       const int s = s0 + tid;
       const bool occ = s < (int)cap && tkey[s] >= 0;
       const unsigned b = __ballot_sync(FULL, occ);
@@ -388,16 +430,25 @@ __global__ void __launch_bounds__(RB_THREADS) k_rows_block(RowSpace R,
   }
 }
 
+template <int THREADS, int E>
+void launch_rows_block(const RowSpace &R, const int32_t *items, int64_t count, int &occ,
+                       cudaStream_t st, const Dev &d) {
+  constexpr int smem = 2 * THREADS * E * 12;
+  auto kern = k_rows_block<THREADS, E>;
+  if (!occ) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, THREADS, smem);
+    occ = nb > 0 ? nb : 1;
+  }
+  int64_t blocks = count;
+  if (blocks > (int64_t)d.sms * occ) blocks = (int64_t)d.sms * occ;
+  kern<<<(int)blocks, THREADS, smem, st>>>(R, items, count);
+}
+
 void launch_rows_small(const RowSpace &R, const int32_t *items, const int64_t *seg,
                        const int64_t *cnt, cudaStream_t st, const Dev &d, int *launches) {
-  static int occ_b = 0;
-  if (!occ_b) {
-    const int smem = RB_CAP * 12;
-    cudaFuncSetAttribute(k_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rows_block, RB_THREADS, smem);
-    occ_b = nb > 0 ? nb : 1;
-  }
+  static int occ_b = 0, occ_b8 = 0;
   auto groups = [&](int c, int G, auto kern) {
     if (cnt[c] <= 0) return;
     const int64_t warps = (cnt[c] * G + 31) / 32;
@@ -418,10 +469,13 @@ void launch_rows_small(const RowSpace &R, const int32_t *items, const int64_t *s
     ++*launches;
   }
   if (cnt[RC_BLOCK] > 0) {
-    int64_t blocks = cnt[RC_BLOCK];
-    if (blocks > (int64_t)d.sms * occ_b) blocks = (int64_t)d.sms * occ_b;
-    k_rows_block<<<(int)blocks, RB_THREADS, RB_CAP * 12, st>>>(R, items + seg[RC_BLOCK],
-                                                               cnt[RC_BLOCK]);
+    launch_rows_block<512, RC_BLOCK_MAX / 512>(R, items + seg[RC_BLOCK], cnt[RC_BLOCK], occ_b,
+                                               st, d);
+    ++*launches;
+  }
+  if (cnt[RC_BLOCK8K] > 0) {
+    launch_rows_block<1024, RC_BLOCK8K_MAX / 1024>(R, items + seg[RC_BLOCK8K], cnt[RC_BLOCK8K],
+                                                   occ_b8, st, d);
     ++*launches;
   }
 }
@@ -437,7 +491,7 @@ __global__ void k_big_bounds(const RowSpace R, const int32_t *__restrict__ items
                              int64_t *bound) {
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H;
        h += (int64_t)gridDim.x * blockDim.x) {
-    bound[h] = R.rcnt[items[h]];
+    bound[h] = R.boff[items[h] + 1] - R.boff[items[h]];
   }
 }
 
@@ -572,29 +626,46 @@ void launch_big_window(const RowSpace &R, const int32_t *items, const BigRows &B
 
 // ------------------------------------------------------------- copy ------
 
-// Row C's unique entries from the start of its flat range to offg[C].
-template <int G>
+// The unique entries of every row, from the start of its region to offg[C].
+// A warp takes 32 consecutive rows: their outputs are one contiguous segment
+// [offg[r0], offg[r0 + 32]), written coalesced; each position finds its row
+// by a binary search over the 33 offsets held in shared memory.
 __global__ void __launch_bounds__(256) k_rows_copy(const RowSpace R, int64_t ntot,
                                                    const int64_t *__restrict__ offg,
                                                    int32_t *nbr_out, int64_t *w_out) {
-  const int lane = threadIdx.x & 31;
-  const int gl = lane & (G - 1);
-  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
-  for (int64_t C = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; C < ntot; C += groups) {
-    const int64_t dst = offg[C], nu = offg[C + 1] - dst;
-    if (nu == 0) continue;
-    const int64_t src = R.boff[C];
-    for (int64_t t = gl; t < nu; t += G) {
-      nbr_out[dst + t] = R.tnbr[src + t];
-      w_out[dst + t] = R.tw[src + t];
+  __shared__ int64_t s_off[8][33];
+  __shared__ int64_t s_src[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; r0 < ntot;
+       r0 += warps_total * 32) {
+    const int64_t r = r0 + lane;
+    s_off[wib][lane] = offg[r < ntot ? r : ntot];
+    if (lane == 0) s_off[wib][32] = offg[r0 + 32 < ntot ? r0 + 32 : ntot];
+    s_src[wib][lane] = r < ntot ? R.boff[r] : 0;
+    __syncwarp();
+    const int64_t o0 = s_off[wib][0], o1 = s_off[wib][32];
+    for (int64_t p = o0 + lane; p < o1; p += 32) {
+      // the last row whose output starts at or before p (rows without
+      // entries share their offset with the next row)
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[wib][mid] <= p) lo = mid; else hi = mid;
+      }
+      const int64_t src = s_src[wib][lo] + (p - s_off[wib][lo]);
+      nbr_out[p] = R.tnbr[src];
+      w_out[p] = R.tw[src];
     }
+    __syncwarp();
   }
 }
 
 void launch_rows_copy(const RowSpace &R, int64_t ntot, const int64_t *offg, int32_t *nbr_out,
                       int64_t *w_out, cudaStream_t st, const Dev &d) {
   if (ntot <= 0) return;
-  k_rows_copy<4><<<grid_of(ntot * 4, 256, d), 256, 0, st>>>(R, ntot, offg, nbr_out, w_out);
+  k_rows_copy<<<grid_of((ntot + 31) / 32 * 32, 256, d), 256, 0, st>>>(R, ntot, offg, nbr_out,
+                                                                      w_out);
 }
 
 // ------------------------------------------------ sorted rows (export) ----

@@ -122,6 +122,10 @@ struct JobDev {
   // and gnbr[e] = pos[nbr[e]] is what the best-move kernels gather through
   const int32_t *pos;
   const int32_t *gnbr;  // = nbr without a layout
+  // this round's label words already gathered per entry (null: gather through
+  // gnbr): gw[e - off[0]] = lk[gnbr[e]], written by k_gather_words in rounds
+  // that read every row
+  unsigned long long *gw;
   int64_t n;
   int64_t p, q;
   // the next round tests V' in the kernels (JF_PULL) instead of marking it
@@ -311,13 +315,19 @@ struct Dev {
 };
 
 // Round kernels (k_round.cu).
+// gw[f - estart[j]] of job j = its label word of entry off[0] + (f - estart[j])
+// for f in [estart[j], estart[j+1]) (estart[njobs] = etot; jobs without a gw
+// buffer have no entries there).
+void launch_gather_words(const JobDev *jobs, const int64_t *estart, int njobs, int64_t etot,
+                         cudaStream_t st, const Dev &d);
 void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
 // ev (nullable, NB events): ev[b] is recorded after degree bucket b's kernels.
-// fuse_small: the <= 4 .. <= 32 buckets in one resident launch (k_bm_small).
+// fuse_small: the <= 4 .. <= 32 buckets in one resident launch (k_bm_small);
+// prefetch: the one-chunk table kernels pipeline their vertices.
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev, bool fuse_small);
+                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch);
 // jmoves[2j] = moves of job j, jmoves[2j + 1] = entries of its movers' rows.
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);
@@ -384,9 +394,12 @@ void scan_exclusive_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st, co
 
 // Compress by rows (k_rows.cu).  Classes of coarse rows by the number of
 // entries of their members.
-enum RowClass : int { RC_G4 = 0, RC_G8, RC_G16, RC_G32, RC_WARP, RC_BLOCK, RC_BIG, RC_N };
-constexpr int RC_WARP_MAX = 256;    // warp + shared table of 2 slots per entry
-constexpr int RC_BLOCK_MAX = 4096;  // block + shared table of 2 slots per entry
+enum RowClass : int {
+  RC_G4 = 0, RC_G8, RC_G16, RC_G32, RC_WARP, RC_BLOCK, RC_BLOCK8K, RC_BIG, RC_N
+};
+constexpr int RC_WARP_MAX = 256;     // warp + shared table of 2 slots per entry
+constexpr int RC_BLOCK_MAX = 4096;   // 512-thread block + shared table of 2 slots per entry
+constexpr int RC_BLOCK8K_MAX = 8192; // 1024-thread block + 192 KB shared table
 constexpr int RC_CHUNK = 4096;      // entries per insertion unit of a big row
 constexpr int RC_SCHUNK = 4096;     // table slots per compaction unit of a big row
 
@@ -397,8 +410,8 @@ struct RowSpace {
   const int32_t *gmapp;     // global coarse id at the flat gather positions
   const int64_t *rank;      // rank[vstart_j] = first global coarse id of job j
   const int64_t *boff;      // [ntot + 1] region of coarse row C: [boff[C], boff[C+1])
-  int64_t *rcnt;            // [ntot] entries appended to each region (zeroed)
-  int32_t *tnbr;            // [entries] job-local coarse id of the far end
+  const int64_t *rpos;      // [vt] place of each fine vertex's entries in its region
+  int32_t *tnbr;            // [entries] job-local coarse id of the far end, -1: a hole
   int64_t *tw;              // [entries] weight
   int64_t *ucnt;            // [ntot + 1] unique entries per row (zeroed)
   unsigned long long *intra;  // entries inside a cluster (counted)
@@ -416,10 +429,12 @@ struct BigRows {
   int64_t H;
 };
 
-// rbound[gmap[i]] += deg(i) for every flat vertex (rbound zeroed).
+// rbound[gmap[i]] += deg(i) for every flat vertex (rbound zeroed); rpos[i]
+// receives the value before the addition.
 void launch_rbound(const CJob *jobs, const int64_t *vstart, int njobs, int64_t vt,
-                   const int32_t *gmap, int64_t *rbound, cudaStream_t st, const Dev &d);
-// Appends every inter-cluster entry to its coarse row's region.
+                   const int32_t *gmap, int64_t *rbound, int64_t *rpos, cudaStream_t st,
+                   const Dev &d);
+// Writes every entry into its coarse row's region (intra-cluster ones as holes).
 void launch_emit_rows(const RowSpace &R, int64_t vt, cudaStream_t st, const Dev &d);
 void launch_rows_classify(const RowSpace &R, int64_t ntot, bool fill, unsigned long long *cnt,
                           const int64_t *seg, int32_t *items, cudaStream_t st, const Dev &d);

@@ -39,7 +39,8 @@ class lcc_schedule(C.Structure):
 
 
 class lcc_tuning(C.Structure):
-    _fields_ = [("warp_max", C.c_int32), ("fuse_small", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("warp_max", C.c_int32), ("fuse_small", C.c_int32), ("prefetch", C.c_int32),
+                ("pregather", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class lcc_stats(C.Structure):
@@ -337,29 +338,37 @@ def lcc_objective(g, lambda_p, lambda_q, mode, labels):
     return num, den.value
 
 
+def _tuning_dict(t):
+    return {"warp_max": t.warp_max, "fuse_small": t.fuse_small, "prefetch": t.prefetch,
+            "pregather": t.pregather}
+
+
 def lcc_get_tuning(device=0):
-    """The kernel tuning used on `device`: {"warp_max", "fuse_small"}."""
+    """The kernel tuning used on `device`: {"warp_max", "fuse_small", "prefetch",
+    "pregather"}."""
     t = lcc_tuning()
     _check(load().lcc_get_tuning(int(device), C.byref(t)))
-    return {"warp_max": t.warp_max, "fuse_small": t.fuse_small}
+    return _tuning_dict(t)
 
 
-def lcc_set_tuning(device, warp_max, fuse_small=1):
+def lcc_set_tuning(device, warp_max, fuse_small=1, prefetch=0, pregather=1):
     t = lcc_tuning()
     t.warp_max = int(warp_max)
     t.fuse_small = int(fuse_small)
+    t.prefetch = int(prefetch)
+    t.pregather = int(pregather)
     _check(load().lcc_set_tuning(int(device), C.byref(t)))
 
 
 def lcc_autotune(g, lambda_p, lambda_q, mode, cache_path=None):
-    """Times every tuning (warp_max x fuse_small) on three best-move rounds of
-    g (or reads the cache file's line for this device) and applies the
-    fastest; returns it as {"warp_max", "fuse_small"}."""
+    """Times tunings on three best-move rounds of g, one field at a time
+    (warp_max, then fuse_small, prefetch and pregather), or reads the cache file's line
+    for this device, and applies the fastest; returns it as a dict."""
     t = lcc_tuning()
     path = cache_path.encode() if cache_path else None
     _check(load().lcc_autotune(g.handle, int(lambda_p), int(lambda_q), int(mode), path,
                                C.byref(t)))
-    return {"warp_max": t.warp_max, "fuse_small": t.fuse_small}
+    return _tuning_dict(t)
 
 
 def lcc_desired_noalloc(off, nbr, w, k, lambda_p, lambda_q, labels, K, out, stream=None):

@@ -229,3 +229,23 @@ def test_twin_round_trace(coin):
     again = T.cluster_trace(g["off"], g["nbr"], g["w"], 1, 1, mode=T.NODEW_DEGREE, coin=coin,
                             seed=5, threads=1)[1]
     assert np.array_equal(again, tr)
+
+
+def test_exact_range_bound_equals_the_oracles():
+    """Custom node weights summing to 2^32: p = 2^61 puts p * (sum k)^2 at
+    exactly 2^125 and both the twin and the oracle refuse; p = 2^61 - 1 is
+    accepted by both with the same result."""
+    import torch
+    import oracle as O
+    from paper_2108_01731_gb300 import inputs as I
+    g = I.to_numpy(I.pairs_to_csr(torch.tensor([0, 1, 2, 0]), torch.tensor([1, 2, 3, 3]), 5))
+    k = np.full(5, 1 << 30, np.int64)
+    k[4] = 0
+    with pytest.raises(Exception):
+        T.cluster(g["off"], g["nbr"], None, 1 << 61, 1, mode=T.NODEW_CUSTOM, k=k)
+    with pytest.raises(OverflowError):
+        O.cluster(g["off"], g["nbr"], None, 1 << 61, 1, mode=O.NODEW_CUSTOM, k=k)
+    p = (1 << 61) - 1
+    a = T.cluster(g["off"], g["nbr"], None, p, 1, mode=T.NODEW_CUSTOM, k=k)
+    b = O.cluster(g["off"], g["nbr"], None, p, 1, mode=O.NODEW_CUSTOM, k=k)
+    assert np.array_equal(a[0], b[0]) and a[1:4] == b[1:4]

@@ -261,17 +261,17 @@ def test_tuning_routes_without_changing_results(L, tmp_path):
             g = GRAPHS[name]
             G = L.lcc_load_csr(g["off"], g["nbr"], g["w"])
             wl, num, _, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode)
-            for fs in (0, 1):
+            for fs, pf, pg in ((0, 0, 0), (1, 0, 1), (0, 1, 1), (1, 1, 0)):
                 for wm in (32, 64, 128, 256):
-                    L.lcc_set_tuning(0, wm, fs)
+                    L.lcc_set_tuning(0, wm, fs, pf, pg)
                     labels, _, st = L.lcc_cluster(G, p, q, mode, None)
-                    assert np.array_equal(labels, wl), (name, wm, fs)
+                    assert np.array_equal(labels, wl), (name, wm, fs, pf, pg)
                     assert st["obj_num"] == num and st["edges_scanned"] == wst[2]
             G.free()
         graphs = [GRAPHS[x] for x in ("sbm", "rmat", "cl")]
         Gs = [L.lcc_load_csr(g["off"], g["nbr"], g["w"]) for g in graphs]
         for fs in (0, 1):
-            L.lcc_set_tuning(0, 256, fs)
+            L.lcc_set_tuning(0, 256, fs, fs, 1 - fs)
             labs, _ = L.lcc_cluster_batch(Gs, [1] * 3, [1] * 3, [O.NODEW_DEGREE] * 3)
             for g, lab in zip(graphs, labs):
                 wl, *_ = O.cluster(g["off"], g["nbr"], g["w"], 1, 1, mode=O.NODEW_DEGREE)
@@ -283,17 +283,21 @@ def test_tuning_routes_without_changing_results(L, tmp_path):
         path = tmp_path / "tuning.txt"
         t = L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path))
         assert t["warp_max"] in (32, 64, 128, 256) and t["fuse_small"] in (0, 1)
+        assert t["prefetch"] in (0, 1) and t["pregather"] in (0, 1)
         assert L.lcc_get_tuning(0) == t
-        assert path.read_text().strip().endswith(" %d %d" % (t["warp_max"], t["fuse_small"]))
-        L.lcc_set_tuning(0, 32 if t["warp_max"] != 32 else 256, 1 - t["fuse_small"])
+        assert path.read_text().strip().endswith(
+            " %d %d %d %d" % (t["warp_max"], t["fuse_small"], t["prefetch"], t["pregather"]))
+        L.lcc_set_tuning(0, 32 if t["warp_max"] != 32 else 256, 1 - t["fuse_small"],
+                         1 - t["prefetch"], 1 - t["pregather"])
         assert L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path)) == t
         assert L.lcc_get_tuning(0) == t
         G.free()
-        for bad in ((0, 1), (48, 1), (512, 1), (256, 2)):
+        for bad in ((0, 1), (48, 1), (512, 1), (256, 2), (256, 1, 2), (256, 1, 0, 2)):
             with pytest.raises(L.LccError):
                 L.lcc_set_tuning(0, *bad)
     finally:
-        L.lcc_set_tuning(0, before["warp_max"], before["fuse_small"])
+        L.lcc_set_tuning(0, before["warp_max"], before["fuse_small"], before["prefetch"],
+                         before["pregather"])
 
 
 def check_cluster_case(L, case):

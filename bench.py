@@ -612,6 +612,7 @@ def run_ours(args, rank, world, local):
                                   "frac": round(edges / (bm_ms / 1e3) / gather_rate, 4),
                                   "source": "torch.index_select, 2^28 uniform indices "
                                             "into a 2^26-word int64 table, timed here"},
+                "ms_gather_pass": round(statistics.mean(s["ms_gather"] for s in stats), 2),
                 "ms_per_bucket": dict(zip(BUCKETS,
                                           [round(statistics.mean(s["ms_bucket"][i]
                                                                  for s in stats), 2)

@@ -142,7 +142,9 @@ typedef struct lcc_stats {
   int64_t obj_den;         /* q, or q * 2m in LCC_NODEW_DEGREE mode */
   double objective;        /* (double)num / den */
   /* device time in ms, filled when LCC_SCHED_TIMING is set */
-  double ms_bestmove;      /* best-move kernels (all degree buckets) */
+  double ms_bestmove;      /* best-move kernels (all degree buckets, and the
+                              pass that gathers the label words of a round
+                              that reads every row: ms_gather) */
   double ms_round_other;   /* frontier, apply and marking kernels */
   double ms_contract;      /* compression (relabel, sort, reduce, CSR) */
   double ms_other;         /* flatten, refinement set-up, final labels */
@@ -171,6 +173,8 @@ typedef struct lcc_stats {
      calls_capped == 0 shows that every call converged. */
   int64_t calls;
   int64_t calls_capped;
+  double ms_gather;        /* the gathered-word passes (lcc_tuning.pregather),
+                              included in ms_bestmove */
 } lcc_stats;
 
 typedef struct lcc_graph lcc_graph;

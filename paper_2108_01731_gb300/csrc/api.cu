@@ -225,6 +225,7 @@ static void fill_stats(const Job &J, const Engine &E, lcc_stats *s, double ms_to
   s->bytes_contract_min = E.stats.contract_min_bytes;
   s->calls = J.calls;
   s->calls_capped = J.calls_capped;
+  s->ms_gather = E.stats.ms_gather;
   for (int i = 0; i < NB && i < 16; ++i) {
     s->ms_bucket[i] = E.stats.ms_bucket[i];
     s->bucket_entries[i] = E.stats.bucket_entries[i];

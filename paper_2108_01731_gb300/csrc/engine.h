@@ -176,6 +176,7 @@ struct EngineStats {
   int64_t contract_min_bytes = 0;  // least bytes of the contractions (lcc_stats)
   int64_t rounds = 0;
   double ms_bm = 0, ms_round_other = 0, ms_contract = 0, ms_other = 0;
+  double ms_gather = 0;  // the gathered-word passes (part of ms_bm)
   double ms_bucket[NB] = {0};
   int64_t bucket_entries[NB] = {0};
   int64_t bucket_vertices[NB] = {0};
@@ -238,6 +239,7 @@ class Engine {
   void *h_stage2_ = nullptr;
   size_t h_stage2_bytes_ = 0;
   cudaEvent_t ev_[8];
+  cudaEvent_t ev_gw_;  // end of the gathered-word pass of a round
   cudaEvent_t bev_[NB];
   void *stage(size_t bytes);
   void *stage2(size_t bytes);

@@ -55,7 +55,7 @@ class lcc_stats(C.Structure):
                 ("pairs_sorted", C.c_int64), ("kernel_launches", C.c_int64),
                 ("ms_bucket", C.c_double * 16), ("bucket_entries", C.c_int64 * 16),
                 ("bucket_vertices", C.c_int64 * 16), ("bytes_contract_min", C.c_int64),
-                ("calls", C.c_int64), ("calls_capped", C.c_int64)]
+                ("calls", C.c_int64), ("calls_capped", C.c_int64), ("ms_gather", C.c_double)]
 
 
 class lcc_round(C.Structure):

@@ -384,7 +384,17 @@ typedef struct lcc_tuning {
                           pass (8 bytes per entry of extra device memory), and
                           the best-move kernels read those words as a stream;
                           0: every entry gathers its own word */
-  int32_t reserved[4]; /* zero */
+  int32_t part_min;    /* 1024, 4096, 8192 (the default) or 16384: rows of
+                          more than part_min entries are hash-partitioned by
+                          cluster id into parts of about 2048 entries, each
+                          part merged in one 256-thread block's shared memory
+                          and the parts' best clusters reduced per row (a
+                          row whose part overflows its table falls back to
+                          global tables).  0: no partitioning; rows up to 8192
+                          entries in one block, up to 131072 in a thread-block
+                          cluster's distributed shared memory, longer ones in
+                          windowed global tables */
+  int32_t reserved[3]; /* zero */
 } lcc_tuning;
 
 /* lcc_get_tuning / lcc_set_tuning -- the tuning used by later calls on CUDA

@@ -402,7 +402,10 @@ static void check_tuning(const lcc_tuning *t) {
   if (t->fuse_small != 0 && t->fuse_small != 1) fail(LCC_ERR_INVALID, "fuse_small must be 0 or 1");
   if (t->prefetch != 0 && t->prefetch != 1) fail(LCC_ERR_INVALID, "prefetch must be 0 or 1");
   if (t->pregather != 0 && t->pregather != 1) fail(LCC_ERR_INVALID, "pregather must be 0 or 1");
-  for (int i = 0; i < 4; ++i)
+  const int pm = t->part_min;
+  if (pm != 0 && pm != 1024 && pm != 4096 && pm != 8192 && pm != 16384)
+    fail(LCC_ERR_INVALID, "part_min must be 0, 1024, 4096, 8192 or 16384");
+  for (int i = 0; i < 3; ++i)
     if (t->reserved[i]) fail(LCC_ERR_INVALID, "reserved tuning fields must be zero");
 }
 
@@ -481,17 +484,19 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
       char line[512];
       bool found = false;
       while (!found && fgets(line, sizeof(line), f)) {
-        // "<device name>|<SMs> <warp_max> [<fuse_small>]"
+        // "<device name>|<SMs> <warp_max> [<fuse_small> <prefetch> <pregather> <part_min>]"
         std::string l(line);
         if (l.size() <= key.size() || l.compare(0, key.size(), key) != 0 || l[key.size()] != ' ')
           continue;
-        int wm = 0, fs = 1, pf = 0, pg = 1;
-        const int nread = sscanf(l.c_str() + key.size() + 1, "%d %d %d %d", &wm, &fs, &pf, &pg);
+        int wm = 0, fs = 1, pf = 0, pg = 1, pbg = 8192;
+        const int nread =
+            sscanf(l.c_str() + key.size() + 1, "%d %d %d %d %d", &wm, &fs, &pf, &pg, &pbg);
         if (nread < 1) fail(LCC_ERR_INVALID, "malformed tuning line for this device");
         t.warp_max = wm;
         t.fuse_small = nread >= 2 ? fs : 1;
         t.prefetch = nread >= 3 ? pf : 0;
         t.pregather = nread >= 4 ? pg : 1;
+        t.part_min = nread >= 5 ? pbg : 8192;
         found = true;
       }
       fclose(f);
@@ -519,10 +524,11 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
   try {
     time_rounds(g, lambda_p, lambda_q, mode, 1);  // first-use costs outside the comparison
     // one field at a time, each from the best so far: warp_max, then
-    // fuse_small, then prefetch
+    // fuse_small, prefetch, pregather and part_min
     memset(&t, 0, sizeof(t));
     t.fuse_small = 1;
     t.pregather = 1;
+    t.part_min = 8192;
     for (int c : {32, 64, 128, 256}) {
       t.warp_max = c;
       trial(t);
@@ -536,6 +542,14 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
     t = best;
     t.pregather = 1 - t.pregather;
     trial(t);
+    {
+      const lcc_tuning base = best;
+      for (int c : {0, 1024, 4096, 16384}) {
+        t = base;
+        t.part_min = c;
+        trial(t);
+      }
+    }
   } catch (...) {
     set_tuning(g->dev, before);
     throw;
@@ -545,8 +559,8 @@ lcc_status lcc_autotune(const lcc_graph *g, int64_t lambda_p, int64_t lambda_q, 
   if (cache_path) {
     FILE *f = fopen(cache_path, "a");
     if (!f) fail(LCC_ERR_INVALID, std::string("cannot write the tuning file ") + cache_path);
-    fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.warp_max, t.fuse_small, t.prefetch,
-            t.pregather);
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.warp_max, t.fuse_small, t.prefetch,
+            t.pregather, t.part_min);
     fclose(f);
   }
   if (out) *out = t;

@@ -38,6 +38,18 @@ static int64_t hub_window() {
   return (int64_t)1 << 27;
 }
 
+// Shared-table slots of one part of the partitioned long-row path (at most
+// PART_TP); the LCC_PART_TABLE_SLOTS environment variable lowers it (tests
+// use a small table so that parts overflow and their rows take the fallback).
+static int32_t part_table_slots() {
+  const char *e = getenv("LCC_PART_TABLE_SLOTS");
+  if (e) {
+    const long long v = atoll(e);
+    if (v >= 32 && v <= PART_TP) return (int32_t)(v & ~31LL);
+  }
+  return PART_TP;
+}
+
 // Table slots of the longest coarse rows processed per pass of Compress; the
 // LCC_ROW_WINDOW_SLOTS environment variable overrides it (tests use a small
 // window to exercise many passes).
@@ -74,6 +86,7 @@ lcc_tuning tuning_for(int dev) {
   t.warp_max = T_WARP;
   t.fuse_small = 1;
   t.pregather = 1;
+  t.part_min = 8192;
   return t;
 }
 
@@ -154,7 +167,8 @@ Engine::~Engine() {
   Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                     &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
                     &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,    &s_layout_,
-                    &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_};
+                    &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_, &s_pmeta_, &s_prow_,
+                    &s_pflag_, &s_pword_,  &s_pw_,     &s_pscore_, &s_pcid_, &s_pdesc_};
   for (Scratch *s : all) s->release(st_);
   cudaStreamSynchronize(st_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -165,7 +179,9 @@ size_t Engine::scratch_bytes() const {
   const Scratch *all[] = {&s_jobs_,  &s_vstart_, &s_items_,  &s_cnt_,    &s_ctr_,    &s_jmoves_,
                           &s_moved_, &s_hkeys_,  &s_hvals_,  &s_hmeta_,  &s_hpart_s_, &s_hpart_c_,
                           &s_hstay_, &s_hiso_,   &s_ljobs_,  &s_info_,   &s_obj_,
-                          &s_layout_, &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_};
+                          &s_layout_, &s_coin_,  &s_jheld_,  &s_gw_,     &s_gwoff_,
+                          &s_pmeta_, &s_prow_,  &s_pflag_, &s_pword_,  &s_pw_,
+                          &s_pscore_, &s_pcid_, &s_pdesc_};
   size_t t = 0;
   for (const Scratch *s : all) t += s->bytes;
   return t;
@@ -536,6 +552,14 @@ void Engine::round(std::vector<Job *> &js) {
   std::vector<CoinJob> coins(nj);
   std::vector<int64_t> vs(nj + 1);
   int64_t vt = 0, caps[NB] = {0}, hubcap = 0, hubs = 0, hub_su = 0, hub_max = 0;
+  // rows of the buckets from seg0 up take the partitioned path (tuning
+  // part_min: 0 = none; 1024, 4096, 8192 or 16384 = rows longer than that)
+  const int seg0 = tun.part_min == 0 ? NB
+                   : tun.part_min <= 1024 ? B_T4K
+                   : tun.part_min <= 4096 ? B_T8K
+                   : tun.part_min <= 8192 ? B_T16K : B_T32K;
+  PartStat big;
+  memset(&big, 0, sizeof(big));
   bool wide = false, any_cl = false, any_mark = false, any_apply = false, any_coin = false;
   for (int i = 0; i < nj; ++i) {
     Job *J = js[i];
@@ -605,9 +629,29 @@ void Engine::round(std::vector<Job *> &js) {
     hubs += L.info.bcnt[B_HUB];
     hub_su += L.info.hub_sunits;
     hub_max = std::max(hub_max, L.info.hub_maxcap);
+    for (int bk = seg0; bk < NB; ++bk) {
+      const PartStat &ps = L.info.pst[bk - PB0];
+      big.rows += ps.rows;
+      big.nnz += ps.nnz;
+      big.parts += ps.parts;
+      big.chunks += ps.chunks;
+      big.cells += ps.cells;
+      big.cap += ps.cap;
+      big.sunits += ps.sunits;
+      big.maxcap = std::max(big.maxcap, ps.maxcap);
+    }
     wide |= L.wide;
   }
   vs[nj] = vt;
+  // the hub tables are then sized for all the partitioned path's rows (they
+  // serve its fallback rows)
+  const bool part_mode = big.rows > 0;
+  if (part_mode) {
+    hubcap = big.cap;
+    hubs = big.rows;
+    hub_su = big.sunits;
+    hub_max = big.maxcap;
+  }
 
   Buckets b;
   int64_t tot = 0;
@@ -643,6 +687,38 @@ void Engine::round(std::vector<Job *> &js) {
     h.iso_seen = s_hiso_.get<int32_t>(hubs, st_);
     h.max_hubs = hubs;
     h.max_sunits = hub_su;
+  }
+  PartBufs pb;
+  memset(&pb, 0, sizeof(pb));
+  if (part_mode) {
+    const int64_t R = big.rows, NPt = big.parts, NC = big.chunks;
+    const int64_t NCe = big.cells, NE = big.nnz;
+    int64_t *pm = s_pmeta_.get<int64_t>(3 * (R + 1) + (NCe + 1) + R + 2 +
+                                            scan_tmp_elems(std::max(NCe, R) + 1), st_);
+    pb.part_off = pm;
+    pb.chunk_off = pm + (R + 1);
+    pb.cell_off = pm + 2 * (R + 1);
+    pb.cells = pm + 3 * (R + 1);
+    pb.stay = pb.cells + (NCe + 1);
+    pb.nfallback = pb.stay + R;
+    pb.nrows = pb.nfallback + 1;
+    pb.scan_tmp = pb.nrows + 1;
+    pb.row = s_prow_.get<uint64_t>(2 * R, st_);
+    pb.fallback = pb.row + R;
+    pb.flag = s_pflag_.get<int32_t>(R, st_);
+    pb.pword = s_pword_.get<unsigned long long>(NE, st_);
+    pb.pw = s_pw_.get<int64_t>(NE, st_);
+    pb.part_score = s_pscore_.get<i128>(NPt, st_);
+    pb.part_cid = s_pcid_.get<int32_t>(NPt + NC, st_);
+    pb.chunk_row = pb.part_cid + NPt;
+    pb.desc = s_pdesc_.get<PartDesc>(NPt, st_);
+    pb.max_rows = R;
+    pb.max_parts = NPt;
+    pb.max_chunks = NC;
+    pb.max_cells = NCe;
+    pb.max_entries = NE;
+    pb.table_slots = part_table_slots();
+    pb.seg0 = seg0;
   }
   unsigned long long *gwbuf = nullptr;
   int64_t *dgw = nullptr;
@@ -689,7 +765,7 @@ void Engine::round(std::vector<Job *> &js) {
   }
   if (timing) CK(cudaEventRecord(ev_gw_, st_));
   launch_bestmove(wide, dt, b, h, hub_passes, ctr, st_, d_, &launches, timing ? bev_ : nullptr,
-                  tun.fuse_small != 0, tun.prefetch != 0);
+                  tun.fuse_small != 0, tun.prefetch != 0, part_mode ? &pb : nullptr);
   if (timing) CK(cudaEventRecord(ev_[2], st_));
   if (any_coin) {
     launch_coin(dt, dcoin, b, dheld, st_, d_);

@@ -233,6 +233,7 @@ class Engine {
   Scratch s_hkeys_, s_hvals_, s_hmeta_, s_hpart_s_, s_hpart_c_, s_hstay_, s_hiso_;
   Scratch s_ljobs_, s_info_, s_obj_, s_layout_;
   Scratch s_coin_, s_jheld_, s_gw_, s_gwoff_;
+  Scratch s_pmeta_, s_prow_, s_pflag_, s_pword_, s_pw_, s_pscore_, s_pcid_, s_pdesc_;
   // pinned host staging
   void *h_stage_ = nullptr;
   size_t h_stage_bytes_ = 0;

@@ -94,6 +94,24 @@ __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jo
         hun += (deg + HUB_CHUNK - 1) / HUB_CHUNK;
         hsu += (cap + HUB_SCHUNK - 1) / HUB_SCHUNK;
       }
+      if (b >= PB0) {
+        // rows of more than 1024 entries are few: their sizes go straight
+        // to the job's per-bucket totals
+        PartStat *ps = &info[j].pst[b - PB0];
+        const int64_t P = part_count_of(deg), C = part_chunks_of(deg);
+        const int64_t cap = hub_cap(deg);
+        atomicAdd((unsigned long long *)&ps->rows, 1ull);
+        atomicAdd((unsigned long long *)&ps->nnz, (unsigned long long)deg);
+        atomicAdd((unsigned long long *)&ps->parts, (unsigned long long)P);
+        if (C) {
+          atomicAdd((unsigned long long *)&ps->chunks, (unsigned long long)C);
+          atomicAdd((unsigned long long *)&ps->cells, (unsigned long long)(P * C));
+        }
+        atomicAdd((unsigned long long *)&ps->cap, (unsigned long long)cap);
+        atomicAdd((unsigned long long *)&ps->sunits,
+                  (unsigned long long)((cap + HUB_SCHUNK - 1) / HUB_SCHUNK));
+        atomicMax((unsigned long long *)&ps->maxcap, (unsigned long long)cap);
+      }
       if (ra > rmax) rmax = ra;
       wabs += ra;
       const int64_t kv = J->k[v];

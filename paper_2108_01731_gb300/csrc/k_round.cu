@@ -657,7 +657,8 @@ struct Chunk {
   uint32_t mv;  // LK_MOVED if some neighbour of the chunk moved
 };
 
-template <int E>
+// (W = false: the weights are not loaded and read as 0)
+template <int E, bool W = true>
 __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_t lo, int64_t hi,
                                            int stride, int t, Chunk<E> &x) {
   if (J.gw) {
@@ -669,7 +670,7 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
       x.k[i] = KNONE;
       x.w[i] = 0;
       if (e < hi) {
-        x.w[i] = weight_at(J, beg + e);
+        if (W) x.w[i] = weight_at(J, beg + e);
         label_at(J, beg + e, x.c[i], x.k[i], x.mv);
       }
     }
@@ -683,7 +684,7 @@ __device__ __forceinline__ void load_chunk(const JobView &J, int64_t beg, int64_
     x.w[i] = 0;
     if (e < hi) {
       u[i] = ld_stream(J.nbr + beg + e);
-      x.w[i] = weight_at(J, beg + e);
+      if (W) x.w[i] = weight_at(J, beg + e);
     }
   }
   x.mv = 0;
@@ -1171,12 +1172,12 @@ __global__ void __launch_bounds__(1024) k_hub_prep(const JobDev *__restrict__ jo
   __shared__ int64_t s_a[1024], s_b[1024], s_c[1024];
   __shared__ int64_t run_a, run_b, run_c;
   const int tid = threadIdx.x;
-  int64_t H = seg_count(b, B_HUB);
+  int64_t H = h.list ? *h.list_cnt : seg_count(b, B_HUB);
   if (H > h.max_hubs) {
     if (tid == 0) atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
     H = h.max_hubs;
   }
-  const uint64_t *items = b.items + b.seg_start[B_HUB];
+  const uint64_t *items = h.list ? h.list : b.items + b.seg_start[B_HUB];
   if (tid == 0) { run_a = 0; run_b = 0; run_c = 0; }
   __syncthreads();
   for (int64_t base = 0; base < H; base += 1024) {
@@ -1257,7 +1258,7 @@ __global__ void __launch_bounds__(256) k_hub_insert(const JobDev *__restrict__ j
   const int64_t h1 = hub_lower(h.tbl_off, H, lo + h.window);
   if (h0 >= h1) return;
   const int64_t U0 = h.unit_off[h0], U1 = h.unit_off[h1];
-  const uint64_t *items = b.items + b.seg_start[B_HUB];
+  const uint64_t *items = h.list ? h.list : b.items + b.seg_start[B_HUB];
   bool fail = false;
   for (int64_t u = U0 + blockIdx.x; u < U1; u += gridDim.x) {
     const int hh = find_seg(h.unit_off, H, u);
@@ -1297,7 +1298,7 @@ __global__ void __launch_bounds__(256) k_hub_score(const JobDev *__restrict__ jo
   const int64_t h1 = hub_lower(h.tbl_off, H, lo + h.window);
   if (h0 >= h1) return;
   const int64_t SU0 = h.sunit_off[h0], SU1 = h.sunit_off[h1];
-  const uint64_t *items = b.items + b.seg_start[B_HUB];
+  const uint64_t *items = h.list ? h.list : b.items + b.seg_start[B_HUB];
   long long ncand = 0;
   for (int64_t su = SU0 + blockIdx.x; su < SU1; su += gridDim.x) {
     const int hh = find_seg(h.sunit_off, H, su);
@@ -1344,7 +1345,7 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
                                                    HubBufs h, int64_t *ctr) {
   const int lane = threadIdx.x & 31;
   const int64_t H = ctr[C_HUBS];
-  const uint64_t *items = b.items + b.seg_start[B_HUB];
+  const uint64_t *items = h.list ? h.list : b.items + b.seg_start[B_HUB];
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   PullCount::init();
   for (int64_t hh = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); hh < H;
@@ -1370,6 +1371,386 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
   PullCount::flush(ctr);
 }
 
+// ------------------------- long rows: hash-partitioned shared-memory merges ----
+
+// Rows of the buckets from P.seg0 up (a tuning).  A row's entries are split
+// by a hash of their cluster into P parts, so that every cluster of the row
+// lies in exactly one part; each part is then merged in one block's
+// shared-memory table with no cluster barrier, no remote atomic and no
+// global table, and the parts' best candidates are reduced per row.  A row
+// of one part is merged straight from its entries and decided by the block.
+// A part whose distinct clusters overflow the table (possible only when many
+// clusters collide in the partition hash) marks its row, and such rows go
+// through the global-table hub kernels instead.
+
+// Part of cluster c among np parts: a multiplicative hash independent of the
+// one that places clusters in a part's table.
+__device__ __forceinline__ int part_of(int32_t c, int64_t np) {
+  const uint32_t h = (uint32_t)(((uint64_t)(uint32_t)c * 0xD6E8FEB86659FD93ull) >> 32);
+  return (int)(((uint64_t)h * (uint64_t)np) >> 32);
+}
+
+// One thread per row slot i <= max_rows: the row's item and its counts of
+// parts, chunks and cells (zero past the round's rows), scanned afterwards
+// into offsets.
+__global__ void __launch_bounds__(256) k_part_fill(const JobDev *__restrict__ jobs, Buckets b,
+                                                   PartBufs P, int64_t *ctr) {
+  const int nseg = B_HUB - P.seg0 + 1;
+  int64_t seg_o[NPB + 1];
+  int64_t H = 0;
+  for (int k = 0; k < nseg; ++k) {
+    seg_o[k] = H;
+    H += seg_count(b, P.seg0 + k);
+  }
+  seg_o[nseg] = H;
+  if (H > P.max_rows) {
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      atomicOr((unsigned long long *)&ctr[C_ERR], (unsigned long long)E_HUB_OVERFLOW);
+    H = P.max_rows;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *P.nrows = H;
+    *P.nfallback = 0;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= P.max_rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = 0, u = 0;
+    if (i < H) {
+      int k = 0;
+      while (i >= seg_o[k + 1]) ++k;
+      const uint64_t item = b.items[b.seg_start[P.seg0 + k] + (i - seg_o[k])];
+      const JobDev *J = jobs + (int)(item >> 32);
+      const int32_t v = (int32_t)(uint32_t)item;
+      const int64_t deg = J->off[v + 1] - J->off[v];
+      a = part_count_of(deg);
+      u = part_chunks_of(deg);
+      P.row[i] = item;
+      P.stay[i] = 0;
+      P.flag[i] = 0;
+    }
+    P.part_off[i] = a;
+    P.chunk_off[i] = u;
+    P.cell_off[i] = a * u;
+  }
+}
+
+// One warp per row: the row of each of its chunks (so that a chunk finds its
+// row with one load instead of a search).
+__global__ void __launch_bounds__(256) k_part_index(PartBufs P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t H = *P.nrows;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < H;
+       h += warps_total)
+    for (int64_t u = P.chunk_off[h] + lane; u < P.chunk_off[h + 1]; u += 32)
+      P.chunk_row[u] = (int32_t)h;
+}
+
+// Count (SCATTER = false) or scatter (true) pass over chunks of PART_CH
+// entries of the rows of more than one part: each entry's part from its
+// cluster.  The count pass writes the chunk's entries per part into
+// cells[cell_off[h] + part * C + chunk] (part major, so that the scan groups
+// each row's entries by part, chunks in order) and notes a moved neighbour;
+// the scatter pass writes each entry to its part's run at the scanned cell
+// plus its rank in the chunk.  With few parts, the lanes of a warp that hold
+// the same part take their ranks from one shared atomic.
+constexpr int PC_T = 256, PC_E = 4;  // a chunk in PART_CH / (PC_T * PC_E) sub-batches
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(PC_T, 8) k_part_chunks(const JobDev *__restrict__ jobs, PartBufs P) {
+  __shared__ int s_h[PART_MAXP];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t H = *P.nrows;
+  if (H == 0) return;
+  const int64_t NC = P.chunk_off[H];
+  for (int64_t u = blockIdx.x; u < NC; u += gridDim.x) {
+    const int64_t h = P.chunk_row[u];
+    const uint64_t item = P.row[h];
+    const JobView J = view_of(jobs + (int)(item >> 32));
+    const int32_t v = (int32_t)(uint32_t)item;
+    const int64_t beg = J.off[v];
+    const int64_t deg = J.off[v + 1] - beg;
+    const int64_t np = P.part_off[h + 1] - P.part_off[h];
+    const int64_t C = P.chunk_off[h + 1] - P.chunk_off[h];
+    const int64_t ci = u - P.chunk_off[h];
+    const int64_t lo = ci * PART_CH;
+    const int64_t hi = lo + PART_CH < deg ? lo + PART_CH : deg;
+    const bool agg = np <= 256;  // the same for the whole block
+    const int64_t cb = P.cell_off[h] + ci;
+    for (int p = tid; p < (int)np; p += PC_T) s_h[p] = 0;
+    __syncthreads();
+    uint32_t mv = 0;
+    // ranks in the chunk are running counts, so each sub-batch is written
+    // as soon as its ranks are known
+    for (int64_t s0 = lo; s0 < hi; s0 += PC_T * PC_E) {
+      const int64_t s1 = s0 + PC_T * PC_E < hi ? s0 + PC_T * PC_E : hi;
+      Chunk<PC_E> x;
+      load_chunk<PC_E, SCATTER>(J, beg, s0, s1, PC_T, tid, x);
+      mv |= x.mv;
+      int part[PC_E], rk[PC_E];
+#pragma unroll
+      for (int i = 0; i < PC_E; ++i) part[i] = x.c[i] >= 0 ? part_of(x.c[i], np) : -1;
+      if (agg) {
+#pragma unroll
+        for (int i = 0; i < PC_E; ++i) {
+          const unsigned peers = __match_any_sync(FULL, part[i]);
+          const int leader = __ffs(peers) - 1;
+          int base = 0;
+          if (lane == leader && part[i] >= 0) base = atomicAdd(&s_h[part[i]], __popc(peers));
+          base = __shfl_sync(FULL, base, leader);
+          rk[i] = base + __popc(peers & ((1u << lane) - 1u));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < PC_E; ++i) rk[i] = part[i] >= 0 ? atomicAdd(&s_h[part[i]], 1) : 0;
+      }
+      if (SCATTER) {
+#pragma unroll
+        for (int i = 0; i < PC_E; ++i) {
+          if (part[i] < 0) continue;
+          const int64_t pos = P.cells[cb + (int64_t)part[i] * C] + rk[i];
+          P.pword[pos] = slot_word(x.c[i], x.k[i]);
+          P.pw[pos] = x.w[i];
+        }
+      }
+    }
+    const int anymv = __syncthreads_or(mv != 0);
+    if (!SCATTER) {
+      for (int p = tid; p < (int)np; p += PC_T) P.cells[cb + (int64_t)p * C] = s_h[p];
+      if (tid == 0 && anymv) atomicOr(&P.flag[h], 2);
+    }
+    __syncthreads();  // s_h is rebuilt for the next chunk
+  }
+}
+
+// One warp per row, after the scan of the count cells: each part's run of
+// entries and its row in one 16-byte descriptor (a row of one part: st = -1
+// and its degree, for a merge straight from the row).
+__global__ void __launch_bounds__(256) k_part_desc(const JobDev *__restrict__ jobs, PartBufs P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t H = *P.nrows;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < H;
+       h += warps_total) {
+    const int64_t p0 = P.part_off[h], np = P.part_off[h + 1] - p0;
+    if (np == 1) {
+      if (lane == 0) {
+        const uint64_t item = P.row[h];
+        const JobDev *J = jobs + (int)(item >> 32);
+        const int32_t v = (int32_t)(uint32_t)item;
+        PartDesc d;
+        d.st = -1;
+        d.cnt = (int32_t)(J->off[v + 1] - J->off[v]);
+        d.h = (int32_t)h;
+        P.desc[p0] = d;
+      }
+      continue;
+    }
+    const int64_t C = P.chunk_off[h + 1] - P.chunk_off[h];
+    const int64_t cb = P.cell_off[h];
+    for (int64_t pi = lane; pi < np; pi += 32) {
+      const int64_t st = P.cells[cb + pi * C];
+      PartDesc d;
+      d.st = st;
+      d.cnt = (int32_t)(P.cells[cb + (pi + 1) * C] - st);
+      d.h = (int32_t)h;
+      P.desc[p0 + pi] = d;
+    }
+  }
+}
+
+// One part per block iteration (PART_T threads): its entries merged in a
+// shared table of 3.25 slots per entry (at most table_slots <= PART_TP),
+// scored, and the used slots emptied as they are read.  Two barriers per part:
+// after the inserts, and after the scan (the per-warp results go to one of
+// two buffers, so that warp 0 reduces them while the next part's inserts
+// run).  Several blocks per SM keep independent parts in flight.
+template <typename S>
+__global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restrict__ jobs,
+                                                          PartBufs P, int64_t *ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NW = PART_T / 32, E = 4, STEP = PART_T * E;
+  unsigned long long *tkey = (unsigned long long *)smem;
+  unsigned long long *tval = tkey + PART_TP;
+  __shared__ S red_s[2][NW];
+  __shared__ int32_t red_c[2][NW];
+  __shared__ long long red_w[2][NW];
+  __shared__ int red_v[2][NW];
+  __shared__ int s_mv[2];
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  for (int sl = tid; sl < PART_TP; sl += PART_T) {
+    tkey[sl] = SLOT_EMPTY;
+    tval[sl] = 0;
+  }
+  if (tid < 2) s_mv[tid] = 0;
+  PullCount::init();  // includes the barrier that publishes the empty table
+  const int64_t H = *P.nrows;
+  const int64_t NP = H > 0 ? P.part_off[H] : 0;
+  long long ncand = 0;
+  auto at = [&](uint32_t sl, unsigned long long *&kp, unsigned long long *&vp) {
+    kp = tkey + sl;
+    vp = tval + sl;
+  };
+  int par = 0;
+  // the next part's descriptor is loaded while the current part is merged
+  PartDesc nd;
+  if (blockIdx.x < NP) nd = P.desc[blockIdx.x];
+  for (int64_t q = blockIdx.x; q < NP; q += gridDim.x) {
+    const PartDesc d = nd;
+    if (q + gridDim.x < NP) nd = P.desc[q + gridDim.x];
+    const int64_t h = d.h;
+    const uint64_t item = P.row[h];
+    const JobView J = view_of(jobs + (int)(item >> 32));
+    const int32_t v = (int32_t)(uint32_t)item;
+    // the row's own label and weight are needed only when the part is scored
+    const int32_t Lv = J.L[v];
+    const int64_t kv = J.k[v];
+    const bool direct = d.st < 0;
+    // 3.25 slots per entry (at most table_slots): few probes per insert
+    int64_t cap = ((int64_t)d.cnt * 13 + 3) / 4;
+    cap = (cap + 31) & ~(int64_t)31;
+    if (cap < 32) cap = 32;
+    if (cap > P.table_slots) cap = P.table_slots;
+    const AnyCap geo((uint32_t)cap);
+    // a part of at most two sub-batches keeps the slots its threads stored
+    // first in registers and scores only those; a longer one scans the table
+    const bool two = d.cnt <= 2 * STEP;
+    uint32_t won0[E], won1[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      won0[i] = NOSLOT;
+      won1[i] = NOSLOT;
+    }
+    bool fail = false;
+    uint32_t mv = 0;
+    const int64_t beg = direct ? J.off[v] : 0;
+    for (int64_t t0 = 0; t0 < d.cnt; t0 += STEP) {
+      const int64_t t1 = t0 + STEP < d.cnt ? t0 + STEP : d.cnt;
+      Chunk<E> x;
+      if (direct) {
+        load_chunk(J, beg, t0, t1, PART_T, tid, x);
+        mv |= x.mv;
+      } else {
+        x.mv = 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int64_t e = t0 + (int64_t)i * PART_T + tid;
+          x.c[i] = -1;
+          x.k[i] = KNONE;
+          x.w[i] = 0;
+          if (e < t1) {
+            const unsigned long long wd =
+                (unsigned long long)ld_stream((const int64_t *)(P.pword + d.st + e));
+            x.c[i] = (int32_t)(uint32_t)wd;
+            x.k[i] = (uint32_t)(wd >> 32);
+            x.w[i] = ld_stream(P.pw + d.st + e);
+          }
+        }
+      }
+      if (!two)
+        fail |= !insert_chunk(x, at, geo);
+      else if (t0 == 0)
+        fail |= !insert_chunk_won(x, at, geo, won0);
+      else
+        fail |= !insert_chunk_won(x, at, geo, won1);
+    }
+    if (mv) atomicOr(&s_mv[par], 1);
+    fail = __syncthreads_or(fail) != 0;
+    S best = ScoreOps<S>::lowest();
+    int32_t bc = INT32_MAX;
+    long long w_stay = 0;
+    int vseen = 0;
+    if (two) {
+      scan_won<S, E>(J, won0, at, v, Lv, kv, best, bc, w_stay, vseen, ncand);
+      scan_won<S, E>(J, won1, at, v, Lv, kv, best, bc, w_stay, vseen, ncand);
+    } else {
+      scan_slots_reset<S>(J, tkey, tval, tid, (int)cap, PART_T, v, Lv, kv, best, bc, w_stay,
+                          vseen, ncand);
+    }
+    w_stay = warp_sum_ll(w_stay);
+    const int vs = __any_sync(FULL, vseen);
+    warp_argmax<S>(best, bc);
+    if (lane == 0) {
+      red_s[par][wib] = best;
+      red_c[par][wib] = bc;
+      red_w[par][wib] = w_stay;
+      red_v[par][wib] = vs;
+    }
+    __syncthreads();  // the table is empty and the warps' results are in
+    if (wib == 0) {
+      S bs = lane < NW ? red_s[par][lane] : ScoreOps<S>::lowest();
+      int32_t bcc = lane < NW ? red_c[par][lane] : INT32_MAX;
+      long long ws = lane < NW ? red_w[par][lane] : 0;
+      int vv = lane < NW ? red_v[par][lane] : 0;
+      warp_argmax<S>(bs, bcc);
+      ws = warp_sum_ll(ws);
+      vv = __any_sync(FULL, vv);
+      if (lane == 0) {
+        const int moved = s_mv[par];
+        s_mv[par] = 0;
+        if (direct) {
+          if (fail) {
+            const int64_t pos = (int64_t)atomicAdd((unsigned long long *)P.nfallback, 1ull);
+            P.fallback[pos] = item;
+          } else {
+            write_desired<S>(J, v, d.cnt, Lv, kv, own_weight(J, v, Lv), bs, bcc, ws, vv != 0,
+                             moved != 0);
+          }
+        } else {
+          P.part_score[q] = (i128)bs;
+          P.part_cid[q] = bcc;
+          if (ws) atomicAdd((unsigned long long *)&P.stay[h], (unsigned long long)ws);
+          if (vv || fail) atomicOr(&P.flag[h], (vv ? 1 : 0) | (fail ? 4 : 0));
+        }
+      }
+    }
+    par ^= 1;
+  }
+  ncand = warp_sum_ll(ncand);
+  if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
+  PullCount::flush(ctr);
+}
+
+// One warp per row of more than one part: the best of its parts, then the
+// decision; a row whose part overflowed goes to the fallback list for the
+// global-table kernels.
+template <typename S>
+__global__ void __launch_bounds__(256) k_part_final(const JobDev *__restrict__ jobs, PartBufs P,
+                                                    int64_t *ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t H = *P.nrows;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  PullCount::init();
+  for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < H;
+       h += warps_total) {
+    const int64_t q0 = P.part_off[h], q1 = P.part_off[h + 1];
+    if (q1 - q0 == 1) continue;  // decided by the merge
+    const uint64_t item = P.row[h];
+    const JobView J = view_of(jobs + (int)(item >> 32));
+    const int32_t v = (int32_t)(uint32_t)item;
+    S best = ScoreOps<S>::lowest();
+    int32_t bc = INT32_MAX;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const S sc = (S)P.part_score[q];
+      const int32_t c = P.part_cid[q];
+      if (better<S>(sc, c, best, bc)) { best = sc; bc = c; }
+    }
+    warp_argmax<S>(best, bc);
+    if (lane == 0) {
+      const int fl = P.flag[h];
+      if (fl & 4) {
+        const int64_t pos = (int64_t)atomicAdd((unsigned long long *)P.nfallback, 1ull);
+        P.fallback[pos] = item;
+      } else {
+        const int32_t Lv = J.L[v];
+        write_desired<S>(J, v, J.off[v + 1] - J.off[v], Lv, J.k[v], own_weight(J, v, Lv), best,
+                         bc, (long long)P.stay[h], (fl & 1) != 0, (fl & 2) != 0);
+      }
+    }
+  }
+  PullCount::flush(ctr);
+}
+
 // ------------------------------------------------------------ dispatch ----
 
 namespace {
@@ -1378,6 +1759,12 @@ int occ_blocks(K kernel, int threads, size_t smem) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
   return nb > 0 ? nb : 1;
+}
+
+int grid_of_rows(int64_t n, const Dev &d) {
+  int64_t g = (n + 255) / 256;
+  if (g > (int64_t)d.sms * 8) g = (int64_t)d.sms * 8;
+  return (int)(g > 0 ? g : 1);
 }
 
 struct TableLaunch {
@@ -1420,7 +1807,7 @@ void launch_table(const JobDev *jobs, const Buckets &b, int64_t *ctr, cudaStream
 template <typename S>
 void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64_t hub_passes,
                    int64_t *ctr, cudaStream_t st, const Dev &d, int *launches, cudaEvent_t *ev,
-                   bool fuse_small, bool prefetch) {
+                   bool fuse_small, bool prefetch, const PartBufs *pb) {
   auto mark = [&](int bk) {
     if (ev) cudaEventRecord(ev[bk], st);
   };
@@ -1506,29 +1893,79 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
       launch_table<S, 1, 256, TP_BLK, 4, 1, true, B_BLK>(jobs, b, ctr, st, tl[0], launches);
   }
   mark(B_BLK);
-  if (b.seg_cap[B_T4K] > 0) {
+  // buckets from seg0 up go to the partitioned path
+  const int seg0 = pb ? pb->seg0 : NB;
+  if (B_T4K < seg0 && b.seg_cap[B_T4K] > 0) {
     if (prefetch)
       launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K, true>(jobs, b, ctr, st, tlp[2],
                                                                 launches);
     else
       launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K>(jobs, b, ctr, st, tl[1], launches);
   }
-  mark(B_T4K);
-  if (b.seg_cap[B_T8K] > 0)
+  if (B_T4K < seg0) mark(B_T4K);
+  if (B_T8K < seg0 && b.seg_cap[B_T8K] > 0)
     launch_table<S, 1, 1024, TP_8K, 4, 2, false, B_T8K>(jobs, b, ctr, st, tl[2], launches);
-  mark(B_T8K);
-  if (b.seg_cap[B_T16K] > 0)
+  if (B_T8K < seg0) mark(B_T8K);
+  if (B_T16K < seg0 && b.seg_cap[B_T16K] > 0)
     launch_table<S, 2, 1024, TP_8K, 4, 2, false, B_T16K>(jobs, b, ctr, st, tl[3], launches);
-  mark(B_T16K);
-  if (b.seg_cap[B_T32K] > 0)
+  if (B_T16K < seg0) mark(B_T16K);
+  if (B_T32K < seg0 && b.seg_cap[B_T32K] > 0)
     launch_table<S, 4, 1024, TP_8K, 4, 2, false, B_T32K>(jobs, b, ctr, st, tl[4], launches);
-  mark(B_T32K);
-  if (b.seg_cap[B_T64K] > 0)
+  if (B_T32K < seg0) mark(B_T32K);
+  if (B_T64K < seg0 && b.seg_cap[B_T64K] > 0)
     launch_table<S, 8, 1024, TP_8K, 4, 2, false, B_T64K>(jobs, b, ctr, st, tl[5], launches);
-  mark(B_T64K);
-  if (b.seg_cap[B_T128K] > 0)
+  if (B_T64K < seg0) mark(B_T64K);
+  if (B_T128K < seg0 && b.seg_cap[B_T128K] > 0)
     launch_table<S, 16, 1024, TP_8K, 4, 2, false, B_T128K>(jobs, b, ctr, st, tl[6], launches);
-  mark(B_T128K);
+  if (B_T128K < seg0) mark(B_T128K);
+  if (pb) {
+    // hash-partitioned merges, then the global-table kernels for the rows
+    // whose part overflowed
+    static int occ_merge = 0;
+    if (!occ_merge) {
+      cudaFuncSetAttribute(k_part_merge<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           PART_TP * 16);
+      int nb = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_part_merge<S>, PART_T, PART_TP * 16);
+      occ_merge = nb > 0 ? nb : 1;
+    }
+    const int64_t R = pb->max_rows;
+    k_part_fill<<<grid_of_rows(R + 1, d), 256, 0, st>>>(jobs, b, *pb, ctr);
+    scan_exclusive_i64(pb->part_off, R, pb->scan_tmp, st, d);
+    scan_exclusive_i64(pb->chunk_off, R, pb->scan_tmp, st, d);
+    scan_exclusive_i64(pb->cell_off, R, pb->scan_tmp, st, d);
+    const int64_t rg0 = (R + 7) / 8;
+    const int rg = (int)(rg0 < (int64_t)d.sms * 8 ? rg0 : (int64_t)d.sms * 8);
+    int64_t g = pb->max_chunks < (int64_t)d.sms * 8 ? pb->max_chunks : (int64_t)d.sms * 8;
+    if (pb->max_chunks > 0) {
+      cudaMemsetAsync(pb->cells, 0, (pb->max_cells + 1) * sizeof(int64_t), st);
+      k_part_index<<<rg, 256, 0, st>>>(*pb);
+      k_part_chunks<false><<<(int)g, PC_T, 0, st>>>(jobs, *pb);
+      scan_exclusive_i64(pb->cells, pb->max_cells, pb->scan_tmp, st, d);
+      k_part_chunks<true><<<(int)g, PC_T, 0, st>>>(jobs, *pb);
+      *launches += 6;
+    }
+    k_part_desc<<<rg, 256, 0, st>>>(jobs, *pb);
+    g = pb->max_parts < (int64_t)d.sms * occ_merge ? pb->max_parts : (int64_t)d.sms * occ_merge;
+    k_part_merge<S><<<(int)(g > 0 ? g : 1), PART_T, PART_TP * 16, st>>>(jobs, *pb, ctr);
+    k_part_final<S><<<rg, 256, 0, st>>>(jobs, *pb, ctr);
+    *launches += 13;
+    HubBufs hf = h;
+    hf.list = pb->fallback;
+    hf.list_cnt = pb->nfallback;
+    k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, hf, ctr);
+    for (int64_t p = 0; p < hub_passes; ++p) {
+      const int64_t lo = p * hf.window;
+      k_hub_clear<<<d.sms * 8, 256, 0, st>>>(hf, ctr, lo);
+      k_hub_insert<<<d.sms * occ[5], 256, 0, st>>>(jobs, b, hf, ctr, lo);
+      k_hub_score<S><<<d.sms * occ[6], 256, 0, st>>>(jobs, b, hf, ctr, lo);
+      *launches += 3;
+    }
+    k_hub_final<S><<<rg, 256, 0, st>>>(jobs, b, hf, ctr);
+    *launches += 2;
+    for (int bk = seg0; bk <= B_HUB; ++bk) mark(bk);
+    return;
+  }
   if (b.seg_cap[B_HUB] > 0) {
     k_hub_prep<<<1, 1024, 0, st>>>(jobs, b, h, ctr);
     for (int64_t p = 0; p < hub_passes; ++p) {
@@ -1549,12 +1986,14 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
 
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch) {
+                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch,
+                     const PartBufs *pb) {
   if (wide)
-    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small, prefetch);
+    bestmove_impl<i128>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small, prefetch,
+                        pb);
   else
     bestmove_impl<int64_t>(jobs, b, h, hub_passes, ctr, st, d, launches, ev, fuse_small,
-                           prefetch);
+                           prefetch, pb);
 }
 
 // --------------------------------------------------------------- apply ----

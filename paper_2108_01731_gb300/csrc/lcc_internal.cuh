@@ -180,6 +180,42 @@ struct HubBufs {
   int32_t *iso_seen;  // [max_hubs] bit 0: cluster id v occurs; bit 1: a neighbour moved
   int64_t max_hubs;
   int64_t max_sunits;
+  // rows to process: the B_HUB segment, or (when set) list[0 .. *list_cnt)
+  const uint64_t *list;
+  const int64_t *list_cnt;
+};
+
+// One part of the partitioned path: its run of entries and its row.
+struct PartDesc {
+  int64_t st;   // first entry in pword / pw
+  int32_t cnt;  // entries
+  int32_t h;    // row
+};
+
+// The partitioned path's arrays (see PART_*): per row h < H of the long-row
+// buckets, its item and prefix offsets of its parts, chunks and count cells;
+// per part its best candidate; per row the stay weight and flags.
+struct PartBufs {
+  uint64_t *row;          // [max_rows]
+  int64_t *part_off;      // [max_rows + 1]
+  int64_t *chunk_off;     // [max_rows + 1]
+  int64_t *cell_off;      // [max_rows + 1]
+  int64_t *cells;         // [max_cells + 1] counts per (row, part, chunk), scanned in place
+  unsigned long long *pword;  // [max_entries] entries grouped by (row, part): packed word
+  int64_t *pw;            // [max_entries] and weight
+  i128 *part_score;       // [max_parts]
+  int32_t *part_cid;      // [max_parts]
+  int64_t *stay;          // [max_rows]
+  int32_t *flag;          // [max_rows] bit 0: cluster id v occurs; 1: a neighbour moved; 2: overflow
+  uint64_t *fallback;     // [max_rows] rows whose part overflowed its table
+  int64_t *nfallback;     // [1]
+  int64_t *nrows;         // [1] rows this round (written by k_part_prep)
+  int64_t *scan_tmp;      // [scan_tmp_elems(max(max_cells, max_rows) + 1)]
+  int32_t *chunk_row;     // [max_chunks] row of each chunk
+  PartDesc *desc;         // [max_parts]
+  int64_t max_rows, max_parts, max_chunks, max_cells, max_entries;
+  int32_t table_slots;    // slots of a part's table at most (a multiple of 32, <= PART_TP)
+  int32_t seg0;           // first bucket taken by the path (PB0 .. B_HUB)
 };
 
 // Contraction view of one job's level.
@@ -221,6 +257,16 @@ constexpr int LAYOUT_CLASSES = 34;
 // Levels whose packed words take more than this many bytes get a layout.
 constexpr int64_t LAYOUT_MIN_BYTES = (int64_t)64 << 20;
 
+// Sizes of the partitioned best-move path over the rows of one degree
+// bucket (B_T4K and above; see PART_*).
+struct PartStat {
+  int64_t rows, nnz;
+  int64_t parts, chunks, cells;  // sums of P, of the rows' chunks, and of P * chunks
+  int64_t cap, sunits, maxcap;   // the rows' global tables (the fallback)
+};
+constexpr int PB0 = B_T4K;           // first bucket the partitioned path can take
+constexpr int NPB = B_HUB - PB0 + 1;
+
 // Per-job results of the level statistics kernel.
 struct LevelInfo {
   int64_t bcnt[NB];     // vertices per degree bucket
@@ -235,7 +281,29 @@ struct LevelInfo {
   int64_t hub_maxcap;   // largest hub table
   int64_t nnz;          // entries (sum of deg)
   int64_t ksat;         // nonzero: the sum of node weights reached 2^62 (ksum is then not exact)
+  // rows of the buckets B_T4K .. B_HUB, per bucket (the partitioned path)
+  PartStat pst[NPB];
 };
+
+// Partitioned best-move path for the rows of the buckets from a tuned one
+// (lcc_tuning.part_min) up: the entries of a row are split by a hash of
+// their cluster into P = ceil(deg / PART_ENT) parts (at most PART_MAXP),
+// counted and scattered in chunks of PART_CH entries, and each part is merged
+// by one PART_T-thread block in a table of at most PART_TP slots.  A row of
+// one part is merged straight from its entries.
+constexpr int PART_ENT = 1024;
+constexpr int PART_MAXP = 4096;
+constexpr int PART_CH = 4096;
+constexpr int PART_T = 256;
+constexpr int PART_TP = 3328;  // table slots of a part's block (52 KB, 3.25 * PART_ENT)
+__host__ __device__ inline int64_t part_count_of(int64_t deg) {
+  const int64_t p = (deg + PART_ENT - 1) / PART_ENT;
+  return p < PART_MAXP ? p : PART_MAXP;
+}
+// Chunks of the count and scatter passes (none for a row of one part).
+__host__ __device__ inline int64_t part_chunks_of(int64_t deg) {
+  return part_count_of(deg) > 1 ? (deg + PART_CH - 1) / PART_CH : 0;
+}
 
 // Per-job accumulators of the objective kernels.
 struct ObjAcc {
@@ -324,10 +392,13 @@ void launch_frontier(const JobDev *jobs, const int64_t *vstart, int njobs, int64
                      const Buckets &b, int64_t *ctr, cudaStream_t st, const Dev &d);
 // ev (nullable, NB events): ev[b] is recorded after degree bucket b's kernels.
 // fuse_small: the <= 4 .. <= 32 buckets in one resident launch (k_bm_small);
-// prefetch: the one-chunk table kernels pipeline their vertices.
+// prefetch: the one-chunk table kernels pipeline their vertices; pb (nullable):
+// rows of more than PART_MIN entries take the partitioned path, and h (with
+// hub_passes) then serves its fallback rows.
 void launch_bestmove(bool wide, const JobDev *jobs, const Buckets &b, const HubBufs &h,
                      int64_t hub_passes, int64_t *ctr, cudaStream_t st, const Dev &d,
-                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch);
+                     int *launches, cudaEvent_t *ev, bool fuse_small, bool prefetch,
+                     const PartBufs *pb);
 // jmoves[2j] = moves of job j, jmoves[2j + 1] = entries of its movers' rows.
 void launch_apply(const JobDev *jobs, const Buckets &b, int64_t *jmoves, uint64_t *moved,
                   int64_t moved_cap, int64_t *ctr, cudaStream_t st, const Dev &d);

@@ -40,7 +40,8 @@ class lcc_schedule(C.Structure):
 
 class lcc_tuning(C.Structure):
     _fields_ = [("warp_max", C.c_int32), ("fuse_small", C.c_int32), ("prefetch", C.c_int32),
-                ("pregather", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("pregather", C.c_int32), ("part_min", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class lcc_stats(C.Structure):
@@ -340,29 +341,30 @@ def lcc_objective(g, lambda_p, lambda_q, mode, labels):
 
 def _tuning_dict(t):
     return {"warp_max": t.warp_max, "fuse_small": t.fuse_small, "prefetch": t.prefetch,
-            "pregather": t.pregather}
+            "pregather": t.pregather, "part_min": t.part_min}
 
 
 def lcc_get_tuning(device=0):
     """The kernel tuning used on `device`: {"warp_max", "fuse_small", "prefetch",
-    "pregather"}."""
+    "pregather", "part_min"}."""
     t = lcc_tuning()
     _check(load().lcc_get_tuning(int(device), C.byref(t)))
     return _tuning_dict(t)
 
 
-def lcc_set_tuning(device, warp_max, fuse_small=1, prefetch=0, pregather=1):
+def lcc_set_tuning(device, warp_max, fuse_small=1, prefetch=0, pregather=1, part_min=8192):
     t = lcc_tuning()
     t.warp_max = int(warp_max)
     t.fuse_small = int(fuse_small)
     t.prefetch = int(prefetch)
     t.pregather = int(pregather)
+    t.part_min = int(part_min)
     _check(load().lcc_set_tuning(int(device), C.byref(t)))
 
 
 def lcc_autotune(g, lambda_p, lambda_q, mode, cache_path=None):
     """Times tunings on three best-move rounds of g, one field at a time
-    (warp_max, then fuse_small, prefetch and pregather), or reads the cache file's line
+    (warp_max, then fuse_small, prefetch, pregather and part_min), or reads the cache file's line
     for this device, and applies the fastest; returns it as a dict."""
     t = lcc_tuning()
     path = cache_path.encode() if cache_path else None

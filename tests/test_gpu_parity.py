@@ -284,20 +284,83 @@ def test_tuning_routes_without_changing_results(L, tmp_path):
         t = L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path))
         assert t["warp_max"] in (32, 64, 128, 256) and t["fuse_small"] in (0, 1)
         assert t["prefetch"] in (0, 1) and t["pregather"] in (0, 1)
+        assert t["part_min"] in (0, 1024, 4096, 8192, 16384)
         assert L.lcc_get_tuning(0) == t
         assert path.read_text().strip().endswith(
-            " %d %d %d %d" % (t["warp_max"], t["fuse_small"], t["prefetch"], t["pregather"]))
+            " %d %d %d %d %d" % (t["warp_max"], t["fuse_small"], t["prefetch"], t["pregather"],
+                                 t["part_min"]))
         L.lcc_set_tuning(0, 32 if t["warp_max"] != 32 else 256, 1 - t["fuse_small"],
-                         1 - t["prefetch"], 1 - t["pregather"])
+                         1 - t["prefetch"], 1 - t["pregather"], 1024 if t["part_min"] != 1024 else 0)
         assert L.lcc_autotune(G, 1, 1, O.NODEW_DEGREE, str(path)) == t
         assert L.lcc_get_tuning(0) == t
         G.free()
-        for bad in ((0, 1), (48, 1), (512, 1), (256, 2), (256, 1, 2), (256, 1, 0, 2)):
+        for bad in ((0, 1), (48, 1), (512, 1), (256, 2), (256, 1, 2), (256, 1, 0, 2),
+                    (256, 1, 0, 1, 1), (256, 1, 0, 1, 2048)):
             with pytest.raises(L.LccError):
                 L.lcc_set_tuning(0, *bad)
     finally:
         L.lcc_set_tuning(0, before["warp_max"], before["fuse_small"], before["prefetch"],
-                         before["pregather"])
+                         before["pregather"], before["part_min"])
+
+
+def test_partitioned_long_rows_match_oracle(L, monkeypatch):
+    """Rows longer than part_min entries split by cluster hash into parts of
+    about 2048 entries, each merged in one block's shared memory (rows of one
+    part merged straight from their entries), for every part_min from 1024 to
+    16384 and with the path off; the "giant" graph's hubs of 12,000 to
+    140,000 draws, a signed-weight graph with rows of 8,000 to 32,000 entries
+    and the hub and R-MAT graphs, alone and in a batch.  Then with the parts'
+    tables cut to 64 slots, so that nearly every part overflows and its row
+    takes the global-table fallback.  Labels, objective and scanned entries
+    are the oracle's every time."""
+    before = L.lcc_get_tuning(0)
+    graphs = dict(GRAPHS)
+    graphs["giant_w"] = I.to_numpy(I.hub_graph(60000, 6, 0, [9000, 20000, 30000, 45000],
+                                               seed=8, w_lo=-5, w_hi=9))
+    cases = [("giant", O.NODEW_DEGREE, 1, 1, {}),
+             ("giant", O.NODEW_UNIT, 1, 40, {"vset": O.VSET_NBR_VERTICES}),
+             ("giant_w", O.NODEW_CUSTOM, 2, 9, {"vset": O.VSET_NBR_CLUSTERS}),
+             ("giant_w", O.NODEW_UNIT, 1, 8, {}),
+             ("giant", O.NODEW_DEGREE, 1, 1, {"coin": True, "seed": 11}),
+             ("hubs", O.NODEW_DEGREE, 1, 1, {}),
+             ("rmat", O.NODEW_DEGREE, 1, 1, {"vset": O.VSET_ALL})]
+    want = {}
+    for i, (name, mode, p, q, kw) in enumerate(cases):
+        g = graphs[name]
+        k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None
+        wl, num, _, wst = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=mode, k=k, **kw)
+        want[i] = (wl, num, wst[2])
+
+    def run_all(tag):
+        for i, (name, mode, p, q, kw) in enumerate(cases):
+            g = graphs[name]
+            k = node_weights(g, O.NODEW_CUSTOM, 9) if mode == O.NODEW_CUSTOM else None
+            G = L.lcc_load_csr(g["off"], g["nbr"], g["w"], node_w=k)
+            sched = L.schedule(**kw) if kw else None
+            labels, _, st = L.lcc_cluster(G, p, q, mode, sched)
+            G.free()
+            wl, num, scanned = want[i]
+            assert np.array_equal(labels, wl), (tag, name, mode, kw)
+            assert st["obj_num"] == num and st["edges_scanned"] == scanned, (tag, name, mode, kw)
+        batch = [graphs[x] for x in ("giant", "giant_w", "giant")]
+        Gs = [L.lcc_load_csr(g["off"], g["nbr"], g["w"]) for g in batch]
+        labs, _ = L.lcc_cluster_batch(Gs, [1, 1, 1], [1, 8, 1],
+                                      [O.NODEW_DEGREE, O.NODEW_UNIT, O.NODEW_DEGREE])
+        for G in Gs:
+            G.free()
+        assert np.array_equal(labs[0], want[0][0]) and np.array_equal(labs[2], want[0][0]), tag
+        assert np.array_equal(labs[1], want[3][0]), tag
+
+    try:
+        for pm in (8192, 1024, 4096, 16384, 0):
+            L.lcc_set_tuning(0, 256, 1, 0, 1, pm)
+            run_all(pm)
+        L.lcc_set_tuning(0, 256, 1, 0, 1, 1024)
+        monkeypatch.setenv("LCC_PART_TABLE_SLOTS", "64")
+        run_all("64 slots")
+    finally:
+        L.lcc_set_tuning(0, before["warp_max"], before["fuse_small"], before["prefetch"],
+                         before["pregather"], before["part_min"])
 
 
 def check_cluster_case(L, case):

@@ -25,112 +25,214 @@ int grid_for(int64_t work, int threads, const Dev &d, int per_sm = 8) {
 
 // ------------------------------------------------------- level statistics --
 
-// One warp per vertex: degree bucket, hub table sizes, row sum of |w|, node
-// weight range.  Lane 0 keeps running totals for the job it is on and
-// flushes them with atomics when the job changes.
+// A warp takes 32 consecutive vertices, one per lane: degree bucket, hub
+// table sizes, row sum of |w|, node weight range.  A lane sums a short row's
+// weights itself; the warp sums each long row together.  The warp keeps
+// running totals for the job it is on (per lane, reduced when the job
+// changes; bucket counts by ballot, in shared memory); a window that spans
+// two jobs sends each vertex's figures to its own job directly.
+namespace {
+constexpr int64_t KSAT = (int64_t)1 << 62;
+
+struct StatAcc {
+  int64_t hcap, hun, hsu, hmax, rmax, kmax, ksum, wabs, kneg, ents, ksat;
+};
+
+__device__ __forceinline__ int64_t wmax_ll(int64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t y = __shfl_xor_sync(FULL, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+// Adds totals to job I's figures (the caller's lane holds the whole total;
+// bucket counts go separately).
+__device__ void stats_flush(LevelInfo *I, const StatAcc &a) {
+  if (a.hcap) atomicAdd((unsigned long long *)&I->hub_cap, (unsigned long long)a.hcap);
+  if (a.hun) atomicAdd((unsigned long long *)&I->hub_units, (unsigned long long)a.hun);
+  if (a.hsu) atomicAdd((unsigned long long *)&I->hub_sunits, (unsigned long long)a.hsu);
+  atomicMax((unsigned long long *)&I->rmax, (unsigned long long)a.rmax);
+  atomicMax((unsigned long long *)&I->kmax, (unsigned long long)a.kmax);
+  int64_t ksat = a.ksat;
+  if (a.ksum) {
+    // node weights are non-negative and every addend is below 2^62, so the
+    // add that carries the total past 2^62 sees it before any wrap
+    const unsigned long long old =
+        atomicAdd((unsigned long long *)&I->ksum, (unsigned long long)a.ksum);
+    if (old >= (unsigned long long)KSAT || old + (unsigned long long)a.ksum >= (unsigned long long)KSAT)
+      ksat = 1;
+  }
+  if (ksat) atomicOr((unsigned long long *)&I->ksat, 1ull);
+  if (a.wabs) atomicAdd((unsigned long long *)&I->wabs, (unsigned long long)a.wabs);
+  if (a.kneg) atomicAdd((unsigned long long *)&I->pad, (unsigned long long)a.kneg);
+  if (a.hmax) atomicMax((unsigned long long *)&I->hub_maxcap, (unsigned long long)a.hmax);
+  if (a.ents) atomicAdd((unsigned long long *)&I->nnz, (unsigned long long)a.ents);
+}
+
+__device__ __forceinline__ void stats_clear(StatAcc &a) {
+  a.hcap = a.hun = a.hsu = a.hmax = a.rmax = a.kmax = a.ksum = a.wabs = a.kneg = a.ents = a.ksat = 0;
+}
+
+// One vertex's figures into a lane's totals (its bucket is counted apart).
+__device__ __forceinline__ void stats_add(StatAcc &a, int64_t deg, int b, long long ra,
+                                          int64_t kv) {
+  a.ents += deg;
+  if (b == B_HUB) {
+    const int64_t cap = hub_cap(deg);
+    a.hcap += cap;
+    if (cap > a.hmax) a.hmax = cap;
+    a.hun += (deg + HUB_CHUNK - 1) / HUB_CHUNK;
+    a.hsu += (cap + HUB_SCHUNK - 1) / HUB_SCHUNK;
+  }
+  if (ra > a.rmax) a.rmax = ra;
+  a.wabs += ra;
+  if (kv < 0) {
+    a.kneg += 1;
+  } else {
+    if (kv > a.kmax) a.kmax = kv;
+    if (kv >= KSAT - a.ksum) a.ksat = 1;  // the running total would reach 2^62
+    else a.ksum += kv;
+  }
+}
+
+// The rows of more than 1024 entries are few: their partitioned-path sizes
+// go straight to the job's per-bucket totals.
+__device__ __forceinline__ void part_stats_add(LevelInfo *I, int64_t deg, int b) {
+  if (b < PB0) return;
+  PartStat *ps = &I->pst[b - PB0];
+  const int64_t P = part_count_of(deg), C = part_chunks_of(deg);
+  const int64_t cap = hub_cap(deg);
+  atomicAdd((unsigned long long *)&ps->rows, 1ull);
+  atomicAdd((unsigned long long *)&ps->nnz, (unsigned long long)deg);
+  atomicAdd((unsigned long long *)&ps->parts, (unsigned long long)P);
+  if (C) {
+    atomicAdd((unsigned long long *)&ps->chunks, (unsigned long long)C);
+    atomicAdd((unsigned long long *)&ps->cells, (unsigned long long)(P * C));
+  }
+  atomicAdd((unsigned long long *)&ps->cap, (unsigned long long)cap);
+  atomicAdd((unsigned long long *)&ps->sunits,
+            (unsigned long long)((cap + HUB_SCHUNK - 1) / HUB_SCHUNK));
+  atomicMax((unsigned long long *)&ps->maxcap, (unsigned long long)cap);
+}
+}  // namespace
+
 __global__ void __launch_bounds__(256) k_level_stats(const LJob *__restrict__ jobs,
                                                      const int64_t *__restrict__ vstart,
                                                      int njobs, int64_t vtot, LevelInfo *info) {
-  const int lane = threadIdx.x & 31;
+  __shared__ long long s_bc[8][NB];  // the warp's bucket counts for job cur
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  int cur = -1;
-  int64_t bc[NB];
-  int64_t hcap = 0, hun = 0, hsu = 0, rmax = 0, kmax = 0, ksum = 0, wabs = 0, kneg = 0, hmax = 0,
-          ents = 0, ksat = 0;
-  for (int i = 0; i < NB; ++i) bc[i] = 0;
+  int cur = -1;  // the job of the warp's running totals (warp-uniform)
+  StatAcc acc;
+  stats_clear(acc);
+  if (lane < NB) s_bc[wib][lane] = 0;
+  __syncwarp();
+  // reduces the lanes' totals into lane 0 and adds them to job cur
   auto flush = [&]() {
     if (cur < 0) return;
-    LevelInfo *I = info + cur;
-    for (int i = 0; i < NB; ++i)
-      if (bc[i]) atomicAdd((unsigned long long *)&I->bcnt[i], (unsigned long long)bc[i]);
-    if (hcap) atomicAdd((unsigned long long *)&I->hub_cap, (unsigned long long)hcap);
-    if (hun) atomicAdd((unsigned long long *)&I->hub_units, (unsigned long long)hun);
-    if (hsu) atomicAdd((unsigned long long *)&I->hub_sunits, (unsigned long long)hsu);
-    atomicMax((unsigned long long *)&I->rmax, (unsigned long long)rmax);
-    atomicMax((unsigned long long *)&I->kmax, (unsigned long long)kmax);
-    if (ksum) {
-      // node weights are non-negative and each addend is below 2^62, so the
-      // add that carries the total past 2^62 sees it before any wrap
-      const unsigned long long old = atomicAdd((unsigned long long *)&I->ksum, (unsigned long long)ksum);
-      if (old >= (1ull << 62) || old + (unsigned long long)ksum >= (1ull << 62)) ksat = 1;
+    acc.hcap = wsum_ll(acc.hcap);
+    acc.hun = wsum_ll(acc.hun);
+    acc.hsu = wsum_ll(acc.hsu);
+    acc.wabs = wsum_ll(acc.wabs);
+    acc.kneg = wsum_ll(acc.kneg);
+    acc.ents = wsum_ll(acc.ents);
+    acc.hmax = wmax_ll(acc.hmax);
+    acc.rmax = wmax_ll(acc.rmax);
+    acc.kmax = wmax_ll(acc.kmax);
+    // each lane's ksum is below 2^62: pairwise sums cannot wrap, and a sum
+    // that reaches 2^62 saturates the flag
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int64_t y = __shfl_xor_sync(FULL, acc.ksum, o);
+      const int64_t ys = __shfl_xor_sync(FULL, acc.ksat, o);
+      acc.ksum += y;
+      acc.ksat |= ys;
+      if (acc.ksum >= KSAT) {
+        acc.ksum = KSAT - 1;
+        acc.ksat = 1;
+      }
     }
-    if (ksat) atomicOr((unsigned long long *)&I->ksat, 1ull);
-    if (wabs) atomicAdd((unsigned long long *)&I->wabs, (unsigned long long)wabs);
-    if (kneg) atomicAdd((unsigned long long *)&I->pad, (unsigned long long)kneg);
-    if (hmax) atomicMax((unsigned long long *)&I->hub_maxcap, (unsigned long long)hmax);
-    if (ents) atomicAdd((unsigned long long *)&I->nnz, (unsigned long long)ents);
-    for (int i = 0; i < NB; ++i) bc[i] = 0;
-    hcap = hun = hsu = rmax = kmax = ksum = wabs = kneg = hmax = ents = ksat = 0;
+    if (lane == 0) stats_flush(info + cur, acc);
+    __syncwarp();
+    if (lane < NB) {
+      const long long c = s_bc[wib][lane];
+      if (c) atomicAdd((unsigned long long *)&info[cur].bcnt[lane], (unsigned long long)c);
+      s_bc[wib][lane] = 0;
+    }
+    __syncwarp();
+    stats_clear(acc);
   };
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < vtot;
-       i += warps_total) {
-    const int j = find_job(vstart, njobs, i);
-    const LJob *J = jobs + j;
-    const int64_t v = i - vstart[j];
-    const int64_t beg = J->off[v], end = J->off[v + 1];
+  for (int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; i0 < vtot;
+       i0 += warps_total * 32) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < vtot;
+    int j = 0;
+    int64_t deg = 0, beg = 0, kv = 0;
+    const LJob *J = jobs;
+    if (valid) {
+      j = find_job(vstart, njobs, i);
+      J = jobs + j;
+      const int64_t v = i - vstart[j];
+      beg = J->off[v];
+      deg = J->off[v + 1] - beg;
+      kv = J->k[v];
+    }
+    // row sums of |w|: short rows by their lane, long rows by the warp
     long long ra = 0;
-    if (J->wtype == W_NONE) {
-      ra = end - beg;
-    } else {
-      for (int64_t e = beg + lane; e < end; e += 32) {
+    const bool wt = valid && J->wtype != W_NONE;
+    if (valid && !wt) ra = deg;
+    if (wt && deg <= 32) {
+#pragma unroll 4
+      for (int64_t e = beg; e < beg + deg; ++e) {
         const long long x = load_w(J->w, J->wtype, e);
         ra += x < 0 ? -x : x;
       }
-      ra = wsum_ll(ra);
     }
-    if (lane == 0) {
-      if (j != cur) {
+    for (unsigned m = __ballot_sync(FULL, wt && deg > 32); m; m &= m - 1) {
+      const int l = __ffs(m) - 1;
+      const int jl = __shfl_sync(FULL, j, l);
+      const int64_t bl = __shfl_sync(FULL, beg, l), dl = __shfl_sync(FULL, deg, l);
+      const LJob *Jl = jobs + jl;
+      long long sl = 0;
+      for (int64_t e = bl + lane; e < bl + dl; e += 32) {
+        const long long x = load_w(Jl->w, Jl->wtype, e);
+        sl += x < 0 ? -x : x;
+      }
+      sl = wsum_ll(sl);
+      if (lane == l) ra = sl;
+    }
+    const int b = valid ? bucket_of(deg, J->warp_max) : -1;
+    if (valid) part_stats_add(info + j, deg, b);
+    const int j0 = __shfl_sync(FULL, j, 0);
+    if (__all_sync(FULL, !valid || j == j0)) {
+      if (j0 != cur) {
         flush();
-        cur = j;
+        cur = j0;
       }
-      const int64_t deg = end - beg;
-      const int b = bucket_of(deg, J->warp_max);
-      bc[b] += 1;
-      ents += deg;
-      if (b == B_HUB) {
-        const int64_t cap = hub_cap(deg);
-        hcap += cap;
-        if (cap > hmax) hmax = cap;
-        hun += (deg + HUB_CHUNK - 1) / HUB_CHUNK;
-        hsu += (cap + HUB_SCHUNK - 1) / HUB_SCHUNK;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const int c = __popc(__ballot_sync(FULL, b == k));
+        if (lane == k && c) s_bc[wib][k] += c;
       }
-      if (b >= PB0) {
-        // rows of more than 1024 entries are few: their sizes go straight
-        // to the job's per-bucket totals
-        PartStat *ps = &info[j].pst[b - PB0];
-        const int64_t P = part_count_of(deg), C = part_chunks_of(deg);
-        const int64_t cap = hub_cap(deg);
-        atomicAdd((unsigned long long *)&ps->rows, 1ull);
-        atomicAdd((unsigned long long *)&ps->nnz, (unsigned long long)deg);
-        atomicAdd((unsigned long long *)&ps->parts, (unsigned long long)P);
-        if (C) {
-          atomicAdd((unsigned long long *)&ps->chunks, (unsigned long long)C);
-          atomicAdd((unsigned long long *)&ps->cells, (unsigned long long)(P * C));
-        }
-        atomicAdd((unsigned long long *)&ps->cap, (unsigned long long)cap);
-        atomicAdd((unsigned long long *)&ps->sunits,
-                  (unsigned long long)((cap + HUB_SCHUNK - 1) / HUB_SCHUNK));
-        atomicMax((unsigned long long *)&ps->maxcap, (unsigned long long)cap);
-      }
-      if (ra > rmax) rmax = ra;
-      wabs += ra;
-      const int64_t kv = J->k[v];
-      if (kv < 0) {
-        kneg += 1;
-      } else {
-        if (kv > kmax) kmax = kv;
-        if (kv >= ((int64_t)1 << 62) - ksum) ksat = 1;  // the running total would reach 2^62
-        else ksum += kv;
-      }
+      if (valid) stats_add(acc, deg, b, ra, kv);
+    } else if (valid) {
+      // a window across two jobs: each vertex's figures to its own job
+      StatAcc one;
+      stats_clear(one);
+      stats_add(one, deg, b, ra, kv);
+      stats_flush(info + j, one);
+      atomicAdd((unsigned long long *)&info[j].bcnt[b], 1ull);
     }
   }
-  if (lane == 0) flush();
+  flush();
 }
 
 void launch_level_stats(const LJob *jobs, const int64_t *vstart, int njobs, int64_t vtot,
                         LevelInfo *info, cudaStream_t st, const Dev &d) {
   if (vtot <= 0) return;
-  k_level_stats<<<grid_for(vtot * 32, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, info);
+  k_level_stats<<<grid_for(vtot, 256, d), 256, 0, st>>>(jobs, vstart, njobs, vtot, info);
 }
 
 // ---------------------------------------------------------- gather layout --

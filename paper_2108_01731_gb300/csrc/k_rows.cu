@@ -156,14 +156,41 @@ __global__ void __launch_bounds__(256) k_emit_rows(RowSpace R, int64_t vt) {
       const int64_t vs = R.vstart[j0];
       const int32_t cbase = (int32_t)R.rank[vs];
       const int64_t e1 = s_e[wib][32];
-      for (int64_t e = s_e[wib][0] + lane; e < e1; e += 32) {
-        int lo = 0, hi = 32;  // the last vertex whose row starts at or before e
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_e[wib][mid] <= e) lo = mid; else hi = mid;
+      const int32_t *__restrict__ gnbr = J->gnbr;
+      const int32_t *__restrict__ gmapp = R.gmapp + vs;
+      // EU entries per lane per step: all their loads are issued before
+      // any of their stores
+      constexpr int EU = 4;
+      for (int64_t e0 = s_e[wib][0] + lane; e0 < e1; e0 += 32 * EU) {
+        int32_t cv[EU], Cr[EU];
+        int64_t pos[EU], wv[EU];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+          const int64_t e = e0 + 32 * u;
+          cv[u] = 0;
+          Cr[u] = 0;
+          pos[u] = -1;
+          wv[u] = 0;
+          if (e < e1) {
+            int lo = 0, hi = 32;  // the last vertex whose row starts at or before e
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (s_e[wib][mid] <= e) lo = mid; else hi = mid;
+            }
+            Cr[u] = s_c[wib][lo];
+            pos[u] = s_dst[wib][lo] + (e - s_e[wib][lo]);
+            cv[u] = __ldg(gmapp + __ldg(gnbr + e));
+            wv[u] = load_w(J->w, J->wtype, e);
+          }
         }
-        emit_one(R, J, vs, cbase, s_c[wib][lo], e, s_dst[wib][lo] + (e - s_e[wib][lo]),
-                 nintra);
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+          if (pos[u] < 0) continue;
+          const bool intra = cv[u] == Cr[u];
+          R.tnbr[pos[u]] = intra ? -1 : cv[u] - cbase;
+          R.tw[pos[u]] = wv[u];
+          nintra += intra ? 1 : 0;
+        }
       }
       __syncwarp();
     } else if (valid) {
@@ -645,17 +672,39 @@ __global__ void __launch_bounds__(256) k_rows_copy(const RowSpace R, int64_t nto
     s_src[wib][lane] = r < ntot ? R.boff[r] : 0;
     __syncwarp();
     const int64_t o0 = s_off[wib][0], o1 = s_off[wib][32];
-    for (int64_t p = o0 + lane; p < o1; p += 32) {
-      // the last row whose output starts at or before p (rows without
-      // entries share their offset with the next row)
-      int lo = 0, hi = 32;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_off[wib][mid] <= p) lo = mid; else hi = mid;
+    const int32_t *__restrict__ tnbr = R.tnbr;
+    const int64_t *__restrict__ tw = R.tw;
+    // CU positions per lane per step, loads before stores
+    constexpr int CU = 4;
+    for (int64_t p0 = o0 + lane; p0 < o1; p0 += 32 * CU) {
+      int32_t nb[CU];
+      int64_t wv[CU];
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int64_t p = p0 + 32 * u;
+        nb[u] = 0;
+        wv[u] = 0;
+        if (p < o1) {
+          // the last row whose output starts at or before p (rows without
+          // entries share their offset with the next row)
+          int lo = 0, hi = 32;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[wib][mid] <= p) lo = mid; else hi = mid;
+          }
+          const int64_t src = s_src[wib][lo] + (p - s_off[wib][lo]);
+          nb[u] = __ldcs(tnbr + src);
+          wv[u] = __ldcs(tw + src);
+        }
       }
-      const int64_t src = s_src[wib][lo] + (p - s_off[wib][lo]);
-      nbr_out[p] = R.tnbr[src];
-      w_out[p] = R.tw[src];
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int64_t p = p0 + 32 * u;
+        if (p < o1) {
+          nbr_out[p] = nb[u];
+          w_out[p] = wv[u];
+        }
+      }
     }
     __syncwarp();
   }

@@ -891,7 +891,11 @@ template <typename S, int E, int BK>
 __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     k_bm_warp(const JobDev *__restrict__ jobs, Buckets b, int64_t *ctr) {
   constexpr int WPB = 4;
-  constexpr int CAP = 64 * E;  // >= 2 * 32 * E
+  // slots per entry, before rounding up to a power of two: 4 for rows of
+  // up to 64 entries (fewer probes), 2 for longer ones (so that the
+  // tables do not cap the blocks per SM)
+  constexpr int SPREAD = E <= 2 ? 4 : 2;
+  constexpr int CAP = SPREAD * 32 * E;
   __shared__ unsigned long long tkey[WPB][CAP];
   __shared__ unsigned long long tval[WPB][CAP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -920,7 +924,7 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
     Chunk<E> x;
     load_chunk(J, beg, 0, deg, 32, lane, x);
     const Own o = own_of(J, v);
-    const int cap = (int)next_pow2(2 * (int64_t)deg);
+    const int cap = (int)next_pow2(SPREAD * (int64_t)deg);
     uint32_t won[E];
     fail |= !insert_chunk_won(x, at, Pow2Cap((uint32_t)cap), won);
     const bool row_moved = __any_sync(FULL, x.mv != 0);  // after the gathers have landed
@@ -1042,7 +1046,9 @@ __global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__
     // per entry of the row, a multiple of 32
     int64_t P;
     if (POW2) {
-      P = next_pow2(2 * deg) / CS;
+      // 4 slots per entry for rows of up to 256 entries (WARP_CAP), else 2
+      constexpr int64_t SP = BK == B_WARP ? 4 : 2;
+      P = next_pow2(SP * deg) / CS;
       if (P < 32) P = 32;
     } else {
       P = (deg * 8 + 5 * CS - 1) / (5 * CS);

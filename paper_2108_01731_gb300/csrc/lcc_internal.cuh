@@ -64,7 +64,7 @@ constexpr int T_BLK = 1024;
 constexpr int TP_BLK = 2048;     // table slots of the B_BLK kernel (power of two, 2 per entry)
 constexpr int TP_4K = 8192;      // of the B_T4K kernel (power of two, 2 per entry)
 constexpr int TP_8K = 13312;     // per block of the larger-row kernels (>= 1.6 * 8192)
-constexpr int WARP_CAP = 512;    // >= 2 * T_WARP
+constexpr int WARP_CAP = 1024;   // of the B_WARP kernel (power of two, 4 per entry)
 constexpr int HUB_CHUNK = 2048;  // edges per insertion unit
 constexpr int HUB_SCHUNK = 4096; // table slots per scoring unit
 

@@ -175,11 +175,12 @@ def random_gather_rate(dev):
 
 
 # DRAM bytes per scanned entry of the best-move kernels (dram__bytes_read.sum
-# + dram__bytes_write.sum over a round, per entry), from one ncu capture of a
-# small case of the same kernels (the capture and its scaling are recorded
-# beside it under profiles/), and the sha256[:16] of the k_round.cu it was
-# taken on.  The figure is reported only while that source is unchanged.
-BESTMOVE_TRAFFIC = {"k_round.cu": None, "dram_bytes_per_entry": None}
+# + dram__bytes_write.sum over every best-move launch of one step, per
+# scanned entry), from one ncu capture of the R-MAT 2^22 step (the capture and
+# its scaling are recorded under profiles/bestmove_dram_rmat22.md), and the
+# sha256[:16] of the k_round.cu it was taken on.  The figure is reported only
+# while that source is unchanged.
+BESTMOVE_TRAFFIC = {"k_round.cu": "92a3e28524d49748", "dram_bytes_per_entry": 39.16}
 
 
 def profile_traffic(src=None, measured=None):

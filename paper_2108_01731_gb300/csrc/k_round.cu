@@ -962,8 +962,11 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
 // cluster scores it and empties its slot (one chunk and CS <= 2: a vertex
 // costs one step per distinct cluster), or each block scans and empties its
 // own share, so no clearing pass is needed.  Block 0 combines the results.
+// The 256-thread kernel is held to 5 blocks per SM worth of registers (its
+// 32 KB tables allow 7; at 60 registers it ran 4).
 template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK, bool PF = false>
-__global__ void __launch_bounds__(THREADS) k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1)
+    k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
                                                       int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;

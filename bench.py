@@ -33,8 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Degree buckets of the best-move kernels (row lengths), as in lcc_stats.
-BUCKETS = ["<=4", "<=8", "<=16", "<=32", "<=64", "<=128", "<=256", "<=1024", "<=4096",
-           "<=8192", "<=16384", "<=32768", "<=65536", "<=131072", ">131072"]
+BUCKETS = ["<=4", "<=8", "<=16", "<=32", "<=64", "<=128", "<=256", "<=1024", "<=2048",
+           "<=4096", "<=8192", "<=16384", "<=32768", "<=65536", "<=131072", ">131072"]
 
 WORKLOADS = {
     # name: generator, node-weight mode, lambda p/q, rounds per Best-Moves

@@ -153,9 +153,10 @@ typedef struct lcc_stats {
   int64_t pairs_sorted;    /* inter-cluster entries sorted by compression */
   int64_t kernel_launches; /* kernels launched by this call */
   /* best-move device time per degree bucket (rows of <=4, <=8, <=16, <=32,
-     <=64, <=128, <=256, <=1024, <=4096, <=8192, <=16384, <=32768, <=65536,
-     <=131072 entries, and longer; the last element is unused), filled when
-     LCC_SCHED_TIMING is set */
+     <=64, <=128, <=256, <=1024, <=2048, <=4096, <=8192, <=16384, <=32768,
+     <=65536, <=131072 entries, and longer), filled when LCC_SCHED_TIMING is
+     set; with the partitioned path on (lcc_tuning.part_min), its whole time
+     is in the first bucket it takes */
   double ms_bucket[16];
   int64_t bucket_entries[16];  /* entries processed per degree bucket (after a
                                   round that marks no V', every row with an

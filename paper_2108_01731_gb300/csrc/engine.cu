@@ -555,7 +555,7 @@ void Engine::round(std::vector<Job *> &js) {
   // rows of the buckets from seg0 up take the partitioned path (tuning
   // part_min: 0 = none; 1024, 4096, 8192 or 16384 = rows longer than that)
   const int seg0 = tun.part_min == 0 ? NB
-                   : tun.part_min <= 1024 ? B_T4K
+                   : tun.part_min <= 1024 ? B_T2K
                    : tun.part_min <= 4096 ? B_T8K
                    : tun.part_min <= 8192 ? B_T16K : B_T32K;
   PartStat big;

@@ -963,9 +963,9 @@ __global__ void __launch_bounds__(128, E >= 8 ? 5 : (E >= 4 ? 7 : 8))
 // costs one step per distinct cluster), or each block scans and empties its
 // own share, so no clearing pass is needed.  Block 0 combines the results.
 // The 256-thread kernel is held to 5 blocks per SM worth of registers (its
-// 32 KB tables allow 7; at 60 registers it ran 4).
+// 32 KB tables allow 7; at 60 registers it ran 4), the 512-thread one to 2.
 template <typename S, int CS, int THREADS, int TP, int E, int CH, bool POW2, int BK, bool PF = false>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1)
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : (THREADS == 512 ? 2 : 1))
     k_bm_table(const JobDev *__restrict__ jobs, Buckets b,
                                                       int64_t *ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1822,7 +1822,7 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   };
   static int occ[10] = {0};
   static bool init = false;
-  static TableLaunch tl[8], tlp[3];
+  static TableLaunch tl[9], tlp[4];
   if (!init) {
     occ[0] = occ_blocks(k_bm_group<4, S>, 256, 0);
     occ[1] = occ_blocks(k_bm_group<8, S>, 256, 0);
@@ -1904,6 +1904,14 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
   mark(B_BLK);
   // buckets from seg0 up go to the partitioned path
   const int seg0 = pb ? pb->seg0 : NB;
+  if (B_T2K < seg0 && b.seg_cap[B_T2K] > 0) {
+    if (prefetch)
+      launch_table<S, 1, 512, TP_2K, 4, 1, true, B_T2K, true>(jobs, b, ctr, st, tlp[3],
+                                                               launches);
+    else
+      launch_table<S, 1, 512, TP_2K, 4, 1, true, B_T2K>(jobs, b, ctr, st, tl[8], launches);
+  }
+  if (B_T2K < seg0) mark(B_T2K);
   if (B_T4K < seg0 && b.seg_cap[B_T4K] > 0) {
     if (prefetch)
       launch_table<S, 1, 1024, TP_4K, 4, 1, true, B_T4K, true>(jobs, b, ctr, st, tlp[2],

@@ -50,18 +50,20 @@ enum Bucket : int {
   B_W128 = 5,   // deg <= 128: 4 entries per lane
   B_WARP = 6,   // deg <= 256: one 128-thread block, 2 entries per thread
   B_BLK = 7,    // deg <= 1024: one 256-thread block, shared-memory table
-  B_T4K = 8,    // deg <= 4096: one 1024-thread block
-  B_T8K = 9,    // deg <= 8192: one 1024-thread block, two chunks per thread
-  B_T16K = 10,  // deg <= 16384: cluster of 2 blocks, table in distributed shared memory
-  B_T32K = 11,  // deg <= 32768: cluster of 4
-  B_T64K = 12,  // deg <= 65536: cluster of 8
-  B_T128K = 13, // deg <= 131072: cluster of 16 (a non-portable cluster size)
-  B_HUB = 14,   // larger: global-memory table, many blocks per vertex
-  NB = 15
+  B_T2K = 8,    // deg <= 2048: one 512-thread block
+  B_T4K = 9,    // deg <= 4096: one 1024-thread block
+  B_T8K = 10,   // deg <= 8192: one 1024-thread block, two chunks per thread
+  B_T16K = 11,  // deg <= 16384: cluster of 2 blocks, table in distributed shared memory
+  B_T32K = 12,  // deg <= 32768: cluster of 4
+  B_T64K = 13,  // deg <= 65536: cluster of 8
+  B_T128K = 14, // deg <= 131072: cluster of 16 (a non-portable cluster size)
+  B_HUB = 15,   // larger: global-memory table, many blocks per vertex
+  NB = 16
 };
 constexpr int T_WARP = 256;
 constexpr int T_BLK = 1024;
 constexpr int TP_BLK = 2048;     // table slots of the B_BLK kernel (power of two, 2 per entry)
+constexpr int TP_2K = 4096;      // of the B_T2K kernel (power of two, 2 per entry)
 constexpr int TP_4K = 8192;      // of the B_T4K kernel (power of two, 2 per entry)
 constexpr int TP_8K = 13312;     // per block of the larger-row kernels (>= 1.6 * 8192)
 constexpr int WARP_CAP = 1024;   // of the B_WARP kernel (power of two, 4 per entry)
@@ -81,6 +83,7 @@ __host__ __device__ inline int bucket_of(int64_t deg, int warp_max = T_WARP) {
     return B_WARP;
   }
   if (deg <= T_BLK) return B_BLK;
+  if (deg <= 2048) return B_T2K;
   if (deg <= 4096) return B_T4K;
   if (deg <= 8192) return B_T8K;
   if (deg <= 16384) return B_T16K;
@@ -258,13 +261,13 @@ constexpr int LAYOUT_CLASSES = 34;
 constexpr int64_t LAYOUT_MIN_BYTES = (int64_t)64 << 20;
 
 // Sizes of the partitioned best-move path over the rows of one degree
-// bucket (B_T4K and above; see PART_*).
+// bucket (B_T2K and above; see PART_*).
 struct PartStat {
   int64_t rows, nnz;
   int64_t parts, chunks, cells;  // sums of P, of the rows' chunks, and of P * chunks
   int64_t cap, sunits, maxcap;   // the rows' global tables (the fallback)
 };
-constexpr int PB0 = B_T4K;           // first bucket the partitioned path can take
+constexpr int PB0 = B_T2K;           // first bucket the partitioned path can take
 constexpr int NPB = B_HUB - PB0 + 1;
 
 // Per-job results of the level statistics kernel.
@@ -281,7 +284,7 @@ struct LevelInfo {
   int64_t hub_maxcap;   // largest hub table
   int64_t nnz;          // entries (sum of deg)
   int64_t ksat;         // nonzero: the sum of node weights reached 2^62 (ksum is then not exact)
-  // rows of the buckets B_T4K .. B_HUB, per bucket (the partitioned path)
+  // rows of the buckets B_T2K .. B_HUB, per bucket (the partitioned path)
   PartStat pst[NPB];
 };
 

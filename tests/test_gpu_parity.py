@@ -32,7 +32,8 @@ def graphs():
         "rmat": I.to_numpy(I.rmat(14, 120000, seed=5)),
         "signed": I.to_numpy(I.random_signed_graph(300, 0.1, -4, 6, seed=6)),
         "giant": I.to_numpy(I.hub_graph(150000, 5, 0,
-                                        [5000, 12000, 25000, 50000, 100000, 140000],
+                                        [1300, 1700, 2000, 3000, 5000, 12000, 25000, 50000,
+                                         100000, 140000],
                                         seed=7, w_lo=1, w_hi=3)),
     }
 
@@ -307,7 +308,7 @@ def test_partitioned_long_rows_match_oracle(L, monkeypatch):
     """Rows longer than part_min entries split by cluster hash into parts of
     about 2048 entries, each merged in one block's shared memory (rows of one
     part merged straight from their entries), for every part_min from 1024 to
-    16384 and with the path off; the "giant" graph's hubs of 12,000 to
+    16384 and with the path off; the "giant" graph's hubs of 1,300 to
     140,000 draws, a signed-weight graph with rows of 8,000 to 32,000 entries
     and the hub and R-MAT graphs, alone and in a batch.  Then with the parts'
     tables cut to 64 slots, so that nearly every part overflows and its row

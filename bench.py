@@ -635,6 +635,29 @@ def run_ours(args, rank, world, local):
                    "frac": (round(c_min / (c_ms / 1e3) / 1e9 / peak, 4) if c_ms > 0 else None),
                    "bytes": "least bytes over the contraction's device time"}
 
+    # the legs that use the device-resident graph run first; it is freed
+    # before the end-to-end leg loads the same graph again from host memory,
+    # so that the two copies and their levels never share the device
+    coin = None
+    twin = None
+    if rank == 0 and not args.no_coin:
+        def run_coin():
+            sc = L.schedule(num_iter=wl["num_iter"], coin=True, seed=0)
+            torch.cuda.synchronize()
+            e0.record()
+            st = L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sc, labels_out=labels)[2]
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), st
+        coin = coin_leg(run_coin, wl)
+    if rank == 0 and not args.no_twin:
+        twin = twin_round(host, wl, lambda lab: L.lcc_desired(G, wl["p"], wl["q"],
+                                                              wl["mode"], lab))
+    torch.cuda.synchronize()
+    G.free()
+    G = None
+    torch.cuda.empty_cache()
+
     e2e = None
     if not args.no_e2e:
         pinned = {k: (torch.from_numpy(v).pin_memory() if v is not None else None)
@@ -667,15 +690,11 @@ def run_ours(args, rank, world, local):
         del pinned
 
     cpu = None
-    twin = None
     serving = None
     if rank == 0:
         v, desc, _ = oracle_sample(host, wl, args.cpu_seconds)
         cpu = {"value": round(v, 6), "unit": "GEdges/s", "cores": 1, "kind": "oracle",
                "sample": desc}
-        if not args.no_twin:
-            twin = twin_round(host, wl, lambda lab: L.lcc_desired(G, wl["p"], wl["q"],
-                                                                  wl["mode"], lab))
         if args.serving > 0:
             serving = serving_bench(L, args.serving, dev, args.serving_large)
     line = {"metric": "best-move GEdges/s", "value": round(value, 4), "unit": "GEdges/s",
@@ -717,16 +736,8 @@ def run_ours(args, rank, world, local):
         line["serving"] = serving
     if wl["mode"] == 1:
         line["config"]["modularity"] = modularity(stats[-1], wl["q"])
-    if rank == 0 and not args.no_coin:
-        def run_coin():
-            sc = L.schedule(num_iter=wl["num_iter"], coin=True, seed=0)
-            torch.cuda.synchronize()
-            e0.record()
-            st = L.lcc_cluster(G, wl["p"], wl["q"], wl["mode"], sc, labels_out=labels)[2]
-            e1.record()
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1), st
-        line["coin_schedule"] = coin_leg(run_coin, wl)
+    if coin is not None:
+        line["coin_schedule"] = coin
     if rank == 0 and args.sweep:
         try:
             line["density_sweep"] = density_sweep(L, dev, max(1, min(args.steps, 3)))
@@ -734,10 +745,6 @@ def run_ours(args, rank, world, local):
             line["density_sweep"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    try:
-        G.free()
-    except Exception:  # noqa: BLE001  (the line is out; a failed release ends the run anyway)
-        pass
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

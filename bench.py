@@ -177,20 +177,25 @@ def random_gather_rate(dev):
 # DRAM bytes per scanned entry of the best-move kernels (dram__bytes_read.sum
 # + dram__bytes_write.sum over every best-move launch of one step, per
 # scanned entry), from one ncu capture of the R-MAT 2^22 step (the capture and
-# its scaling are recorded under profiles/bestmove_dram_rmat22.md), and the
-# sha256[:16] of the k_round.cu it was taken on.  The figure is reported only
-# while that source is unchanged.
-BESTMOVE_TRAFFIC = {"k_round.cu": "92a3e28524d49748", "dram_bytes_per_entry": 39.16}
+# its scaling are recorded under profiles/bestmove_dram_rmat22.md), the
+# sha256[:16] of the k_round.cu it was taken on and the pregather tuning it
+# ran with.  The figure is reported only while that source is unchanged and
+# the timed run uses the same pregather choice (the flat gather pass moves
+# about 12 bytes per entry of its own).
+BESTMOVE_TRAFFIC = {"k_round.cu": "83f4e7da07330cea", "pregather": 1,
+                    "dram_bytes_per_entry": 39.16}
 
 
-def profile_traffic(src=None, measured=None):
+def profile_traffic(src=None, measured=None, pregather=None):
     """DRAM bytes per scanned entry of the best-move kernels, if measured on
-    the current kernel source (else None)."""
+    the current kernel source with the run's pregather choice (else None)."""
     measured = measured or BESTMOVE_TRAFFIC
     src = src or os.path.join(ROOT, "paper_2108_01731_gb300", "csrc", "k_round.cu")
     if not measured.get("k_round.cu") or not os.path.exists(src):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != measured["k_round.cu"]:
+        return None
+    if pregather is not None and measured.get("pregather") not in (None, pregather):
         return None
     return measured["dram_bytes_per_entry"]
 
@@ -598,7 +603,7 @@ def run_ours(args, rank, world, local):
     rounds = stats[-1]["rounds_total"]
     peak, peak_kind = measured_peaks()
     achieved = bm_bytes / (bm_ms / 1e3) / 1e9
-    tpe = profile_traffic()
+    tpe = profile_traffic(pregather=tuning["pregather"])
     roofline = {"kernel": "best-move (all degree buckets), per round", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
@@ -717,6 +722,7 @@ def run_ours(args, rank, world, local):
                                   "fuse_small": tuning["fuse_small"],
                                   "prefetch": tuning["prefetch"],
                                   "pregather": tuning["pregather"],
+                                  "part_min": tuning["part_min"],
                                   "autotune_s": round(t_tune, 2),
                                   "chosen_by": ("lcc_autotune on this graph before timing "
                                                 "(3 best-move rounds per routing)"

@@ -13,12 +13,15 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_profile_traffic_only_for_the_measured_source(tmp_path):
+def test_profile_traffic_only_for_the_measured_source_and_tuning(tmp_path):
     src = tmp_path / "k.cu"
     src.write_text("kernel source\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     m = {"k_round.cu": sha, "dram_bytes_per_entry": 21.5}
     assert bench.profile_traffic(str(src), m) == 21.5
+    m1 = dict(m, pregather=1)
+    assert bench.profile_traffic(str(src), m1, pregather=1) == 21.5
+    assert bench.profile_traffic(str(src), m1, pregather=0) is None
     src.write_text("changed kernel source\n")
     assert bench.profile_traffic(str(src), m) is None
     assert bench.profile_traffic(str(src), {"k_round.cu": None}) is None

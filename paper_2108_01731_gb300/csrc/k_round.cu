@@ -1386,8 +1386,7 @@ __global__ void __launch_bounds__(256) k_hub_final(const JobDev *__restrict__ jo
 // by a hash of their cluster into P parts, so that every cluster of the row
 // lies in exactly one part; each part is then merged in one block's
 // shared-memory table with no cluster barrier, no remote atomic and no
-// global table, and the parts' best candidates are reduced per row.  A row
-// of one part is merged straight from its entries and decided by the block.
+// global table, and the parts' best candidates are reduced per row.
 // A part whose distinct clusters overflow the table (possible only when many
 // clusters collide in the partition hash) marks its row, and such rows go
 // through the global-table hub kernels instead.
@@ -1533,28 +1532,14 @@ __global__ void __launch_bounds__(PC_T, 8) k_part_chunks(const JobDev *__restric
 }
 
 // One warp per row, after the scan of the count cells: each part's run of
-// entries and its row in one 16-byte descriptor (a row of one part: st = -1
-// and its degree, for a merge straight from the row).
-__global__ void __launch_bounds__(256) k_part_desc(const JobDev *__restrict__ jobs, PartBufs P) {
+// entries and its row in one 16-byte descriptor.
+__global__ void __launch_bounds__(256) k_part_desc(PartBufs P) {
   const int lane = threadIdx.x & 31;
   const int64_t H = *P.nrows;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < H;
        h += warps_total) {
     const int64_t p0 = P.part_off[h], np = P.part_off[h + 1] - p0;
-    if (np == 1) {
-      if (lane == 0) {
-        const uint64_t item = P.row[h];
-        const JobDev *J = jobs + (int)(item >> 32);
-        const int32_t v = (int32_t)(uint32_t)item;
-        PartDesc d;
-        d.st = -1;
-        d.cnt = (int32_t)(J->off[v + 1] - J->off[v]);
-        d.h = (int32_t)h;
-        P.desc[p0] = d;
-      }
-      continue;
-    }
     const int64_t C = P.chunk_off[h + 1] - P.chunk_off[h];
     const int64_t cb = P.cell_off[h];
     for (int64_t pi = lane; pi < np; pi += 32) {
@@ -1585,14 +1570,12 @@ __global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restri
   __shared__ int32_t red_c[2][NW];
   __shared__ long long red_w[2][NW];
   __shared__ int red_v[2][NW];
-  __shared__ int s_mv[2];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   for (int sl = tid; sl < PART_TP; sl += PART_T) {
     tkey[sl] = SLOT_EMPTY;
     tval[sl] = 0;
   }
-  if (tid < 2) s_mv[tid] = 0;
-  PullCount::init();  // includes the barrier that publishes the empty table
+  __syncthreads();  // the empty table
   const int64_t H = *P.nrows;
   const int64_t NP = H > 0 ? P.part_off[H] : 0;
   long long ncand = 0;
@@ -1614,7 +1597,6 @@ __global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restri
     // the row's own label and weight are needed only when the part is scored
     const int32_t Lv = J.L[v];
     const int64_t kv = J.k[v];
-    const bool direct = d.st < 0;
     // 3.25 slots per entry (at most table_slots): few probes per insert
     int64_t cap = ((int64_t)d.cnt * 13 + 3) / 4;
     cap = (cap + 31) & ~(int64_t)31;
@@ -1631,29 +1613,22 @@ __global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restri
       won1[i] = NOSLOT;
     }
     bool fail = false;
-    uint32_t mv = 0;
-    const int64_t beg = direct ? J.off[v] : 0;
     for (int64_t t0 = 0; t0 < d.cnt; t0 += STEP) {
       const int64_t t1 = t0 + STEP < d.cnt ? t0 + STEP : d.cnt;
       Chunk<E> x;
-      if (direct) {
-        load_chunk(J, beg, t0, t1, PART_T, tid, x);
-        mv |= x.mv;
-      } else {
-        x.mv = 0;
+      x.mv = 0;
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-          const int64_t e = t0 + (int64_t)i * PART_T + tid;
-          x.c[i] = -1;
-          x.k[i] = KNONE;
-          x.w[i] = 0;
-          if (e < t1) {
-            const unsigned long long wd =
-                (unsigned long long)ld_stream((const int64_t *)(P.pword + d.st + e));
-            x.c[i] = (int32_t)(uint32_t)wd;
-            x.k[i] = (uint32_t)(wd >> 32);
-            x.w[i] = ld_stream(P.pw + d.st + e);
-          }
+      for (int i = 0; i < E; ++i) {
+        const int64_t e = t0 + (int64_t)i * PART_T + tid;
+        x.c[i] = -1;
+        x.k[i] = KNONE;
+        x.w[i] = 0;
+        if (e < t1) {
+          const unsigned long long wd =
+              (unsigned long long)ld_stream((const int64_t *)(P.pword + d.st + e));
+          x.c[i] = (int32_t)(uint32_t)wd;
+          x.k[i] = (uint32_t)(wd >> 32);
+          x.w[i] = ld_stream(P.pw + d.st + e);
         }
       }
       if (!two)
@@ -1663,7 +1638,6 @@ __global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restri
       else
         fail |= !insert_chunk_won(x, at, geo, won1);
     }
-    if (mv) atomicOr(&s_mv[par], 1);
     fail = __syncthreads_or(fail) != 0;
     S best = ScoreOps<S>::lowest();
     int32_t bc = INT32_MAX;
@@ -1695,32 +1669,19 @@ __global__ void __launch_bounds__(PART_T, 3) k_part_merge(const JobDev *__restri
       ws = warp_sum_ll(ws);
       vv = __any_sync(FULL, vv);
       if (lane == 0) {
-        const int moved = s_mv[par];
-        s_mv[par] = 0;
-        if (direct) {
-          if (fail) {
-            const int64_t pos = (int64_t)atomicAdd((unsigned long long *)P.nfallback, 1ull);
-            P.fallback[pos] = item;
-          } else {
-            write_desired<S>(J, v, d.cnt, Lv, kv, own_weight(J, v, Lv), bs, bcc, ws, vv != 0,
-                             moved != 0);
-          }
-        } else {
-          P.part_score[q] = (i128)bs;
-          P.part_cid[q] = bcc;
-          if (ws) atomicAdd((unsigned long long *)&P.stay[h], (unsigned long long)ws);
-          if (vv || fail) atomicOr(&P.flag[h], (vv ? 1 : 0) | (fail ? 4 : 0));
-        }
+        P.part_score[q] = (i128)bs;
+        P.part_cid[q] = bcc;
+        if (ws) atomicAdd((unsigned long long *)&P.stay[h], (unsigned long long)ws);
+        if (vv || fail) atomicOr(&P.flag[h], (vv ? 1 : 0) | (fail ? 4 : 0));
       }
     }
     par ^= 1;
   }
   ncand = warp_sum_ll(ncand);
   if (lane == 0 && ncand) atomicAdd((unsigned long long *)&ctr[C_CANDS], (unsigned long long)ncand);
-  PullCount::flush(ctr);
 }
 
-// One warp per row of more than one part: the best of its parts, then the
+// One warp per row: the best of its parts, then the
 // decision; a row whose part overflowed goes to the fallback list for the
 // global-table kernels.
 template <typename S>
@@ -1733,7 +1694,6 @@ __global__ void __launch_bounds__(256) k_part_final(const JobDev *__restrict__ j
   for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < H;
        h += warps_total) {
     const int64_t q0 = P.part_off[h], q1 = P.part_off[h + 1];
-    if (q1 - q0 == 1) continue;  // decided by the merge
     const uint64_t item = P.row[h];
     const JobView J = view_of(jobs + (int)(item >> 32));
     const int32_t v = (int32_t)(uint32_t)item;
@@ -1962,7 +1922,7 @@ void bestmove_impl(const JobDev *jobs, const Buckets &b, const HubBufs &h, int64
       k_part_chunks<true><<<(int)g, PC_T, 0, st>>>(jobs, *pb);
       *launches += 6;
     }
-    k_part_desc<<<rg, 256, 0, st>>>(jobs, *pb);
+    k_part_desc<<<rg, 256, 0, st>>>(*pb);
     g = pb->max_parts < (int64_t)d.sms * occ_merge ? pb->max_parts : (int64_t)d.sms * occ_merge;
     k_part_merge<S><<<(int)(g > 0 ? g : 1), PART_T, PART_TP * 16, st>>>(jobs, *pb, ctr);
     k_part_final<S><<<rg, 256, 0, st>>>(jobs, *pb, ctr);

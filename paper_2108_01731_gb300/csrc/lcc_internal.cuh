@@ -292,20 +292,21 @@ struct LevelInfo {
 // (lcc_tuning.part_min) up: the entries of a row are split by a hash of
 // their cluster into P = ceil(deg / PART_ENT) parts (at most PART_MAXP),
 // counted and scattered in chunks of PART_CH entries, and each part is merged
-// by one PART_T-thread block in a table of at most PART_TP slots.  A row of
-// one part is merged straight from its entries.
+// by one PART_T-thread block in a table of at most PART_TP slots.
 constexpr int PART_ENT = 1024;
 constexpr int PART_MAXP = 4096;
 constexpr int PART_CH = 4096;
 constexpr int PART_T = 256;
 constexpr int PART_TP = 3328;  // table slots of a part's block (52 KB, 3.25 * PART_ENT)
+// every row the path can take (more than T_BLK entries) has several parts
+static_assert(PART_ENT <= T_BLK, "a row of the partitioned path must have more than one part");
 __host__ __device__ inline int64_t part_count_of(int64_t deg) {
   const int64_t p = (deg + PART_ENT - 1) / PART_ENT;
   return p < PART_MAXP ? p : PART_MAXP;
 }
-// Chunks of the count and scatter passes (none for a row of one part).
+// Chunks of the count and scatter passes.
 __host__ __device__ inline int64_t part_chunks_of(int64_t deg) {
-  return part_count_of(deg) > 1 ? (deg + PART_CH - 1) / PART_CH : 0;
+  return (deg + PART_CH - 1) / PART_CH;
 }
 
 // Per-job accumulators of the objective kernels.

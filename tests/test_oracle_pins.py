@@ -456,31 +456,42 @@ def rows_graph(n, rows):
     return {"n": n, "off": off, "nbr": nbr, "w": w}
 
 
-def brute_best_moves(g, k, p, q, L, num_iter, vset, trace, rows=None, depth=0, phase=0):
+def brute_best_moves(g, k, p, q, L, num_iter, vset, trace, rows=None, depth=0, phase=0,
+                     coin_seed=None):
     """Algorithm 1's Best-Moves with every desired cluster found by brute
     force (re-evaluating the Sec. 2 definition per candidate), the moves of a
     round applied together (Sec. 3.2.1) and V' per Sec. 3.2.2.  L is updated
     in place; the moves of each round are appended to `trace`, and with
-    `rows` a record (depth, phase, round, |V'|, entries, moved, 0) too."""
+    `rows` a record (depth, phase, round, |V'|, entries, moved, held) too.
+    With coin_seed, a vertex that wants to move does so only when the
+    SplitMix64 coin of (seed, phase, depth, round, vertex) allows it; one held
+    back keeps its label and is evaluated again next round, and the call ends
+    when no vertex wants to move."""
     W, E = dense(g)
     n = g["n"]
     off, nbr = g["off"], g["nbr"]
     vp = np.ones(n, bool)
     any_moved = False
-    for _ in range(num_iter):
+    for t in range(num_iter):
         D = L.copy()
         for v in range(n):
             if vp[v]:
                 D[v] = brute_desired(g, W, E, k, p, q, L, v)
+        want = D != L
+        held = np.zeros(n, bool)
+        if coin_seed is not None:
+            held = np.array([bool(want[v]) and not coin(coin_seed, phase, depth, t, v)
+                             for v in range(n)], bool)
+            D[held] = L[held]
         moved = D != L
         trace.append(int(moved.sum()))
         if rows is not None:
             deg = np.diff(off)
             rows.append((depth, phase, len(trace) - 1, int(vp.sum()), int(deg[vp].sum()),
-                         int(moved.sum()), 0))
-        if not moved.any():
+                         int(moved.sum()), int(held.sum())))
+        if not want.any():
             break
-        any_moved = True
+        any_moved |= bool(moved.any())
         left = set(int(x) for x in L[moved])
         L[:] = D
         vp = np.zeros(n, bool)
@@ -493,23 +504,28 @@ def brute_best_moves(g, k, p, q, L, num_iter, vset, trace, rows=None, depth=0, p
             for x in range(n):
                 if int(L[x]) in left:
                     vp[nbr[off[x]:off[x + 1]]] = True
+        vp |= held
     return any_moved
 
 
-def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log):
+def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log, coin_seed=None,
+                      max_levels=64):
     """Parallel-CC (Algorithm 1) on one level: singletons, Best-Moves, and
-    unless nothing moved or the level did not shrink, Compress (a dictionary
-    keyed by the two endpoint clusters, intra-cluster pairs dropped, coarse
-    node weight = cluster weight, coarse ids = occupied ids in order),
-    recursion, Flatten and -- with refinement (Sec. 3.2.3) -- a full
-    Best-Moves on this level from the flattened labels, at every depth."""
+    unless nothing moved, the level did not shrink or the level cap is
+    reached (at most max_levels levels), Compress (a dictionary keyed by the
+    two endpoint clusters, intra-cluster pairs dropped, coarse node weight =
+    cluster weight, coarse ids = occupied ids in order), recursion, Flatten
+    and -- with refinement (Sec. 3.2.3) -- a full Best-Moves on this level
+    from the flattened labels, at every depth (coin phase 0 on the way down,
+    1 in refinement)."""
     n = g["n"]
     log["levels"] = max(log["levels"], depth + 1)
     L = np.arange(n, dtype=np.int32)
     trace = []
-    moved = brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 0)
+    moved = brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 0,
+                             coin_seed)
     log["rounds"] += len(trace)
-    if not moved:
+    if not moved or depth + 1 >= max_levels:
         return L
     occupied = sorted(set(int(c) for c in L))
     if len(occupied) == n:
@@ -529,11 +545,13 @@ def brute_parallel_cc(g, k, p, q, num_iter, vset, refine, depth, log):
     k2 = np.zeros(n2, np.int64)
     for v in range(n):
         k2[rank[int(L[v])]] += int(k[v])
-    L2 = brute_parallel_cc(rows_graph(n2, rows), k2, p, q, num_iter, vset, refine, depth + 1, log)
+    L2 = brute_parallel_cc(rows_graph(n2, rows), k2, p, q, num_iter, vset, refine, depth + 1, log,
+                           coin_seed, max_levels)
     L = np.array([L2[rank[int(c)]] for c in L], np.int32)
     if refine:
         trace = []
-        brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 1)
+        brute_best_moves(g, k, p, q, L, num_iter, vset, trace, log.get("rows"), depth, 1,
+                         coin_seed)
         log["rounds"] += len(trace)
         log["refine"].append((depth, trace))
     return L
@@ -590,6 +608,78 @@ def test_round_trace_by_brute_force(case):
                        vset=vset, trace=True)
     assert [tuple(int(x) for x in r) for r in tr] == log["rows"]
     assert any(r[3] < n for r in log["rows"])  # V' shrank below V in some round
+
+
+def test_round_trace_counts_isolated_vertices_in_the_first_v_prime():
+    """V' starts as all of V (Algorithm 1), vertices without an edge included:
+    the first round's |V'| counts them (they cannot move), on a graph with
+    three vertices appended that have no edge, at every level of the run."""
+    seed, n, p, q, vset, kmode = DEEP_CASES[1]
+    g0 = small_graph(seed * 7 + n, n=n, p=0.45, lo=-2, hi=5)
+    iso = 3
+    g = {"n": n + iso, "off": np.concatenate([g0["off"], np.repeat(g0["off"][-1], iso)]),
+         "nbr": g0["nbr"], "w": g0["w"]}
+    k = np.ones(n + iso, np.int64)
+    log = {"levels": 0, "rounds": 0, "refine": [], "rows": []}
+    brute_parallel_cc(g, k, p, q, 4, vset, True, 0, log)
+    *_, tr = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=O.NODEW_CUSTOM, k=k, num_iter=4,
+                       vset=vset, trace=True)
+    assert [tuple(int(x) for x in r) for r in tr] == log["rows"]
+    assert log["rows"][0][3] == n + iso
+
+
+@pytest.mark.parametrize("case", DEEP_CASES[:4])
+def test_level_cap_by_brute_force(case):
+    """With a cap of 1, 2 or 3 levels the oracle stops coarsening exactly
+    where Algorithm 1 simulated with the same cap does: labels, exact
+    objective, levels and rounds."""
+    seed, n, p, q, vset, kmode = case
+    g = small_graph(seed * 7 + n, n=n, p=0.45, lo=-2, hi=5)
+    k = np.ones(n, np.int64) if kmode == 0 else (np.arange(n) % 3 + 1).astype(np.int64)
+    W, E = dense(g)
+    for cap in (1, 2, 3):
+        log = {"levels": 0, "rounds": 0, "refine": []}
+        L = brute_parallel_cc(g, k, p, q, 10, vset, True, 0, log, max_levels=cap)
+        first = {}
+        for v in range(n):
+            first.setdefault(int(L[v]), v)
+        want = np.array([first[int(c)] for c in L], np.int32)
+        labels, num, den, st = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=O.NODEW_CUSTOM,
+                                         k=k, num_iter=10, vset=vset, max_levels=cap)
+        assert np.array_equal(labels, want), cap
+        assert Fraction(num, den) == cc_definition(W, E, k, Fraction(p, q), want), cap
+        assert st[0] == log["levels"] == min(cap, log["levels"]) and st[1] == log["rounds"], cap
+        if cap == 1:
+            assert st[0] == 1
+
+
+@pytest.mark.parametrize("ci, cseed", [(1, 2), (1, 8), (2, 26)])
+def test_coin_multilevel_run_by_brute_force(ci, cseed):
+    """With the symmetry-breaking coin, the oracle's whole multi-level run
+    (labels, exact objective, levels, rounds, and the per-round record with
+    the held-back counts) equals Algorithm 1 simulated with brute-force moves
+    and the SplitMix64 coin keyed by (seed, phase, depth, round, vertex),
+    phase 1 in refinement.  The graphs and seeds are ones on which the coin
+    holds vertices back during refinement, so a coin keyed without the phase
+    would change the run."""
+    seed, n, p, q, vset, kmode = DEEP_CASES[ci]
+    g = small_graph(seed * 7 + n, n=n, p=0.45, lo=-2, hi=5)
+    k = np.ones(n, np.int64) if kmode == 0 else (np.arange(n) % 3 + 1).astype(np.int64)
+    W, E = dense(g)
+    log = {"levels": 0, "rounds": 0, "refine": [], "rows": []}
+    L = brute_parallel_cc(g, k, p, q, 10, vset, True, 0, log, coin_seed=cseed)
+    first = {}
+    for v in range(n):
+        first.setdefault(int(L[v]), v)
+    want = np.array([first[int(c)] for c in L], np.int32)
+    labels, num, den, st, tr = O.cluster(g["off"], g["nbr"], g["w"], p, q, mode=O.NODEW_CUSTOM,
+                                         k=k, num_iter=10, vset=vset, coin=True, seed=cseed,
+                                         trace=True)
+    assert np.array_equal(labels, want)
+    assert Fraction(num, den) == cc_definition(W, E, k, Fraction(p, q), want)
+    assert st[0] == log["levels"] and st[1] == log["rounds"]
+    assert [tuple(int(x) for x in r) for r in tr] == log["rows"]
+    assert sum(r[6] for r in log["rows"] if r[1] == 1) > 0  # held back in refinement
 
 
 # ------------------------------------------- range of the exact arithmetic --

@@ -387,7 +387,7 @@ typedef struct lcc_tuning {
                           0: every entry gathers its own word */
   int32_t part_min;    /* 1024, 4096, 8192 (the default) or 16384: rows of
                           more than part_min entries are hash-partitioned by
-                          cluster id into parts of about 2048 entries, each
+                          cluster id into parts of at most about 1024 entries, each
                           part merged in one 256-thread block's shared memory
                           and the parts' best clusters reduced per row (a
                           row whose part overflows its table falls back to

@@ -306,9 +306,8 @@ def test_tuning_routes_without_changing_results(L, tmp_path):
 
 def test_partitioned_long_rows_match_oracle(L, monkeypatch):
     """Rows longer than part_min entries split by cluster hash into parts of
-    about 2048 entries, each merged in one block's shared memory (rows of one
-    part merged straight from their entries), for every part_min from 1024 to
-    16384 and with the path off; the "giant" graph's hubs of 1,300 to
+    at most about 1024 entries, each merged in one block's shared memory, for
+    every part_min from 1024 to 16384 and with the path off; the "giant" graph's hubs of 1,300 to
     140,000 draws, a signed-weight graph with rows of 8,000 to 32,000 entries
     and the hub and R-MAT graphs, alone and in a batch.  Then with the parts'
     tables cut to 64 slots, so that nearly every part overflows and its row
